@@ -1,0 +1,189 @@
+"""FP64 CPU oracle for the batched Keplerian radial-velocity chi-square.
+
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite, the
+package smoke check and the benchmark's CPU-baseline leg may import this
+module.  It wraps ``kc_oracle.c`` (plain C, double precision) through ctypes
+and shares no code with the CUDA path.
+
+Every function takes and returns numpy float64 arrays.  Parameters of one
+system are laid out as (P, K, e, omega, M0) per planet followed by the
+offset gamma (``5*n_pl + 1`` values), the same order as Sec. 4.1 lists them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libkc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-shared", "-fPIC"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no GPU needed); returns the .so path."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", *_CFLAGS, _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        d = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.kco_set_threads.argtypes = [ctypes.c_int]
+        lib.kco_max_threads.restype = ctypes.c_int
+        lib.kco_mean_anomaly.restype = ctypes.c_double
+        lib.kco_mean_anomaly.argtypes = [ctypes.c_double] * 4
+        lib.kco_kepler_E.restype = ctypes.c_double
+        lib.kco_kepler_E.argtypes = [ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int)]
+        lib.kco_true_anomaly.restype = ctypes.c_double
+        lib.kco_true_anomaly.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.kco_planet_velocity.restype = ctypes.c_double
+        lib.kco_planet_velocity.argtypes = [d, ctypes.c_double, ctypes.c_double]
+        lib.kco_chi2.restype = ctypes.c_int
+        lib.kco_chi2.argtypes = [d, d, d, d, i64, ctypes.c_int, i64,
+                                 ctypes.c_double, ctypes.c_double, d, d]
+        lib.kco_chi2_ragged.restype = ctypes.c_int
+        lib.kco_chi2_ragged.argtypes = [d, i64p, i32p, d, d, d, i64p, i64,
+                                        ctypes.c_double, ctypes.c_double, d, d]
+        lib.kco_predict.restype = ctypes.c_int
+        lib.kco_predict.argtypes = [d, d, i64, ctypes.c_int, i64,
+                                    ctypes.c_double, d]
+        lib.kco_kepler_batch.argtypes = [d, d, i64, d, i32p]
+        lib.kco_mean_anomaly_batch.argtypes = [d, ctypes.c_double, d, d, i64, d]
+        lib.kco_true_anomaly_batch.argtypes = [d, d, i64, d]
+        _lib = lib
+        return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a: np.ndarray, ctype=ctypes.c_double):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's batch loops use."""
+    _load().kco_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().kco_max_threads())
+
+
+def mean_anomaly(t, t0, P, M0) -> np.ndarray:
+    """M = 2 pi frac((t - t0)/P) + M0 reduced to [-pi, pi] (Eqs. 4, 6)."""
+    t, P, M0 = np.broadcast_arrays(_f64(t), _f64(P), _f64(M0))
+    t, P, M0 = _f64(t), _f64(P), _f64(M0)
+    out = np.empty_like(t)
+    _load().kco_mean_anomaly_batch(_p(t.ravel()), float(t0), _p(P.ravel()),
+                                   _p(M0.ravel()), t.size, _p(out))
+    return out
+
+
+def kepler_E(M, e, return_iters: bool = False):
+    """Root E of E - e sin E = M (Eq. 1), elementwise."""
+    M, e = np.broadcast_arrays(_f64(M), _f64(e))
+    M, e = _f64(M), _f64(e)
+    E = np.empty_like(M)
+    it = np.empty(M.shape, dtype=np.int32)
+    _load().kco_kepler_batch(_p(M), _p(e), M.size, _p(E),
+                             _p(it, ctypes.c_int32))
+    return (E, it) if return_iters else E
+
+
+def true_anomaly(E, e) -> np.ndarray:
+    E, e = np.broadcast_arrays(_f64(E), _f64(e))
+    E, e = _f64(E), _f64(e)
+    f = np.empty_like(E)
+    _load().kco_true_anomaly_batch(_p(E), _p(e), E.size, _p(f))
+    return f
+
+
+def planet_velocity(p5, t, t0: float = 0.0) -> np.ndarray:
+    """Velocity of one planet (P, K, e, omega, M0) at each time t (Eq. 3)."""
+    p5 = _f64(p5)
+    lib = _load()
+    return np.array([lib.kco_planet_velocity(_p(p5), float(tk), float(t0))
+                     for tk in np.asarray(t, dtype=np.float64).ravel()])
+
+
+def predict(params, t, n_pl: int, t0: float = 0.0) -> np.ndarray:
+    """Model velocities gamma + sum_j v_j(t_k): [n_sys, n_obs] (Eq. 2)."""
+    params, t = _f64(params), _f64(t)
+    n_par = 5 * n_pl + 1
+    params = params.reshape(-1, n_par)
+    out = np.empty((params.shape[0], t.size))
+    rc = _load().kco_predict(_p(params), _p(t), params.shape[0], int(n_pl),
+                             t.size, float(t0), _p(out))
+    if rc != 0:
+        raise ValueError("oracle.predict: bad sizes")
+    return out
+
+
+def chi2(params, t, v, sigma, n_pl: int, t0: float = 0.0,
+         jitter: float = 0.0, grad: bool = False):
+    """chi-square of every system against shared data (Eq. 5).
+
+    Returns chi2 [n_sys], or (chi2, grad [n_sys, 5*n_pl+1]) when grad=True.
+    """
+    params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
+    n_par = 5 * n_pl + 1
+    params = params.reshape(-1, n_par)
+    n_sys = params.shape[0]
+    out = np.empty(n_sys)
+    g = np.empty((n_sys, n_par)) if grad else None
+    rc = _load().kco_chi2(_p(params), _p(t), _p(v), _p(sigma), n_sys,
+                          int(n_pl), t.size, float(t0), float(jitter), _p(out),
+                          _p(g) if grad else None)
+    if rc != 0:
+        raise ValueError("oracle.chi2: bad sizes")
+    return (out, g) if grad else out
+
+
+def chi2_ragged(params, par_off, n_pl, t, v, sigma, obs_off, t0: float = 0.0,
+                jitter: float = 0.0, grad: bool = False):
+    """chi-square of systems with their own planet counts and observations.
+
+    System s: parameters params[par_off[s] : par_off[s] + 5*n_pl[s] + 1],
+    observations t/v/sigma[obs_off[s] : obs_off[s+1]].
+    """
+    params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
+    par_off = np.ascontiguousarray(par_off, dtype=np.int64)
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    n_pl = np.ascontiguousarray(n_pl, dtype=np.int32)
+    n_sys = n_pl.size
+    out = np.empty(n_sys)
+    g = np.empty_like(params) if grad else None
+    rc = _load().kco_chi2_ragged(
+        _p(params), _p(par_off, ctypes.c_int64), _p(n_pl, ctypes.c_int32),
+        _p(t), _p(v), _p(sigma), _p(obs_off, ctypes.c_int64), n_sys,
+        float(t0), float(jitter), _p(out), _p(g) if grad else None)
+    if rc != 0:
+        raise ValueError("oracle.chi2_ragged: bad sizes")
+    return (out, g) if grad else out

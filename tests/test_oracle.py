@@ -1,0 +1,339 @@
+"""Pins for the FP64 CPU oracle against facts other than itself.
+
+Each test checks the oracle against something the paper or the mathematics
+fixes: brute-force bisection of Kepler's equation, exact rational phases,
+the circular-orbit closed form, the radial velocity as the time derivative
+of the line-of-sight position, invariances of chi-square, and central finite
+differences for the gradient.  None of these re-types the oracle's own
+formulas.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+TWO_PI = 2.0 * np.pi
+
+
+# ----------------------------------------------------------------- helpers
+
+def bisect_kepler(M, e, iters=200):
+    """Brute force: bisection of E - e sin E - M on [M - e, M + e]."""
+    M = np.asarray(M, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    lo, hi = M - e, M + e
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        neg = (mid - e * np.sin(mid) - M) < 0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+def exact_cycles(t, t0, P):
+    """frac((t - t0)/P) computed exactly from the binary doubles."""
+    q = (Fraction(float(t)) - Fraction(float(t0))) / Fraction(float(P))
+    return q - (q.numerator // q.denominator)
+
+
+def wrap_pi(x):
+    return (np.asarray(x) + np.pi) % TWO_PI - np.pi
+
+
+def angle_diff(a, b):
+    return np.abs(wrap_pi(np.asarray(a) - np.asarray(b)))
+
+
+# ------------------------------------------------------------ Kepler, Eq.1
+
+def test_kepler_matches_bisection(oracle_mod):
+    e = np.repeat(np.linspace(0.0, 0.99, 34), 41)
+    M = np.tile(np.linspace(-np.pi, np.pi, 41), 34)
+    E = oracle_mod.kepler_E(M, e)
+    Eb = bisect_kepler(M, e)
+    # the root is conditioned by 1/(1 - e cos E) <= 100 here
+    assert np.max(np.abs(E - Eb)) < 5e-14
+
+
+def test_kepler_special_cases(oracle_mod):
+    for e in (0.0, 0.1, 0.5, 0.9, 0.999):
+        assert abs(oracle_mod.kepler_E([0.0], [e])[0]) < 1e-300
+        assert abs(oracle_mod.kepler_E([np.pi], [e])[0] - np.pi) < 1e-15
+        assert abs(oracle_mod.kepler_E([-np.pi], [e])[0] + np.pi) < 1e-15
+    M = np.linspace(-3, 3, 13)
+    assert np.array_equal(oracle_mod.kepler_E(M, np.zeros_like(M)), M)
+
+
+def test_kepler_residual_and_iterations(oracle_mod):
+    rng = np.random.default_rng(1)
+    M = rng.uniform(-np.pi, np.pi, 20000)
+    e = rng.uniform(0.0, 0.999, 20000)
+    E, it = oracle_mod.kepler_E(M, e, return_iters=True)
+    resid = np.abs(E - e * np.sin(E) - M)
+    assert resid.max() < 1e-15
+    assert it.max() < 60
+
+
+def test_kepler_odd_symmetry(oracle_mod):
+    rng = np.random.default_rng(2)
+    M = rng.uniform(0, np.pi, 500)
+    e = rng.uniform(0, 0.95, 500)
+    assert np.max(np.abs(oracle_mod.kepler_E(M, e) + oracle_mod.kepler_E(-M, e))) < 1e-15
+
+
+# ----------------------------------------------------- mean anomaly, Eq. 4/6
+
+def test_mean_anomaly_exact_phase(oracle_mod):
+    """Against exact rational arithmetic at absolute epochs ~2.45e6 d, where
+    single precision fails (Sec. 5, mixed precision)."""
+    rng = np.random.default_rng(3)
+    n = 300
+    t = rng.uniform(2450000.0, 2456000.0, n)
+    P = np.exp(rng.uniform(np.log(0.5), np.log(4000.0), n))
+    M0 = rng.uniform(0, TWO_PI, n)
+    for t0 in (0.0, 2450000.0, 1234.5):
+        M = oracle_mod.mean_anomaly(t, t0, P, M0)
+        assert np.all(M >= -np.pi) and np.all(M <= np.pi)
+        for i in range(n):
+            cyc = exact_cycles(t[i], t0, P[i])
+            ref = TWO_PI * float(cyc) + M0[i]
+            assert angle_diff(M[i], ref) < 4e-15 * 8, (i, t0)
+
+
+def test_mean_anomaly_periodic(oracle_mod):
+    P = np.array([3.7, 17.25, 411.0])
+    M0 = np.array([0.3, 2.0, 5.9])
+    t = np.array([100.0, 250.0, 999.0])
+    a = oracle_mod.mean_anomaly(t, 0.0, P, M0)
+    b = oracle_mod.mean_anomaly(t + P, 0.0, P, M0)
+    assert np.max(angle_diff(a, b)) < 1e-12
+    assert np.max(angle_diff(oracle_mod.mean_anomaly(t, 0.0, P, M0 + TWO_PI), a)) < 1e-14
+    # at the epoch the mean anomaly is M0
+    for i in range(3):
+        at_epoch = oracle_mod.mean_anomaly(t[i:i + 1], t[i], P[i:i + 1], M0[i:i + 1])
+        assert angle_diff(at_epoch[0], M0[i]) < 1e-15
+
+
+# --------------------------------------------------- true anomaly, velocity
+
+def test_true_anomaly_matches_cartesian_form(oracle_mod):
+    rng = np.random.default_rng(4)
+    E = rng.uniform(-np.pi, np.pi, 5000)
+    e = rng.uniform(0, 0.99, 5000)
+    f = oracle_mod.true_anomaly(E, e)
+    D = 1 - e * np.cos(E)
+    cf = (np.cos(E) - e) / D
+    sf = np.sqrt((1 - e) * (1 + e)) * np.sin(E) / D
+    assert np.max(angle_diff(f, np.arctan2(sf, cf))) < 1e-13
+
+
+def test_velocity_is_derivative_of_line_of_sight_position(oracle_mod):
+    """Independent of Eq. 3's printed form: with a = 1 the line-of-sight
+    position is z = (cos E - e) sin w + sqrt(1-e^2) sin E cos w, and
+    v = K sqrt(1-e^2)/n * dz/dt with n = 2 pi/P.  dz/dt by central
+    differences, E by bisection, M = n t + M0 directly."""
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        P = np.exp(rng.uniform(np.log(2.0), np.log(1000.0)))
+        K = rng.uniform(1, 100)
+        e = rng.uniform(0, 0.9)
+        w = rng.uniform(0, TWO_PI)
+        M0 = rng.uniform(0, TWO_PI)
+        n = TWO_PI / P
+        t = rng.uniform(0, 3 * P, 8)
+        h = P * 1e-5
+
+        def z(tt):
+            E = bisect_kepler(wrap_pi(n * tt + M0), np.full_like(tt, e))
+            return (np.cos(E) - e) * np.sin(w) + np.sqrt(1 - e * e) * np.sin(E) * np.cos(w)
+
+        dzdt = (z(t + h) - z(t - h)) / (2 * h)
+        v_ref = K * np.sqrt(1 - e * e) / n * dzdt
+        v = oracle_mod.planet_velocity([P, K, e, w, M0], t, 0.0)
+        assert np.max(np.abs(v - v_ref)) < 1e-6 * K, (P, K, e, w, M0)
+
+
+def test_velocity_circular_closed_form(oracle_mod):
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        P, K = rng.uniform(2, 500), rng.uniform(1, 100)
+        w, M0 = rng.uniform(0, TWO_PI, 2)
+        t = rng.uniform(0, 1000, 16)
+        v = oracle_mod.planet_velocity([P, K, 0.0, w, M0], t, 0.0)
+        assert np.max(np.abs(v - K * np.cos(w + TWO_PI * t / P + M0))) < 1e-11 * K
+
+
+# ------------------------------------------------------------- chi2, Eq. 5
+
+def _random_systems(rng, n_sys, n_pl, e_max=0.9):
+    rows = []
+    for _ in range(n_sys):
+        r = []
+        for _ in range(n_pl):
+            r += [np.exp(rng.uniform(0, np.log(4000))), rng.uniform(1, 100),
+                  rng.uniform(0, e_max), rng.uniform(0, TWO_PI),
+                  rng.uniform(0, TWO_PI)]
+        rows.append(r + [rng.uniform(-10, 10)])
+    return np.array(rows)
+
+
+def test_chi2_circular_closed_form(oracle_mod):
+    rng = np.random.default_rng(7)
+    n_pl, n_obs = 3, 40
+    par = _random_systems(rng, 6, n_pl)
+    par[:, 2:5 * n_pl:5] = 0.0                     # e = 0
+    t = np.sort(rng.uniform(0, 800, n_obs))
+    v = rng.normal(0, 30, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    got = oracle_mod.chi2(par, t, v, sig, n_pl)
+    for s in range(par.shape[0]):
+        V = np.full(n_obs, par[s, -1])
+        for j in range(n_pl):
+            P, K, _, w, M0 = par[s, 5 * j:5 * j + 5]
+            V += K * np.cos(w + TWO_PI * t / P + M0)
+        ref = np.sum((V - v) ** 2 / sig ** 2)
+        assert abs(got[s] - ref) <= 1e-12 * ref
+
+
+def test_chi2_zero_for_noise_free_data(oracle_mod):
+    rng = np.random.default_rng(8)
+    par = _random_systems(rng, 1, 4)
+    t = np.sort(rng.uniform(2450000, 2454000, 256))
+    v = oracle_mod.predict(par, t, 4)[0]
+    sig = rng.uniform(1, 5, 256)
+    assert oracle_mod.chi2(par, t, v, sig, 4)[0] < 1e-20
+
+
+def test_chi2_invariances(oracle_mod):
+    rng = np.random.default_rng(9)
+    n_pl, n_obs = 4, 128
+    par = _random_systems(rng, 8, n_pl)
+    t = np.sort(rng.uniform(2450000, 2454000, n_obs))
+    v = rng.normal(0, 50, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    base = oracle_mod.chi2(par, t, v, sig, n_pl)
+    # planet permutation
+    perm = par.copy()
+    order = [2, 0, 3, 1]
+    for dst, src in enumerate(order):
+        perm[:, 5 * dst:5 * dst + 5] = par[:, 5 * src:5 * src + 5]
+    assert np.allclose(oracle_mod.chi2(perm, t, v, sig, n_pl), base, rtol=1e-13)
+    # common offset on model and data
+    shift = par.copy()
+    shift[:, -1] += 7.5
+    assert np.allclose(oracle_mod.chi2(shift, t, v + 7.5, sig, n_pl), base, rtol=1e-10)
+    # M0 -> M0 + 2 pi
+    m0 = par.copy()
+    m0[:, 4:5 * n_pl:5] += TWO_PI
+    assert np.allclose(oracle_mod.chi2(m0, t, v, sig, n_pl), base, rtol=1e-12)
+    # jitter adds in quadrature to sigma (Eq. 5)
+    jit = 2.5
+    assert np.allclose(oracle_mod.chi2(par, t, v, sig, n_pl, jitter=jit),
+                       oracle_mod.chi2(par, t, v, np.sqrt(sig ** 2 + jit ** 2), n_pl),
+                       rtol=1e-13)
+
+
+def test_chi2_time_shift_by_period(oracle_mod):
+    rng = np.random.default_rng(10)
+    par = _random_systems(rng, 5, 1)
+    t = np.sort(rng.uniform(2450000, 2452000, 32))
+    v = rng.normal(0, 50, 32)
+    sig = rng.uniform(1, 5, 32)
+    for s in range(5):
+        P = par[s, 0]
+        a = oracle_mod.chi2(par[s:s + 1], t, v, sig, 1)
+        b = oracle_mod.chi2(par[s:s + 1], t + P, v, sig, 1)
+        assert abs(a[0] - b[0]) <= 1e-10 * a[0]
+
+
+def test_chi2_zero_amplitude_planet_drops_out(oracle_mod):
+    rng = np.random.default_rng(11)
+    par = _random_systems(rng, 4, 3)
+    par[:, 5 + 1] = 0.0                               # K of planet 1
+    t = np.sort(rng.uniform(2450000, 2452000, 64))
+    v = rng.normal(0, 50, 64)
+    sig = rng.uniform(1, 5, 64)
+    red = np.concatenate([par[:, :5], par[:, 10:]], axis=1)
+    assert np.allclose(oracle_mod.chi2(par, t, v, sig, 3),
+                       oracle_mod.chi2(red, t, v, sig, 2), rtol=1e-14)
+
+
+def test_chi2_invalid_inputs_give_nan(oracle_mod):
+    rng = np.random.default_rng(12)
+    par = _random_systems(rng, 4, 2)
+    par[1, 2] = 1.0          # e = 1
+    par[2, 5] = 0.0          # P = 0
+    t = np.sort(rng.uniform(0, 100, 16))
+    v = rng.normal(0, 5, 16)
+    sig = np.ones(16)
+    out = oracle_mod.chi2(par, t, v, sig, 2)
+    assert np.isfinite(out[0]) and np.isfinite(out[3])
+    assert np.isnan(out[1]) and np.isnan(out[2])
+    sig[3] = 0.0
+    assert np.all(np.isnan(oracle_mod.chi2(par, t, v, sig, 2)))
+
+
+def test_ragged_matches_uniform(oracle_mod):
+    rng = np.random.default_rng(13)
+    par = _random_systems(rng, 6, 2)
+    t = np.sort(rng.uniform(2450000, 2452000, 50))
+    v = rng.normal(0, 50, 50)
+    sig = rng.uniform(1, 5, 50)
+    ref = oracle_mod.chi2(par, t, v, sig, 2)
+    n_pl = np.full(6, 2, np.int32)
+    par_off = np.arange(7) * 11
+    obs_off = np.arange(7) * 50
+    got = oracle_mod.chi2_ragged(par.ravel(), par_off, n_pl, np.tile(t, 6),
+                                 np.tile(v, 6), np.tile(sig, 6), obs_off)
+    assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("t0", [2450000.0, 0.0])
+def test_gradient_matches_central_differences(oracle_mod, t0):
+    rng = np.random.default_rng(14)
+    n_pl, n_obs = 3, 60
+    par = _random_systems(rng, 3, n_pl, e_max=0.8)
+    t = np.sort(rng.uniform(2450000, 2454000, n_obs))
+    v = rng.normal(0, 50, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    chi, g = oracle_mod.chi2(par, t, v, sig, n_pl, t0=t0, grad=True)
+    for s in range(par.shape[0]):
+        fd = np.empty(par.shape[1])
+        for q in range(par.shape[1]):
+            # 1e-6 relative step; a period step moves the phase by
+            # 2 pi |t - t0| h / P^2, so it is sized to move it by 3e-4 rad
+            # (truncation ~1e-8, rounding of a 1e6-cycle phase ~1e-6)
+            h = 1e-6 * max(abs(par[s, q]), 1e-3)
+            if q % 5 == 0 and q < 5 * n_pl:
+                P = par[s, q]
+                h = 3e-4 * P * P / (2 * np.pi * np.max(np.abs(t - t0)))
+            p1, p2 = par[s].copy(), par[s].copy()
+            p1[q] += h
+            p2[q] -= h
+            c1 = oracle_mod.chi2(p1[None], t, v, sig, n_pl, t0=t0)[0]
+            c2 = oracle_mod.chi2(p2[None], t, v, sig, n_pl, t0=t0)[0]
+            fd[q] = (c1 - c2) / (2 * h)
+        scale = np.maximum(np.abs(g[s]), 1e-3 * np.linalg.norm(g[s]))
+        assert np.max(np.abs(fd - g[s]) / scale) < 1e-5, (s, fd, g[s])
+
+
+def test_gradient_circular_closed_form(oracle_mod):
+    """e = 0: dv/dM0 = -K sin(w + M) and dv/dK = cos(w + M)."""
+    rng = np.random.default_rng(15)
+    P, K, w, M0, gam = 37.0, 20.0, 1.1, 0.4, 1.5
+    par = np.array([[P, K, 0.0, w, M0, gam]])
+    t = np.sort(rng.uniform(0, 500, 30))
+    v = rng.normal(0, 20, 30)
+    sig = rng.uniform(1, 5, 30)
+    _, g = oracle_mod.chi2(par, t, v, sig, 1, grad=True)
+    ph = w + TWO_PI * t / P + M0
+    r = gam + K * np.cos(ph) - v
+    wk = 1 / sig ** 2
+    assert np.isclose(g[0, 1], np.sum(2 * wk * r * np.cos(ph)), rtol=1e-12)
+    assert np.isclose(g[0, 4], np.sum(2 * wk * r * -K * np.sin(ph)), rtol=1e-12)
+    assert np.isclose(g[0, 3], np.sum(2 * wk * r * -K * np.sin(ph)), rtol=1e-12)
+    assert np.isclose(g[0, 5], np.sum(2 * wk * r), rtol=1e-12)
+    assert np.isclose(g[0, 0], np.sum(2 * wk * r * -K * np.sin(ph) * (-TWO_PI * t / P ** 2)),
+                      rtol=1e-11)
