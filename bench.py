@@ -1,0 +1,363 @@
+"""Benchmark: planet-observation evaluations per second of the batched
+Keplerian radial-velocity chi-square (mixed precision vs FP64) on GB300.
+
+Workload (default): the paper-shaped batch, n_sys = 4096 model systems with
+n_pl = 4 planets against n_obs = 256 observations of one star (synthetic,
+seeded; the paper's data set is not available).  One step = one fused
+chi-square evaluation of the whole batch (mean anomaly, Kepler solve,
+velocities, residuals, per-system reduction) through the C ABI.
+
+Timing: W warm-up steps, then K timed steps bracketed by a barrier and
+device synchronisation.  Each step's kernel is timed with CUDA events on the
+launching stream; a 256 MiB buffer is rewritten between steps (outside the
+events) so every step starts with a cold L2.  Multi-GPU (torchrun): every
+rank evaluates its own batch of the same shape (weak scaling, no
+data-path collective); the slowest rank's time is reported.
+
+`--impl reference` times the FP64 CPU oracle instead (the paper's
+CPU-reference role), on the host cores, on a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+N_SM = 152
+FP32_LANES_PER_SM = 128
+FALLBACK_SM_MHZ = 2070.0
+
+# Algorithmic FP32 work of one planet-observation evaluation of the mixed
+# path, in FLOPs (FMA = 2, add/mul = 1; MUFU sin/cos/rcp and integer or
+# select operations not counted), from the algorithm as implemented:
+#   double-single mean anomaly 17, start guess 2, three Danby steps of 22,
+#   one accurate sin/cos (Cody-Waite + Taylor) 27, sin/cos update of the
+#   last step 10, velocity 8, planet Kahan sum 4, and per observation the
+#   residual + weighted square + chi2 Kahan sum 10 (shared by n_pl planets).
+def mixed_flops_per_eval(n_pl: int) -> float:
+    return 17 + 2 + 3 * 22 + 27 + 10 + 8 + 4 + 10.0 / n_pl
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="kc", choices=["kc", "reference"])
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the built-in tile heuristic instead of the autotuner")
+    ap.add_argument("--tile", default=None,
+                    help="pin threads_per_system,block for the mixed chi2 kernel")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 / grid-sweep side measurements")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thread = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(
+                        ["nvidia-smi", "-i", str(self.index),
+                         f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                        capture_output=True, text=True, timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._thread = threading.Thread(target=run, daemon=True)
+        self._thread.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._thread:
+            self._thread.join(timeout=10)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 2 + i and s[2 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {}, "fallback"
+
+
+def oracle_cpu_baseline(w, seconds=3.0):
+    """Time the FP64 CPU oracle on the host cores over this workload's batch:
+    whole batches repeated until ~`seconds` of wall time.  Its observations
+    are formed by the oracle itself from the same seeded draws."""
+    import oracle
+    oracle.build()
+    v_obs = oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
+    cores = oracle.max_threads()
+    evals_per = w.n_sys * w.n_pl * w.n_obs
+    oracle.chi2(w.params[:64], w.t, v_obs, w.sigma, w.n_pl, w.t0)   # warm
+    reps, t_start = 0, time.perf_counter()
+    while True:
+        oracle.chi2(w.params, w.t, v_obs, w.sigma, w.n_pl, w.t0)
+        reps += 1
+        el = time.perf_counter() - t_start
+        if el >= seconds:
+            break
+    return {"value": evals_per * reps / el, "unit": "planet-obs evals/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{reps} x the {w.n_sys}-system batch ({evals_per} evals each), "
+                      f"{el:.1f} s wall, OpenMP over systems"}
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm, on the host cores."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    from paper_0812_2976_gb300 import synth
+    oracle.build()
+    w = synth.uniform(args.config, n_sys=None if args.config == 1 else 4096)
+    v = oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
+    per_step = 256                                  # systems per timed step
+    cores = oracle.max_threads()
+    for i in range(args.warmup):
+        sl = slice((i * per_step) % w.n_sys, (i * per_step) % w.n_sys + per_step)
+        oracle.chi2(w.params[sl], w.t, v, w.sigma, w.n_pl, w.t0)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        s0 = (i * per_step) % w.n_sys
+        oracle.chi2(w.params[s0:s0 + per_step], w.t, v, w.sigma, w.n_pl, w.t0)
+    el = time.perf_counter() - t0
+    evals = args.steps * per_step * w.n_pl * w.n_obs
+    value = evals / el
+    line = {
+        "impl": "reference", "metric": "planet-obs evals/s (chi2, npl=4, nobs=256)",
+        "value": value, "unit": "planet-obs evals/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.shape.name, "n_sys_per_step": per_step, "n_pl": w.n_pl,
+                   "n_obs": w.n_obs},
+        "cpu_baseline": {"value": value, "unit": "planet-obs evals/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{per_step} systems of the {w.shape.name} batch per step"},
+        "e2e": {"value": value, "unit": "planet-obs evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_kc(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    import paper_0812_2976_gb300 as kc
+    from paper_0812_2976_gb300 import build, synth
+    build.build()
+    kc._lib.load()
+
+    # each rank its own batch of the same shape (a shard of a larger sweep)
+    w = synth.uniform(args.config, seed=synth.SEED_BASE + args.config + 1000 * rank
+                      if rank else None)
+    P = torch.tensor(w.params, device=dev)
+    T = torch.tensor(w.t, device=dev)
+    S = torch.tensor(w.sigma, device=dev)
+    truth = torch.tensor(w.truth[None, :], device=dev)
+    V = kc.kc_rv_predict(truth, T, t0=w.t0)[0] + torch.tensor(w.noise, device=dev)
+    out = torch.empty(w.n_sys, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    evals = w.n_sys * w.n_pl * w.n_obs
+
+    tile_kind = "heuristic"
+    if args.tile:
+        g, b = (int(x) for x in args.tile.split(","))
+        kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, (g, b))
+        tile_kind = "pinned"
+    tile = kc.kc_get_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs)
+    if not args.no_tune and not args.tile:
+        tile, _ = kc.kc_autotune(P, T, V, S, kernel="chi2", mode="mixed", stream=stream)
+        tile_kind = "autotuned"
+
+    def step():
+        kc.kc_chi2_eval_mixed(P, T, V, S, out=out, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                      # cold L2 for every step
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    t_sum = sum(kernel_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sum = float(tt.item())
+    value = evals * args.steps * world / t_sum
+    ms_per_step = 1e3 * t_sum / args.steps
+
+    # end-to-end through the public API from pinned host buffers
+    hP = torch.tensor(w.params).pin_memory()
+    hT, hV, hS = T.cpu().pin_memory(), V.cpu().pin_memory(), S.cpu().pin_memory()
+    hout = torch.empty(w.n_sys, dtype=torch.float32).pin_memory()
+    dP, dT, dV, dS = (torch.empty_like(P), torch.empty_like(T), torch.empty_like(V),
+                      torch.empty_like(S))
+
+    def e2e_step():
+        dP.copy_(hP, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        dV.copy_(hV, non_blocking=True)
+        dS.copy_(hS, non_blocking=True)
+        kc.kc_chi2_eval_mixed(dP, dT, dV, dS, out=out, stream=stream)
+        hout.copy_(out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e_ev[i][0].record(stream)
+        e2e_step()
+        e_ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
+    h2d = hP.numel() * 8 + 3 * hT.numel() * 8
+    d2h = hout.numel() * 4
+    e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    extras = {}
+    if not args.no_extras:
+        # FP64 path on the same batch ("mixed vs FP64")
+        out64 = torch.empty(w.n_sys, dtype=torch.float64, device=dev)
+        if not args.no_tune:
+            kc.kc_autotune(P, T, V, S, kernel="chi2", mode="fp64", stream=stream)
+        for _ in range(3):
+            kc.kc_chi2_eval(P, T, V, S, out=out64, stream=stream)
+        f_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(min(args.steps, 20))]
+        for a, b in f_ev:
+            flush.fill_(1)
+            a.record(stream)
+            kc.kc_chi2_eval(P, T, V, S, out=out64, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        f_s = sum(a.elapsed_time(b) for a, b in f_ev) / 1e3
+        extras["fp64"] = {"value": evals * len(f_ev) / f_s, "unit": "planet-obs evals/s",
+                          "ms_per_step": 1e3 * f_s / len(f_ev)}
+
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
+    peak_tflops = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz * 1e6 / 1e12
+    flops = mixed_flops_per_eval(w.n_pl) * evals
+    achieved = flops / (t_sum / args.steps) / 1e12 / world
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": f"chi2_mixed_kernel<{w.n_pl}>",
+                "peak_basis": f"FP32 FMA pipe: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP "
+                              f"x {sm_mhz:.0f} MHz ({pk_kind} max SM clock)",
+                "flops_per_eval": mixed_flops_per_eval(w.n_pl)}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "planet-obs evals/s (chi2, npl=4, nobs=256) mixed vs FP64",
+        "value": value, "unit": "planet-obs evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+ds (mixed)",
+        "data": "synthetic",
+        "config": {"workload": w.shape.name, "n_sys": w.n_sys, "n_pl": w.n_pl,
+                   "n_obs": w.n_obs, "per_rank": True, "l2": "flushed between steps",
+                   "tile": {"threads_per_system": tile[0], "block": tile[1], "how": tile_kind}},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * kc.h -- C ABI of the GB300 batched Keplerian radial-velocity chi-square
+ * library (libkc.so).
+ *
+ * The library evaluates, for huge batches of multi-planet Keplerian models,
+ * the goodness of fit against one star's Doppler observations, as set out in
+ * Ford (2008), "Parallel Algorithm for Solving Kepler's Equation on Graphics
+ * Processing Units":
+ *
+ *   M_jk  = 2 pi frac((t_k - t0)/P_j) + M0_j              (Eqs. 4 and 6)
+ *   E_jk  - e_j sin E_jk = M_jk                            (Eq. 1, solved by
+ *                                                           Danby's quartic
+ *                                                           iteration, Eqs. 7-10)
+ *   v_jk  = K_j [cos(omega_j + f_jk) + e_j cos omega_j]    (Eq. 3)
+ *   V_k   = gamma + sum_j v_jk                             (Eq. 2)
+ *   chi2  = sum_k (V_k - v_k)^2 / (sigma_jit^2 + sigma_k^2) (Eq. 5)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Parameter layout.  One system is 5*n_pl + 1 doubles: (P, K, e, omega,
+ *    M0) for each planet in turn (the five per-planet parameters of
+ *    Sec. 4.1), then the systemic offset gamma.  Units: days, m/s, radians.
+ *    A batch is row-major [n_sys][5*n_pl + 1].
+ *  - Observations t, v_obs, sigma are [n_obs] doubles shared by every system
+ *    (Sec. 4.1: "constants to be used for evaluating all models").
+ *  - All array pointers are DEVICE pointers, owned by the caller, naturally
+ *    aligned for their type.  The library never frees or retains them.
+ *  - Every call is asynchronous on `stream` (NULL = the legacy default
+ *    stream).  Host-detectable errors (NULL pointers, sizes out of range)
+ *    return KC_ERR_ARG before anything is launched; a failed launch returns
+ *    KC_ERR_CUDA.  kc_last_error() gives a message for the calling thread.
+ *  - Physically invalid parameters (P <= 0, e outside [0, 1), non-finite
+ *    values) give NaN for that system; a non-positive variance gives NaN for
+ *    every system.  Nothing traps: every device loop has a fixed trip count.
+ *  - n_sys == 0 is a no-op.  n_obs == 0 gives chi2 = 0 (NaN if invalid).
+ *  - Calls are thread-safe; concurrent calls on different streams do not
+ *    share device memory.
+ */
+#ifndef KC_H
+#define KC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *kc_stream;
+
+typedef enum kc_status {
+    KC_OK = 0,
+    KC_ERR_ARG = 1,          /* bad pointer, size or mode                    */
+    KC_ERR_CUDA = 2,         /* a CUDA call or kernel launch failed          */
+    KC_ERR_NOMEM = 3,        /* a plan could not allocate its device memory  */
+    KC_ERR_UNSUPPORTED = 4   /* no sm_103a device / feature not available    */
+} kc_status;
+
+/* Arithmetic of the path (Sec. 5, "Mixed Precision Arithmetic"):
+ *  KC_FP64  - every step in double precision.
+ *  KC_MIXED - the phase frac((t-t0)/P) in pair-of-single (double-single)
+ *             arithmetic, Kepler's equation, the velocities and the residuals
+ *             in single precision, with compensated (Kahan) sums for the
+ *             planet velocities and for chi2 (Sec. 4.4). */
+typedef enum kc_mode { KC_FP64 = 0, KC_MIXED = 1 } kc_mode;
+
+#define KC_MAX_PLANETS 8        /* n_pl range: 1 .. KC_MAX_PLANETS           */
+#define KC_MAX_OBS (1 << 24)    /* n_obs range: 0 .. KC_MAX_OBS              */
+
+/* ------------------------------------------------------------- chi-square */
+
+/* FP64 chi2 of n_sys systems with epoch t0 = 0 and no jitter (the paper's
+ * setting, Eq. 4 with t=0 as epoch and sigma_j = 0 in Eq. 5).
+ *   params [n_sys][5*n_pl+1], t/v_obs/sigma [n_obs], out [n_sys] (double). */
+kc_status kc_chi2_eval(const double *params, const double *t,
+                       const double *v_obs, const double *sigma,
+                       int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                       double *out, kc_stream stream);
+
+/* Mixed-precision chi2 (KC_MIXED arithmetic), t0 = 0, no jitter.
+ *   out [n_sys] (float).  max_kepler_resid [n_sys] (float, may be NULL):
+ *   per system, max over its (planet, observation) pairs of
+ *   |E - e sin E - M| evaluated in single precision at the returned E. */
+kc_status kc_chi2_eval_mixed(const double *params, const double *t,
+                             const double *v_obs, const double *sigma,
+                             int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                             float *out, float *max_kepler_resid,
+                             kc_stream stream);
+
+/* General form: epoch t0 of M0 (Eq. 4) and jitter sigma_j (Eq. 5).
+ * out is double* for KC_FP64 and float* for KC_MIXED.  max_kepler_resid
+ * (float [n_sys], may be NULL) is filled in either mode.
+ * kc_chi2_eval(...) == kc_chi2_eval_ex(..., 0.0, 0.0, KC_FP64, out, NULL, s). */
+kc_status kc_chi2_eval_ex(const double *params, const double *t,
+                          const double *v_obs, const double *sigma,
+                          int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                          double t0, double jitter, kc_mode mode, void *out,
+                          float *max_kepler_resid, kc_stream stream);
+
+/* Gradient of chi2 with respect to all 5*n_pl+1 parameters of every system,
+ * by a hand-written adjoint (Sec. 6 suggests evaluating partial derivatives
+ * in parallel): E is recomputed, not stored, and Kepler's equation is
+ * differentiated implicitly, dE = (dM + sin E de)/(1 - e cos E);
+ * dM/dP = -2 pi (t - t0)/P^2 (jumps of frac() ignored).
+ *   chi2_out [n_sys] (may be NULL), grad_out [n_sys][5*n_pl+1]; both double
+ *   for KC_FP64 and float for KC_MIXED. */
+kc_status kc_chi2_grad(const double *params, const double *t,
+                       const double *v_obs, const double *sigma,
+                       int64_t n_sys, int32_t n_pl, int32_t n_obs, double t0,
+                       double jitter, kc_mode mode, void *chi2_out,
+                       void *grad_out, kc_stream stream);
+
+/* -------------------------------------------------------- model, Kepler */
+
+/* FP64 model velocities V(t_k) = gamma + sum_j v_j(t_k) (Eq. 2):
+ *   v_out [n_sys][n_obs] (double).  Used to synthesise observations and
+ *   for predictive distributions (Sec. 6). */
+kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys,
+                        int32_t n_pl, int32_t n_obs, double t0, double *v_out,
+                        kc_stream stream);
+
+/* Elementwise Kepler solve with the same device solver the chi2 kernels use
+ * (Sec. 4.3): E_out[i] with E - e sin E = M for M[i] in any range and
+ * 0 <= e[i] < 1.  KC_FP64: M, e, E_out are double.  KC_MIXED: float.
+ * E_out is reduced to the branch of M reduced to [-pi, pi]. */
+kc_status kc_kepler_solve(const void *M, const void *e, int64_t n,
+                          kc_mode mode, void *E_out, kc_stream stream);
+
+/* ------------------------------------------------------------ tiling */
+
+/* Launch shape of the uniform-batch kernels: each system is handled by
+ * threads_per_system consecutive threads (a power of two, 1..block; at most
+ * 32 for the gradient kernel), `block` threads per CTA (64..256, a multiple
+ * of 32 and of threads_per_system). */
+typedef struct kc_tile {
+    int32_t threads_per_system;
+    int32_t block;
+} kc_tile;
+
+typedef enum kc_kernel { KC_KERNEL_CHI2 = 0, KC_KERNEL_GRAD = 1 } kc_kernel;
+
+/* Tiles are looked up by (kernel, mode, n_pl, power-of-two bucket of n_sys,
+ * power-of-two bucket of n_obs) in a process-wide table; a missing entry
+ * uses a built-in heuristic.  kc_set_tile (tile == NULL removes the entry)
+ * and kc_get_tile (the tile that would be used) act on that table. */
+kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys,
+                      int32_t n_pl, int32_t n_obs, const kc_tile *tile);
+kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys,
+                      int32_t n_pl, int32_t n_obs, kc_tile *tile);
+
+/* Autotuner: times every admissible tile on the given problem (device
+ * arrays as for kc_chi2_eval_ex / kc_chi2_grad; t0 = 0, no jitter), stores
+ * the fastest in the table and returns it in *best (and its time in
+ * *best_ms, may be NULL).  Blocking: synchronises `stream`; must not be
+ * called while the stream is being captured.  Allocates and frees its own
+ * output buffers (stream-ordered). */
+kc_status kc_autotune(const double *params, const double *t,
+                      const double *v_obs, const double *sigma, int64_t n_sys,
+                      int32_t n_pl, int32_t n_obs, kc_kernel kernel,
+                      kc_mode mode, kc_tile *best, float *best_ms,
+                      kc_stream stream);
+
+/* --------------------------------------------------------------- misc */
+
+const char *kc_status_string(kc_status status);
+
+/* Detail of the calling thread's last non-OK status ("" if none). */
+const char *kc_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t kc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KC_H */

@@ -1,0 +1,259 @@
+"""GB300-native batched Keplerian radial-velocity chi-square (Ford 2008).
+
+Thin PyTorch binding over libkc.so: every function here marshals tensors to
+the C ABI of include/kc.h and calls it on the current CUDA stream; all
+arithmetic runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams only.
+
+Parameters of one system: (P, K, e, omega, M0) per planet, then gamma, so a
+batch is a float64 CUDA tensor [n_sys, 5*n_pl + 1].  Observations t, v_obs,
+sigma are float64 CUDA tensors [n_obs] shared by every system.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import torch
+
+from . import _lib
+from ._lib import KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
+
+__all__ = [
+    "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
+    "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
+    "kc_rv_predict", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
+    "chi2", "n_planets", "library_path",
+]
+
+library_path = _lib.LIB_PATH
+
+
+def _mode(mode) -> int:
+    if mode in (KC_FP64, "fp64", "f64", "double"):
+        return KC_FP64
+    if mode in (KC_MIXED, "mixed"):
+        return KC_MIXED
+    raise ValueError(f"unknown mode {mode!r}: use 'fp64' or 'mixed'")
+
+
+def _ptr(x: Optional[torch.Tensor]) -> Optional[int]:
+    return None if x is None else x.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+
+
+def _dev_f64(name: str, x: torch.Tensor, dim: int) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if x.dim() != dim:
+        raise ValueError(f"{name} must be {dim}-D")
+    return x.contiguous()
+
+
+def n_planets(params: torch.Tensor) -> int:
+    """n_pl from a [n_sys, 5*n_pl+1] parameter batch."""
+    n = params.shape[-1] - 1
+    if n <= 0 or n % 5:
+        raise ValueError("params must have 5*n_pl + 1 columns")
+    return n // 5
+
+
+def _obs(t, v_obs, sigma):
+    t = _dev_f64("t", t, 1)
+    v_obs = _dev_f64("v_obs", v_obs, 1)
+    sigma = _dev_f64("sigma", sigma, 1)
+    if not (t.numel() == v_obs.numel() == sigma.numel()):
+        raise ValueError("t, v_obs and sigma must have the same length")
+    return t, v_obs, sigma
+
+
+def kc_chi2_eval_ex(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
+                    mode="mixed", out: Optional[torch.Tensor] = None,
+                    max_kepler_resid=None, stream=None):
+    """chi2 of every system (include/kc.h: kc_chi2_eval_ex).
+
+    Returns ``out`` [n_sys] (float64 for 'fp64', float32 for 'mixed'); if
+    ``max_kepler_resid`` is True or a float32 tensor, returns (out, resid)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    n_sys, n_pl = params.shape[0], n_planets(params)
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    if out is None:
+        out = torch.empty(n_sys, dtype=dtype, device=params.device)
+    resid = None
+    if max_kepler_resid is True:
+        resid = torch.empty(n_sys, dtype=torch.float32, device=params.device)
+    elif isinstance(max_kepler_resid, torch.Tensor):
+        resid = max_kepler_resid
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_eval_ex(
+        params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), n_sys, n_pl,
+        t.numel(), float(t0), float(jitter), m, out.data_ptr(), _ptr(resid),
+        _stream(stream)), "kc_chi2_eval_ex")
+    return (out, resid) if resid is not None else out
+
+
+def kc_chi2_eval(params, t, v_obs, sigma, out=None, stream=None) -> torch.Tensor:
+    """FP64 chi2, t0 = 0, no jitter (include/kc.h: kc_chi2_eval)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    n_sys = params.shape[0]
+    if out is None:
+        out = torch.empty(n_sys, dtype=torch.float64, device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_eval(params.data_ptr(), t.data_ptr(), v_obs.data_ptr(),
+                                sigma.data_ptr(), n_sys, n_planets(params), t.numel(),
+                                out.data_ptr(), _stream(stream)), "kc_chi2_eval")
+    return out
+
+
+def kc_chi2_eval_mixed(params, t, v_obs, sigma, out=None, max_kepler_resid=None,
+                       stream=None):
+    """Mixed-precision chi2, t0 = 0, no jitter (kc_chi2_eval_mixed)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    n_sys = params.shape[0]
+    if out is None:
+        out = torch.empty(n_sys, dtype=torch.float32, device=params.device)
+    resid = None
+    if max_kepler_resid is True:
+        resid = torch.empty(n_sys, dtype=torch.float32, device=params.device)
+    elif isinstance(max_kepler_resid, torch.Tensor):
+        resid = max_kepler_resid
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_eval_mixed(
+        params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), n_sys,
+        n_planets(params), t.numel(), out.data_ptr(), _ptr(resid), _stream(stream)),
+        "kc_chi2_eval_mixed")
+    return (out, resid) if resid is not None else out
+
+
+def kc_chi2_grad(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
+                 mode="mixed", chi2_out=None, grad_out=None,
+                 stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(chi2 [n_sys], d chi2/d params [n_sys, 5*n_pl+1]) (kc_chi2_grad)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    n_sys = params.shape[0]
+    if chi2_out is None:
+        chi2_out = torch.empty(n_sys, dtype=dtype, device=params.device)
+    if grad_out is None:
+        grad_out = torch.empty(params.shape, dtype=dtype, device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_grad(
+        params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), n_sys,
+        n_planets(params), t.numel(), float(t0), float(jitter), m, chi2_out.data_ptr(),
+        grad_out.data_ptr(), _stream(stream)), "kc_chi2_grad")
+    return chi2_out, grad_out
+
+
+def kc_rv_predict(params, t, t0: float = 0.0, out=None, stream=None) -> torch.Tensor:
+    """FP64 model velocities [n_sys, n_obs] (kc_rv_predict)."""
+    params = _dev_f64("params", params, 2)
+    t = _dev_f64("t", t, 1)
+    n_sys = params.shape[0]
+    if out is None:
+        out = torch.empty((n_sys, t.numel()), dtype=torch.float64, device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_rv_predict(params.data_ptr(), t.data_ptr(), n_sys, n_planets(params),
+                                 t.numel(), float(t0), out.data_ptr(), _stream(stream)),
+               "kc_rv_predict")
+    return out
+
+
+def kc_kepler_solve(M, e, mode="fp64", out=None, stream=None) -> torch.Tensor:
+    """Elementwise E with E - e sin E = M (kc_kepler_solve)."""
+    m = _mode(mode)
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    for name, x in (("M", M), ("e", e)):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != dtype:
+            raise TypeError(f"{name} must be a {dtype} CUDA tensor")
+    M, e = M.contiguous(), e.contiguous()
+    if M.shape != e.shape:
+        raise ValueError("M and e must have the same shape")
+    if out is None:
+        out = torch.empty_like(M)
+    lib = _lib.load()
+    _lib.check(lib.kc_kepler_solve(M.data_ptr(), e.data_ptr(), M.numel(), m, out.data_ptr(),
+                                   _stream(stream)), "kc_kepler_solve")
+    return out
+
+
+def _kernel(kernel) -> int:
+    if kernel in (_lib.KC_KERNEL_CHI2, "chi2"):
+        return _lib.KC_KERNEL_CHI2
+    if kernel in (_lib.KC_KERNEL_GRAD, "grad"):
+        return _lib.KC_KERNEL_GRAD
+    raise ValueError(f"unknown kernel {kernel!r}: use 'chi2' or 'grad'")
+
+
+def kc_autotune(params, t, v_obs, sigma, kernel="chi2", mode="mixed", stream=None):
+    """Time every admissible tile on this problem, keep the fastest for
+    problems of its size class; returns ((threads_per_system, block), ms)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    best = _lib.KcTile()
+    ms = ctypes.c_float()
+    lib = _lib.load()
+    _lib.check(lib.kc_autotune(params.data_ptr(), t.data_ptr(), v_obs.data_ptr(),
+                               sigma.data_ptr(), params.shape[0], n_planets(params), t.numel(),
+                               _kernel(kernel), _mode(mode), ctypes.byref(best),
+                               ctypes.byref(ms), _stream(stream)), "kc_autotune")
+    return (best.threads_per_system, best.block), ms.value
+
+
+def kc_set_tile(kernel, mode, n_sys: int, n_pl: int, n_obs: int, tile=None) -> None:
+    """Pin (threads_per_system, block) for a size class; None restores the default."""
+    lib = _lib.load()
+    ptr = None
+    if tile is not None:
+        ptr = ctypes.byref(_lib.KcTile(int(tile[0]), int(tile[1])))
+    _lib.check(lib.kc_set_tile(_kernel(kernel), _mode(mode), n_sys, n_pl, n_obs, ptr),
+               "kc_set_tile")
+
+
+def kc_get_tile(kernel, mode, n_sys: int, n_pl: int, n_obs: int):
+    """(threads_per_system, block) the library would launch for this problem."""
+    lib = _lib.load()
+    t = _lib.KcTile()
+    _lib.check(lib.kc_get_tile(_kernel(kernel), _mode(mode), n_sys, n_pl, n_obs,
+                               ctypes.byref(t)), "kc_get_tile")
+    return t.threads_per_system, t.block
+
+
+class _Chi2Fn(torch.autograd.Function):
+    """chi2 with the adjoint kernel as backward."""
+
+    @staticmethod
+    def forward(ctx, params, t, v_obs, sigma, t0, jitter, mode):
+        chi, grad = kc_chi2_grad(params, t, v_obs, sigma, t0, jitter, mode)
+        ctx.save_for_backward(grad)
+        return chi
+
+    @staticmethod
+    def backward(ctx, grad_chi2):
+        (grad,) = ctx.saved_tensors
+        g = grad.to(torch.float64) * grad_chi2.to(torch.float64)[:, None]
+        return g, None, None, None, None, None, None
+
+
+def chi2(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
+         mode="mixed") -> torch.Tensor:
+    """Differentiable chi2 [n_sys] with respect to ``params``.
+
+    Without grad, the forward kernel (kc_chi2_eval_ex) runs; with grad the
+    adjoint kernel (kc_chi2_grad) produces chi2 and its gradient in one pass
+    and backward scales it by the incoming gradient."""
+    if params.requires_grad and torch.is_grad_enabled():
+        return _Chi2Fn.apply(params, t, v_obs, sigma, float(t0), float(jitter), mode)
+    return kc_chi2_eval_ex(params, t, v_obs, sigma, t0, jitter, mode)

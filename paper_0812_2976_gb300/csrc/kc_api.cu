@@ -1,0 +1,381 @@
+// kc_api.cu -- the library's C ABI (include/kc.h): argument checks, launch
+// shapes and error reporting around the kernels of kc_fwd.cu / kc_grad.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kc_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+kc_status fail(kc_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+
+kc_status fail(kc_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+kc_status ok() {
+  g_last_error.clear();
+  return KC_OK;
+}
+
+kc_status cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return ok();
+  return fail(KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+kc_status check_uniform(const double *params, const double *t, const double *v,
+                        const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                        const void *out, const char *fn) {
+  if (n_sys < 0) return fail(KC_ERR_ARG, "%s: n_sys < 0", fn);
+  if (n_pl < 1 || n_pl > KC_MAX_PLANETS)
+    return fail(KC_ERR_ARG, "%s: n_pl = %d outside 1..%d", fn, n_pl, KC_MAX_PLANETS);
+  if (n_obs < 0 || n_obs > KC_MAX_OBS)
+    return fail(KC_ERR_ARG, "%s: n_obs = %d outside 0..%d", fn, n_obs, KC_MAX_OBS);
+  if (n_sys > (int64_t(1) << 40)) return fail(KC_ERR_ARG, "%s: n_sys too large", fn);
+  if (n_sys > 0) {
+    if (!params) return fail(KC_ERR_ARG, "%s: params is NULL", fn);
+    if (!out) return fail(KC_ERR_ARG, "%s: output is NULL", fn);
+    if (n_obs > 0 && (!t || !v || !sigma))
+      return fail(KC_ERR_ARG, "%s: t, v_obs or sigma is NULL", fn);
+  }
+  const uintptr_t mis = (uintptr_t)params | (uintptr_t)t | (uintptr_t)v | (uintptr_t)sigma;
+  if (mis & 7) return fail(KC_ERR_ARG, "%s: input not 8-byte aligned", fn);
+  return KC_OK;
+}
+
+}  // namespace
+
+namespace kc {
+
+int obs_tile_for(Kind kind, int n_obs) {
+  const bool f64 = kind == Kind::Chi2F64 || kind == Kind::GradF64;
+  const int cap = f64 ? 2048 : 4096;
+  return n_obs < cap ? (n_obs > 0 ? n_obs : 1) : cap;
+}
+
+// Built-in launch shape.  G threads share one system; enough threads to fill
+// the 152 SMs a few times over, but each thread keeps at least four
+// observations so the per-system combine stays cheap.
+Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
+  const bool grad = kind == Kind::GradF64 || kind == Kind::GradMixed;
+  Tile t;
+  t.block = 256;
+  const int64_t want_threads = int64_t(152) * 2048 * 2;
+  int G = 1;
+  while (G < 256 && n_sys * G < want_threads) G <<= 1;
+  const int max_g_obs = n_obs >= 4 ? n_obs / 4 : 1;
+  while (G > 1 && G > max_g_obs) G >>= 1;
+  if (grad && G > 32) G = 32;
+  if (G < 4) G = 4;
+  t.G = G;
+  t.obs_tile = obs_tile_for(kind, n_obs);
+  (void)n_pl;
+  return t;
+}
+
+namespace {
+
+int bucket(int64_t x) {
+  int b = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+struct TileKey {
+  int kind, n_pl, sys_b, obs_b;
+  bool operator<(const TileKey &o) const {
+    return std::tie(kind, n_pl, sys_b, obs_b) < std::tie(o.kind, o.n_pl, o.sys_b, o.obs_b);
+  }
+};
+
+std::mutex g_tile_mu;
+std::map<TileKey, Tile> g_tiles;
+
+TileKey key_of(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
+  return TileKey{(int)kind, n_pl, bucket(n_sys), bucket(n_obs)};
+}
+
+}  // namespace
+
+Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tiles.find(key_of(kind, n_sys, n_pl, n_obs));
+    if (it != g_tiles.end()) {
+      Tile t = it->second;
+      t.obs_tile = obs_tile_for(kind, n_obs);
+      return t;
+    }
+  }
+  return default_tile(kind, n_sys, n_pl, n_obs);
+}
+
+}  // namespace kc
+
+using kc::Kind;
+using kc::Tile;
+using kc::UniformArgs;
+
+extern "C" {
+
+const char *kc_status_string(kc_status s) {
+  switch (s) {
+    case KC_OK: return "ok";
+    case KC_ERR_ARG: return "invalid argument";
+    case KC_ERR_CUDA: return "CUDA error";
+    case KC_ERR_NOMEM: return "out of device memory";
+    case KC_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *kc_last_error(void) { return g_last_error.c_str(); }
+
+int32_t kc_version(void) { return 100; }
+
+kc_status kc_chi2_eval_ex(const double *params, const double *t, const double *v_obs,
+                          const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                          double t0, double jitter, kc_mode mode, void *out,
+                          float *max_kepler_resid, kc_stream stream) {
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, out,
+                               "kc_chi2_eval_ex");
+  if (st != KC_OK) return st;
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_chi2_eval_ex: bad mode");
+  if (!std::isfinite(t0) || !std::isfinite(jitter))
+    return fail(KC_ERR_ARG, "kc_chi2_eval_ex: t0 and jitter must be finite");
+  if (n_sys == 0) return ok();
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == KC_FP64) {
+    const Tile tile = kc::choose_tile(Kind::Chi2F64, n_sys, n_pl, n_obs);
+    return cuda_status(kc::launch_chi2_f64(a, tile, static_cast<double *>(out),
+                                           max_kepler_resid, s),
+                       "kc_chi2_eval_ex (fp64)");
+  }
+  const Tile tile = kc::choose_tile(Kind::Chi2Mixed, n_sys, n_pl, n_obs);
+  return cuda_status(kc::launch_chi2_mixed(a, tile, static_cast<float *>(out),
+                                           max_kepler_resid, s),
+                     "kc_chi2_eval_ex (mixed)");
+}
+
+kc_status kc_chi2_eval(const double *params, const double *t, const double *v_obs,
+                       const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                       double *out, kc_stream stream) {
+  return kc_chi2_eval_ex(params, t, v_obs, sigma, n_sys, n_pl, n_obs, 0.0, 0.0, KC_FP64, out,
+                         nullptr, stream);
+}
+
+kc_status kc_chi2_eval_mixed(const double *params, const double *t, const double *v_obs,
+                             const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                             float *out, float *max_kepler_resid, kc_stream stream) {
+  return kc_chi2_eval_ex(params, t, v_obs, sigma, n_sys, n_pl, n_obs, 0.0, 0.0, KC_MIXED, out,
+                         max_kepler_resid, stream);
+}
+
+kc_status kc_chi2_grad(const double *params, const double *t, const double *v_obs,
+                       const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                       double t0, double jitter, kc_mode mode, void *chi2_out, void *grad_out,
+                       kc_stream stream) {
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, grad_out,
+                               "kc_chi2_grad");
+  if (st != KC_OK) return st;
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_chi2_grad: bad mode");
+  if (!std::isfinite(t0) || !std::isfinite(jitter))
+    return fail(KC_ERR_ARG, "kc_chi2_grad: t0 and jitter must be finite");
+  if (n_sys == 0) return ok();
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == KC_FP64) {
+    const Tile tile = kc::choose_tile(Kind::GradF64, n_sys, n_pl, n_obs);
+    return cuda_status(kc::launch_grad_f64(a, tile, static_cast<double *>(chi2_out),
+                                           static_cast<double *>(grad_out), s),
+                       "kc_chi2_grad (fp64)");
+  }
+  const Tile tile = kc::choose_tile(Kind::GradMixed, n_sys, n_pl, n_obs);
+  return cuda_status(kc::launch_grad_mixed(a, tile, static_cast<float *>(chi2_out),
+                                           static_cast<float *>(grad_out), s),
+                     "kc_chi2_grad (mixed)");
+}
+
+kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys, int32_t n_pl,
+                        int32_t n_obs, double t0, double *v_out, kc_stream stream) {
+  if (n_sys < 0 || n_obs < 0 || n_obs > KC_MAX_OBS)
+    return fail(KC_ERR_ARG, "kc_rv_predict: bad sizes");
+  if (n_pl < 1 || n_pl > KC_MAX_PLANETS) return fail(KC_ERR_ARG, "kc_rv_predict: bad n_pl");
+  if (n_sys == 0 || n_obs == 0) return ok();
+  if (!params || !t || !v_out) return fail(KC_ERR_ARG, "kc_rv_predict: NULL pointer");
+  if (((uintptr_t)params | (uintptr_t)t | (uintptr_t)v_out) & 7)
+    return fail(KC_ERR_ARG, "kc_rv_predict: pointer not 8-byte aligned");
+  if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_rv_predict: t0 must be finite");
+  return cuda_status(kc::launch_rv_predict(params, t, n_sys, n_pl, n_obs, t0, v_out,
+                                           reinterpret_cast<cudaStream_t>(stream)),
+                     "kc_rv_predict");
+}
+
+kc_status kc_kepler_solve(const void *M, const void *e, int64_t n, kc_mode mode, void *E_out,
+                          kc_stream stream) {
+  if (n < 0) return fail(KC_ERR_ARG, "kc_kepler_solve: n < 0");
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_kepler_solve: bad mode");
+  if (n == 0) return ok();
+  if (!M || !e || !E_out) return fail(KC_ERR_ARG, "kc_kepler_solve: NULL pointer");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == KC_FP64)
+    return cuda_status(kc::launch_kepler_f64(static_cast<const double *>(M),
+                                             static_cast<const double *>(e), n,
+                                             static_cast<double *>(E_out), s),
+                       "kc_kepler_solve (fp64)");
+  return cuda_status(kc::launch_kepler_f32(static_cast<const float *>(M),
+                                           static_cast<const float *>(e), n,
+                                           static_cast<float *>(E_out), s),
+                     "kc_kepler_solve (mixed)");
+}
+
+namespace {
+
+kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
+  if (kernel == KC_KERNEL_CHI2) return mode == KC_FP64 ? kc::Kind::Chi2F64 : kc::Kind::Chi2Mixed;
+  return mode == KC_FP64 ? kc::Kind::GradF64 : kc::Kind::GradMixed;
+}
+
+bool tile_ok(kc_kernel kernel, const kc_tile &t) {
+  const int G = t.threads_per_system, B = t.block;
+  if (B < 64 || B > 256 || (B & 31)) return false;
+  if (G < 1 || G > B || (G & (G - 1)) || (B % G)) return false;
+  if (kernel == KC_KERNEL_GRAD && G > 32) return false;
+  return true;
+}
+
+}  // namespace
+
+kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                      const kc_tile *tile) {
+  if ((kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
+      (mode != KC_FP64 && mode != KC_MIXED) || n_sys < 0 || n_obs < 0 || n_pl < 1 ||
+      n_pl > KC_MAX_PLANETS)
+    return fail(KC_ERR_ARG, "kc_set_tile: bad kernel, mode or sizes");
+  const kc::TileKey key = kc::key_of(kind_of(kernel, mode), n_sys, n_pl, n_obs);
+  std::lock_guard<std::mutex> lk(kc::g_tile_mu);
+  if (!tile) {
+    kc::g_tiles.erase(key);
+    return ok();
+  }
+  if (!tile_ok(kernel, *tile)) return fail(KC_ERR_ARG, "kc_set_tile: inadmissible tile");
+  kc::g_tiles[key] = Tile{tile->threads_per_system, tile->block, 0};
+  return ok();
+}
+
+kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                      kc_tile *tile) {
+  if (!tile || (kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
+      (mode != KC_FP64 && mode != KC_MIXED) || n_sys < 0 || n_obs < 0 || n_pl < 1 ||
+      n_pl > KC_MAX_PLANETS)
+    return fail(KC_ERR_ARG, "kc_get_tile: bad arguments");
+  const Tile t = kc::choose_tile(kind_of(kernel, mode), n_sys, n_pl, n_obs);
+  tile->threads_per_system = t.G;
+  tile->block = t.block;
+  return ok();
+}
+
+kc_status kc_autotune(const double *params, const double *t, const double *v_obs,
+                      const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                      kc_kernel kernel, kc_mode mode, kc_tile *best, float *best_ms,
+                      kc_stream stream) {
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, params,
+                               "kc_autotune");
+  if (st != KC_OK) return st;
+  if ((kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
+      (mode != KC_FP64 && mode != KC_MIXED))
+    return fail(KC_ERR_ARG, "kc_autotune: bad kernel or mode");
+  if (n_sys == 0) return fail(KC_ERR_ARG, "kc_autotune: empty problem");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const kc::Kind kind = kind_of(kernel, mode);
+  const size_t elem = mode == KC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t npar = 5 * (size_t)n_pl + 1;
+  void *chi = nullptr, *grad = nullptr;
+  cudaError_t e = cudaMallocAsync(&chi, elem * n_sys, s);
+  if (e == cudaSuccess && kernel == KC_KERNEL_GRAD) e = cudaMallocAsync(&grad, elem * n_sys * npar, s);
+  if (e != cudaSuccess) {
+    if (chi) cudaFreeAsync(chi, s);
+    return fail(KC_ERR_NOMEM, "kc_autotune: cannot allocate timing buffers: %s",
+                cudaGetErrorString(e));
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, 0.0, 0.0};
+  auto launch = [&](const Tile &tile) -> cudaError_t {
+    switch (kind) {
+      case kc::Kind::Chi2F64: return kc::launch_chi2_f64(a, tile, (double *)chi, nullptr, s);
+      case kc::Kind::Chi2Mixed: return kc::launch_chi2_mixed(a, tile, (float *)chi, nullptr, s);
+      case kc::Kind::GradF64: return kc::launch_grad_f64(a, tile, (double *)chi, (double *)grad, s);
+      case kc::Kind::GradMixed:
+        return kc::launch_grad_mixed(a, tile, (float *)chi, (float *)grad, s);
+    }
+    return cudaErrorInvalidValue;
+  };
+  float best_t = 1e30f;
+  Tile best_tile = kc::default_tile(kind, n_sys, n_pl, n_obs);
+  cudaError_t err = cudaSuccess;
+  for (int B : {128, 256}) {
+    for (int G = 1; G <= B; G <<= 1) {
+      const kc_tile cand{G, B};
+      if (!tile_ok(kernel, cand)) continue;
+      if (n_obs > 0 && G > n_obs) continue;
+      Tile tile{G, B, kc::obs_tile_for(kind, n_obs)};
+      err = launch(tile);                       // warm-up (and smem attribute)
+      if (err != cudaSuccess) break;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        err = launch(tile);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tmin = ms < tmin ? ms : tmin;
+      }
+      if (err != cudaSuccess) break;
+      if (tmin < best_t) {
+        best_t = tmin;
+        best_tile = tile;
+      }
+    }
+    if (err != cudaSuccess) break;
+  }
+  cudaFreeAsync(chi, s);
+  if (grad) cudaFreeAsync(grad, s);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_status(err, "kc_autotune");
+  {
+    std::lock_guard<std::mutex> lk(kc::g_tile_mu);
+    kc::g_tiles[kc::key_of(kind, n_sys, n_pl, n_obs)] = best_tile;
+  }
+  if (best) {
+    best->threads_per_system = best_tile.G;
+    best->block = best_tile.block;
+  }
+  if (best_ms) *best_ms = best_t;
+  return ok();
+}
+
+}  // extern "C"

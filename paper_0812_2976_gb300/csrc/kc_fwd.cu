@@ -1,0 +1,425 @@
+// kc_fwd.cu -- fused chi-square kernels (mean anomaly -> Kepler -> velocity
+// -> residual -> reduction in one pass), model prediction and the
+// elementwise Kepler solver.
+//
+// The paper evaluates chi2 either with four kernels that write M, E and the
+// planet velocities to device memory, or with M and E kernels followed by a
+// fused velocity+chi2 kernel (Sec. 4.4, Table 1).  Here the whole chain runs
+// in registers: only the parameters are read from HBM and one value per
+// system is written back.
+//
+// Work layout: each system is handled by G consecutive threads of a CTA; the
+// thread with index c in its group takes observations k = c, c+G, c+2G, ...
+// The observations (shared by every system, Sec. 4.1) are staged once per
+// CTA in shared memory (Sec. 5, "Device Memory Caching": cooperative load)
+// and the per-planet constants are computed once per (system, planet) in
+// FP64 and kept in shared memory.  Partial chi2 of the G threads are
+// combined with warp shuffles (and shared memory when G > 32).
+#include <cmath>
+
+#include "kc_device.cuh"
+#include "kc_internal.h"
+
+namespace kc {
+
+namespace {
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct MixedLayout {
+  size_t pl, gam, red, obs, w, total;
+  __host__ __device__ MixedLayout(int ST, int J, int nwarps, int obs_tile) {
+    pl = 0;
+    gam = pl + sizeof(PlanetF) * ST * J;
+    red = align_up(gam + sizeof(float) * ST, 16);
+    obs = align_up(red + sizeof(float) * 3 * nwarps, 16);
+    w = obs + sizeof(float4) * obs_tile;
+    total = align_up(w + sizeof(float) * obs_tile, 16);
+  }
+};
+
+struct ObsD {
+  double tau, v, w, pad;
+};
+
+struct F64Layout {
+  size_t pl, gam, red, obs, total;
+  __host__ __device__ F64Layout(int ST, int J, int nwarps, int obs_tile) {
+    pl = 0;
+    gam = pl + sizeof(PlanetD) * ST * J;
+    red = align_up(gam + sizeof(double) * ST, 16);
+    obs = align_up(red + sizeof(double) * 2 * nwarps, 16);
+    total = align_up(obs + sizeof(ObsD) * obs_tile, 16);
+  }
+};
+
+// gamma of system s, or NaN when any parameter of the system is invalid.
+__device__ inline double system_gamma(const double *p, int J) {
+  bool ok = isfinite(p[5 * J]);
+  for (int j = 0; j < J; ++j)
+    ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
+  return ok ? p[5 * J] : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// Inverse variance 1/(sigma_k^2 + sigma_jit^2) (Eq. 5); NaN if not positive.
+__device__ inline double inv_variance(double sigma, double jitter2) {
+  const double var = fma(sigma, sigma, jitter2);
+  return (var > 0.0) ? 1.0 / var : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// ------------------------------------------------------------ mixed
+
+// Thread that handles setup item i: items are dealt round-robin over the
+// warps so that the double-precision setup runs on every SM sub-partition.
+__device__ inline int setup_slot(int tid, int nwarps) { return (tid & 31) * nwarps + (tid >> 5); }
+
+template <int J>
+__global__ void __launch_bounds__(256, 2)
+chi2_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ out,
+                  float *__restrict__ resid_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int block = blockDim.x;
+  const int nwarps = block >> 5;
+  const int ST = block / G;
+  const MixedLayout L(ST, J, nwarps, obs_tile);
+  PlanetF *pl_s = reinterpret_cast<PlanetF *>(smem + L.pl);
+  float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float *red_s = reinterpret_cast<float *>(smem + L.red);
+  float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
+  float *w_s = reinterpret_cast<float *>(smem + L.w);
+
+  const int tid = threadIdx.x;
+  const int64_t sys0 = (int64_t)blockIdx.x * ST;
+  const int npar = 5 * J + 1;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+  const float jit2 = d2f(a.jitter2);
+
+  // per-(system, planet) constants, once, in FP64 (Eqs. 4/6 phase offset)
+  for (int i = setup_slot(tid, nwarps); i < ST * J; i += block) {
+    const int sl = i / J, j = i - sl * J;
+    const int64_t s = sys0 + sl;
+    PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, dref);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < ST; i += block) {
+    const int64_t s = sys0 + i;
+    gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
+  }
+
+  const int sl = tid / G, c = tid - sl * G;
+  const int64_t s = sys0 + sl;
+  const bool want_resid = resid_out != nullptr;
+  Kahan acc = {0.0f, 0.0f};
+  float rmax = 0.0f;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
+    const int nk = min(obs_tile, a.n_obs - k0);
+    __syncthreads();
+    // stage: tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jit^2)
+    for (int k = tid; k < nk; k += block) {
+      float th, tl, vh, vl;
+      split_d(a.t[k0 + k] - t_ref, th, tl);
+      split_d(a.v[k0 + k], vh, vl);
+      obs_s[k] = make_float4(th, tl, vh, vl);
+      const float sg = d2f(a.sigma[k0 + k]);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      w_s[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+    }
+    __syncthreads();
+    const float gam = gam_s[sl];
+    PlanetF q[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) q[j] = pl_s[sl * J + j];
+    for (int k = c; k < nk; k += G) {
+      const float4 o = obs_s[k];
+      const float wk = w_s[k];
+      Kahan V = {0.0f, 0.0f};
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const float M = mean_anomaly_mixed(o.x, o.y, q[j]);
+        float sE, cE;
+        const float E = kepler_f32(M, q[j].e, sE, cE);
+        if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
+        kahan_add(V, velocity_mixed(q[j], sE, cE));
+      }
+      // residual V - v_obs with the model and the observation as float pairs
+      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+      kahan_add(acc, wk * r * r);
+    }
+  }
+
+  // combine the G partial sums of each system
+  const int gw = G < 32 ? G : 32;
+  for (int m = gw >> 1; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+    rmax = fmaxf(rmax, shfl_xor(rmax, m));
+  }
+  if (G > 32) {
+    const int warp = tid >> 5, lane = tid & 31;
+    __syncthreads();
+    if (lane == 0) {
+      red_s[3 * warp] = acc.big;
+      red_s[3 * warp + 1] = acc.small;
+      red_s[3 * warp + 2] = rmax;
+    }
+    __syncthreads();
+    if (c == 0) {
+      for (int w = warp + 1; w < warp + G / 32; ++w) {
+        Kahan o = {red_s[3 * w], red_s[3 * w + 1]};
+        kahan_merge(acc, o);
+        rmax = fmaxf(rmax, red_s[3 * w + 2]);
+      }
+    }
+  }
+  if (c == 0 && s < a.n_sys) {
+    // 0 * gamma turns an invalid system into NaN even when n_obs == 0
+    out[s] = kahan_value(acc) + 0.0f * gam_s[sl];
+    if (resid_out) resid_out[s] = rmax;
+  }
+}
+
+// ------------------------------------------------------------ FP64
+
+template <int J>
+__global__ void __launch_bounds__(256, 2)
+chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
+                float *__restrict__ resid_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int block = blockDim.x;
+  const int ST = block / G;
+  const F64Layout L(ST, J, block / 32, obs_tile);
+  PlanetD *pl_s = reinterpret_cast<PlanetD *>(smem + L.pl);
+  double *gam_s = reinterpret_cast<double *>(smem + L.gam);
+  double *red_s = reinterpret_cast<double *>(smem + L.red);
+  ObsD *obs_s = reinterpret_cast<ObsD *>(smem + L.obs);
+
+  const int tid = threadIdx.x;
+  const int64_t sys0 = (int64_t)blockIdx.x * ST;
+  const int npar = 5 * J + 1;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+
+  for (int i = setup_slot(tid, block >> 5); i < ST * J; i += block) {
+    const int sl = i / J, j = i - sl * J;
+    const int64_t s = sys0 + sl;
+    PlanetD q = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (s < a.n_sys) q = planet_setup_f64(a.params + s * npar + 5 * j, dref);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < ST; i += block) {
+    const int64_t s = sys0 + i;
+    gam_s[i] = s < a.n_sys ? system_gamma(a.params + s * npar, J) : 0.0;
+  }
+
+  const int sl = tid / G, c = tid - sl * G;
+  const int64_t s = sys0 + sl;
+  double acc = 0.0, rmax = 0.0;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
+    const int nk = min(obs_tile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += block) {
+      ObsD o;
+      o.tau = a.t[k0 + k] - t_ref;
+      o.v = a.v[k0 + k];
+      o.w = inv_variance(a.sigma[k0 + k], a.jitter2);
+      o.pad = 0.0;
+      obs_s[k] = o;
+    }
+    __syncthreads();
+    const double gam = gam_s[sl];
+    const PlanetD *q = pl_s + sl * J;
+    for (int k = c; k < nk; k += G) {
+      const ObsD o = obs_s[k];
+      double V = gam;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const PlanetD p = q[j];
+        const double M = mean_anomaly_f64(o.tau, p);
+        double sE, cE;
+        const double E = kepler_f64(M, p.e, sE, cE);
+        rmax = fmax(rmax, fabs((E - M) - p.e * sE));
+        V += velocity_f64(p, sE, cE);
+      }
+      const double r = V - o.v;
+      acc = fma(o.w * r, r, acc);
+    }
+  }
+
+  const int gw = G < 32 ? G : 32;
+  for (int m = gw >> 1; m >= 1; m >>= 1) {
+    acc += shfl_xor(acc, m);
+    rmax = fmax(rmax, shfl_xor(rmax, m));
+  }
+  if (G > 32) {
+    const int warp = tid >> 5, lane = tid & 31;
+    __syncthreads();
+    if (lane == 0) {
+      red_s[2 * warp] = acc;
+      red_s[2 * warp + 1] = rmax;
+    }
+    __syncthreads();
+    if (c == 0) {
+      for (int w = warp + 1; w < warp + G / 32; ++w) {
+        acc += red_s[2 * w];
+        rmax = fmax(rmax, red_s[2 * w + 1]);
+      }
+    }
+  }
+  if (c == 0 && s < a.n_sys) {
+    out[s] = acc + 0.0 * gam_s[sl];
+    if (resid_out) resid_out[s] = (float)rmax;
+  }
+}
+
+// ------------------------------------------------------------ prediction
+
+// V(t_k) = gamma + sum_j v_j(t_k) in FP64, one thread per (system, obs).
+__global__ void rv_predict_kernel(const double *__restrict__ params, const double *__restrict__ t,
+                                  int64_t n_sys, int J, int n_obs, double t0,
+                                  double *__restrict__ v_out) {
+  const int64_t total = n_sys * (int64_t)n_obs;
+  const int npar = 5 * J + 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / n_obs;
+    const int k = (int)(i - s * n_obs);
+    const double *p = params + s * npar;
+    const double t_ref = t[0];
+    double V = system_gamma(p, J);
+    for (int j = 0; j < J; ++j) {
+      const PlanetD q = planet_setup_f64(p + 5 * j, t_ref - t0);
+      const double M = mean_anomaly_f64(t[k] - t_ref, q);
+      double sE, cE;
+      kepler_f64(M, q.e, sE, cE);
+      V += velocity_f64(q, sE, cE);
+    }
+    v_out[i] = V;
+  }
+}
+
+// ------------------------------------------------------------ Kepler only
+
+template <typename T>
+__device__ inline T reduce_pi(T M);
+template <>
+__device__ inline double reduce_pi<double>(double M) {
+  return M - kTwoPi * rint(M * kInvTwoPi);
+}
+template <>
+__device__ inline float reduce_pi<float>(float M) {
+  // reduce in double so that large |M| keeps its phase
+  const double m = (double)M;
+  return (float)(m - kTwoPi * rint(m * kInvTwoPi));
+}
+
+__global__ void kepler_f64_kernel(const double *__restrict__ M, const double *__restrict__ e,
+                                  int64_t n, double *__restrict__ E) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    E[i] = kepler_f64(reduce_pi(M[i]), e[i], s, c);
+  }
+}
+
+__global__ void kepler_f32_kernel(const float *__restrict__ M, const float *__restrict__ e,
+                                  int64_t n, float *__restrict__ E) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s, c;
+    E[i] = kepler_f32(reduce_pi(M[i]), e[i], s, c);
+  }
+}
+
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int grid_for(int64_t n_sys, int ST) { return (int)((n_sys + ST - 1) / ST); }
+
+int elementwise_grid(int64_t n) {
+  const int64_t blocks = (n + 255) / 256;
+  return (int)(blocks < 152 * 32 ? (blocks > 0 ? blocks : 1) : 152 * 32);
+}
+
+}  // namespace
+
+size_t smem_chi2_mixed(int n_pl, const Tile &t) {
+  return MixedLayout(t.block / t.G, n_pl, t.block / 32, t.obs_tile).total;
+}
+
+size_t smem_chi2_f64(int n_pl, const Tile &t) {
+  return F64Layout(t.block / t.G, n_pl, t.block / 32, t.obs_tile).total;
+}
+
+#define KC_DISPATCH_J(J, MACRO) \
+  switch (J) {                  \
+    case 1: MACRO(1); break;    \
+    case 2: MACRO(2); break;    \
+    case 3: MACRO(3); break;    \
+    case 4: MACRO(4); break;    \
+    case 5: MACRO(5); break;    \
+    case 6: MACRO(6); break;    \
+    case 7: MACRO(7); break;    \
+    case 8: MACRO(8); break;    \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out, float *resid,
+                              cudaStream_t st) {
+  const size_t smem = smem_chi2_mixed(a.n_pl, tile);
+  const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                  \
+  err = set_smem(chi2_mixed_kernel<JJ>, smem);                                         \
+  if (err == cudaSuccess)                                                              \
+    chi2_mixed_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
+                                                          resid);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out, float *resid,
+                            cudaStream_t st) {
+  const size_t smem = smem_chi2_f64(a.n_pl, tile);
+  const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                \
+  err = set_smem(chi2_f64_kernel<JJ>, smem);                                         \
+  if (err == cudaSuccess)                                                            \
+    chi2_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
+                                                        resid);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rv_predict(const double *params, const double *t, int64_t n_sys, int n_pl,
+                              int n_obs, double t0, double *v_out, cudaStream_t st) {
+  const int64_t total = n_sys * (int64_t)n_obs;
+  rv_predict_kernel<<<elementwise_grid(total), 256, 0, st>>>(params, t, n_sys, n_pl, n_obs, t0,
+                                                             v_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kepler_f64(const double *M, const double *e, int64_t n, double *E,
+                              cudaStream_t st) {
+  kepler_f64_kernel<<<elementwise_grid(n), 256, 0, st>>>(M, e, n, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kepler_f32(const float *M, const float *e, int64_t n, float *E,
+                              cudaStream_t st) {
+  kepler_f32_kernel<<<elementwise_grid(n), 256, 0, st>>>(M, e, n, E);
+  return cudaGetLastError();
+}
+
+}  // namespace kc

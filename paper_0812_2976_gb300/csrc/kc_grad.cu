@@ -1,0 +1,399 @@
+// kc_grad.cu -- adjoint of the fused chi-square: d chi2 / d(P, K, e, w, M0)
+// for every planet and d chi2 / d gamma, for every system.
+//
+// Sec. 6 of the paper proposes evaluating partial derivatives of the
+// goodness-of-fit statistic in parallel for derivative-based searches.  This
+// kernel does it in the same pass as chi2, without storing anything per
+// observation: per (observation, planet) it solves Kepler's equation (the
+// same fixed-count Danby solver as the forward kernel), keeps sin E and cos E
+// in registers until the residual r_k of the observation is known, then adds
+// 2 w_k r_k dv/dtheta to per-thread accumulators.  The derivatives follow
+// from implicit differentiation of Kepler's equation,
+//   dE = (dM + sin E de)/D,  D = 1 - e cos E,
+// and of the true anomaly, df/dE = beta/D, df/de|E = sin E/(beta D) with
+// beta = sqrt(1 - e^2):
+//   dv/dK  = cos(w+f) + e cos w
+//   dv/dw  = -K [sin(w+f) + e sin w]
+//   dv/dM0 = -K sin(w+f) beta / D^2
+//   dv/de  = K cos w - K sin(w+f) (sin E / D) (1/beta + beta/D)
+//   dv/dP  = dv/dM0 * (-2 pi (t - t0) / P^2)     (frac() jumps ignored)
+//   dV/dgamma = 1.
+// Each system is handled by G <= 32 consecutive threads (one warp segment),
+// combined by shuffles.
+#include <cmath>
+
+#include "kc_device.cuh"
+#include "kc_internal.h"
+
+namespace kc {
+
+namespace {
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Planet constants for the gradient, single precision.
+struct GradPlanetF {
+  PlanetF base;    // phase and velocity constants of the forward path
+  float K, cw, sw, beta, n2;   // n2 = (1/P)^2
+};
+
+struct GradPlanetD {
+  PlanetD base;
+  double K, cw, sw, n2;
+};
+
+__device__ inline GradPlanetF grad_setup_mixed(const double *p, double dref) {
+  GradPlanetF g;
+  g.base = planet_setup_mixed(p, dref);
+  float w_hi, w_lo;
+  split_d(p[3], w_hi, w_lo);
+  float sw, cw;
+  sincosf(w_hi, &sw, &cw);
+  g.sw = __fmaf_rn(w_lo, cw, sw);
+  g.cw = __fmaf_rn(-w_lo, sw, cw);
+  g.K = d2f(p[1]);
+  const float e = g.base.e;
+  g.beta = sqrtf((1.0f - e) * (1.0f + e));
+  const float n = g.base.n_hi;
+  g.n2 = n * n;
+  return g;
+}
+
+__device__ inline GradPlanetD grad_setup_f64(const double *p, double dref) {
+  GradPlanetD g;
+  g.base = planet_setup_f64(p, dref);
+  sincos(p[3], &g.sw, &g.cw);
+  g.K = p[1];
+  g.n2 = g.base.inv_P * g.base.inv_P;
+  return g;
+}
+
+__device__ inline double nan_d() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+__device__ inline double system_gamma_g(const double *p, int J) {
+  bool ok = isfinite(p[5 * J]);
+  for (int j = 0; j < J; ++j)
+    ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
+  return ok ? p[5 * J] : nan_d();
+}
+
+__device__ inline double inv_variance_g(double sigma, double jitter2) {
+  const double var = fma(sigma, sigma, jitter2);
+  return (var > 0.0) ? 1.0 / var : nan_d();
+}
+
+template <typename T>
+struct Partials {
+  T dP, dK, de, dw, dM;
+};
+
+// Partials of one planet's velocity from sin E, cos E and 1/D,
+// D = 1 - e cos E (shared by both precisions).
+template <typename T>
+__device__ __forceinline__ void velocity_partials(T e, T K, T cw, T sw, T beta, T sE, T cE,
+                                                  T invD, Partials<T> &d) {
+  const T cf = (cE - e) * invD;           // cos f
+  const T sf = beta * sE * invD;          // sin f
+  const T c_wf = cw * cf - sw * sf;       // cos(w + f)
+  const T s_wf = sw * cf + cw * sf;       // sin(w + f)
+  d.dK = c_wf + e * cw;
+  d.dw = -K * (s_wf + e * sw);
+  const T ks = K * s_wf * invD;
+  d.dM = -ks * beta * invD;
+  d.de = K * cw - ks * sE * (T(1) / beta + beta * invD);
+}
+
+struct MixedGradLayout {
+  size_t pl, gam, obs, w, total;
+  __host__ __device__ MixedGradLayout(int ST, int J, int obs_tile) {
+    pl = 0;
+    gam = pl + sizeof(GradPlanetF) * ST * J;
+    obs = align_up(gam + sizeof(float) * ST, 16);
+    w = obs + sizeof(float4) * obs_tile;
+    total = align_up(w + sizeof(float2) * obs_tile, 16);
+  }
+};
+
+struct ObsGD {
+  double tau, v, w, dt;    // dt = t - t0
+};
+
+struct F64GradLayout {
+  size_t pl, gam, obs, total;
+  __host__ __device__ F64GradLayout(int ST, int J, int obs_tile) {
+    pl = 0;
+    gam = pl + sizeof(GradPlanetD) * ST * J;
+    obs = align_up(gam + sizeof(double) * ST, 16);
+    total = align_up(obs + sizeof(ObsGD) * obs_tile, 16);
+  }
+};
+
+// ------------------------------------------------------------ mixed
+
+template <int J>
+__global__ void __launch_bounds__(256, 2)
+grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_out,
+                  float *__restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NP = 5 * J + 1;
+  const int block = blockDim.x;
+  const int ST = block / G;
+  const MixedGradLayout L(ST, J, obs_tile);
+  GradPlanetF *pl_s = reinterpret_cast<GradPlanetF *>(smem + L.pl);
+  float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
+  float2 *wt_s = reinterpret_cast<float2 *>(smem + L.w);   // (w_k, t_k - t0)
+
+  const int tid = threadIdx.x;
+  const int64_t sys0 = (int64_t)blockIdx.x * ST;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+  const float dref_f = d2f(dref);
+  const float jit2 = d2f(a.jitter2);
+  const int nwarps = block >> 5;
+
+  for (int i = (tid & 31) * nwarps + (tid >> 5); i < ST * J; i += block) {
+    const int sl = i / J, j = i - sl * J;
+    const int64_t s = sys0 + sl;
+    GradPlanetF q = {};
+    if (s < a.n_sys) q = grad_setup_mixed(a.params + s * NP + 5 * j, dref);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < ST; i += block) {
+    const int64_t s = sys0 + i;
+    gam_s[i] = s < a.n_sys ? (float)system_gamma_g(a.params + s * NP, J) : 0.0f;
+  }
+
+  const int sl = tid / G, c = tid - sl * G;
+  const int64_t s = sys0 + sl;
+  Kahan acc = {0.0f, 0.0f};
+  float g[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = 0.0f;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
+    const int nk = min(obs_tile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += block) {
+      const double tk = a.t[k0 + k];
+      float th, tl, vh, vl;
+      split_d(tk - t_ref, th, tl);
+      split_d(a.v[k0 + k], vh, vl);
+      obs_s[k] = make_float4(th, tl, vh, vl);
+      const float sg = d2f(a.sigma[k0 + k]);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      wt_s[k] = make_float2(var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000),
+                            th + dref_f);
+    }
+    __syncthreads();
+    const float gam = gam_s[sl];
+    const GradPlanetF *q = pl_s + sl * J;
+    for (int k = c; k < nk; k += G) {
+      const float4 o = obs_s[k];
+      const float2 wt = wt_s[k];
+      float sEj[J], cEj[J];
+      Kahan V = {0.0f, 0.0f};
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const PlanetF p = q[j].base;
+        const float M = mean_anomaly_mixed(o.x, o.y, p);
+        kepler_f32(M, p.e, sEj[j], cEj[j]);
+        kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+      }
+      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+      const float wr = wt.x * r;
+      kahan_add(acc, wr * r);
+      const float a2 = 2.0f * wr;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const GradPlanetF qj = q[j];
+        Partials<float> d;
+        const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
+        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+        d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
+        g[5 * j + 0] = fmaf(a2, d.dP, g[5 * j + 0]);
+        g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
+        g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
+        g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
+        g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+      }
+      g[5 * J] += a2;
+    }
+  }
+
+  for (int m = G >> 1; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
+  }
+  if (c == 0 && s < a.n_sys) {
+    const float poison = 0.0f * gam_s[sl];     // NaN for an invalid system
+    if (chi2_out) chi2_out[s] = kahan_value(acc) + poison;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
+  }
+}
+
+// ------------------------------------------------------------ FP64
+
+template <int J>
+__global__ void __launch_bounds__(256)
+grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_out,
+                double *__restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NP = 5 * J + 1;
+  const int block = blockDim.x;
+  const int ST = block / G;
+  const F64GradLayout L(ST, J, obs_tile);
+  GradPlanetD *pl_s = reinterpret_cast<GradPlanetD *>(smem + L.pl);
+  double *gam_s = reinterpret_cast<double *>(smem + L.gam);
+  ObsGD *obs_s = reinterpret_cast<ObsGD *>(smem + L.obs);
+
+  const int tid = threadIdx.x;
+  const int64_t sys0 = (int64_t)blockIdx.x * ST;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+
+  for (int i = (tid & 31) * (block >> 5) + (tid >> 5); i < ST * J; i += block) {
+    const int sl = i / J, j = i - sl * J;
+    const int64_t s = sys0 + sl;
+    GradPlanetD q = {};
+    if (s < a.n_sys) q = grad_setup_f64(a.params + s * NP + 5 * j, dref);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < ST; i += block) {
+    const int64_t s = sys0 + i;
+    gam_s[i] = s < a.n_sys ? system_gamma_g(a.params + s * NP, J) : 0.0;
+  }
+
+  const int sl = tid / G, c = tid - sl * G;
+  const int64_t s = sys0 + sl;
+  double acc = 0.0;
+  double g[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = 0.0;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
+    const int nk = min(obs_tile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += block) {
+      ObsGD o;
+      const double tk = a.t[k0 + k];
+      o.tau = tk - t_ref;
+      o.v = a.v[k0 + k];
+      o.w = inv_variance_g(a.sigma[k0 + k], a.jitter2);
+      o.dt = tk - a.t0;
+      obs_s[k] = o;
+    }
+    __syncthreads();
+    const double gam = gam_s[sl];
+    const GradPlanetD *q = pl_s + sl * J;
+    for (int k = c; k < nk; k += G) {
+      const ObsGD o = obs_s[k];
+      double sEj[J], cEj[J];
+      double V = gam;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const PlanetD p = q[j].base;
+        const double M = mean_anomaly_f64(o.tau, p);
+        kepler_f64(M, p.e, sEj[j], cEj[j]);
+        V += velocity_f64(p, sEj[j], cEj[j]);
+      }
+      const double r = V - o.v;
+      acc = fma(o.w * r, r, acc);
+      const double a2 = 2.0 * o.w * r;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const GradPlanetD qj = q[j];
+        Partials<double> d;
+        const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
+        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
+        d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
+        g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
+        g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);
+        g[5 * j + 2] = fma(a2, d.de, g[5 * j + 2]);
+        g[5 * j + 3] = fma(a2, d.dw, g[5 * j + 3]);
+        g[5 * j + 4] = fma(a2, d.dM, g[5 * j + 4]);
+      }
+      g[5 * J] += a2;
+    }
+  }
+
+  for (int m = G >> 1; m >= 1; m >>= 1) {
+    acc += shfl_xor(acc, m);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
+  }
+  if (c == 0 && s < a.n_sys) {
+    const double poison = 0.0 * gam_s[sl];
+    if (chi2_out) chi2_out[s] = acc + poison;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
+  }
+}
+
+template <typename Kern>
+cudaError_t set_smem(Kern k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t smem_grad(int n_pl, const Tile &t, bool f64) {
+  const int ST = t.block / t.G;
+  return f64 ? F64GradLayout(ST, n_pl, t.obs_tile).total
+             : MixedGradLayout(ST, n_pl, t.obs_tile).total;
+}
+
+#define KC_DISPATCH_J(J, MACRO) \
+  switch (J) {                  \
+    case 1: MACRO(1); break;    \
+    case 2: MACRO(2); break;    \
+    case 3: MACRO(3); break;    \
+    case 4: MACRO(4); break;    \
+    case 5: MACRO(5); break;    \
+    case 6: MACRO(6); break;    \
+    case 7: MACRO(7); break;    \
+    case 8: MACRO(8); break;    \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_grad_mixed(const UniformArgs &a, const Tile &tile, float *chi2, float *grad,
+                              cudaStream_t st) {
+  if (tile.G > 32) return cudaErrorInvalidValue;
+  const size_t smem = smem_grad(a.n_pl, tile, false);
+  const int ST = tile.block / tile.G;
+  const int grid = (int)((a.n_sys + ST - 1) / ST);
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                   \
+  err = set_smem(grad_mixed_kernel<JJ>, smem);                                          \
+  if (err == cudaSuccess)                                                               \
+    grad_mixed_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2, \
+                                                          grad);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2, double *grad,
+                            cudaStream_t st) {
+  if (tile.G > 32) return cudaErrorInvalidValue;
+  const size_t smem = smem_grad(a.n_pl, tile, true);
+  const int ST = tile.block / tile.G;
+  const int grid = (int)((a.n_sys + ST - 1) / ST);
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                 \
+  err = set_smem(grad_f64_kernel<JJ>, smem);                                          \
+  if (err == cudaSuccess)                                                             \
+    grad_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2, \
+                                                        grad);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -1,0 +1,63 @@
+// kc_internal.h -- host-side declarations shared by the library's
+// translation units (launchers and the tile table).  Not installed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/kc.h"
+
+namespace kc {
+
+// Launch shape of a uniform-batch kernel: each system is handled by G
+// consecutive threads (a power of two, 1..block); a CTA of `block` threads
+// covers block/G systems; observations are staged in shared memory
+// `obs_tile` at a time.
+struct Tile {
+  int G;
+  int block;
+  int obs_tile;
+};
+
+struct UniformArgs {
+  const double *params;
+  const double *t;
+  const double *v;
+  const double *sigma;
+  int64_t n_sys;
+  int n_pl;
+  int n_obs;
+  double t0;
+  double jitter2;
+};
+
+// Forward chi2 (kc_fwd.cu).
+cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
+                            float *resid, cudaStream_t st);
+cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out,
+                              float *resid, cudaStream_t st);
+// Gradient (kc_grad.cu).
+cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2,
+                            double *grad, cudaStream_t st);
+cudaError_t launch_grad_mixed(const UniformArgs &a, const Tile &tile, float *chi2,
+                              float *grad, cudaStream_t st);
+// Model velocities and elementwise Kepler (kc_fwd.cu).
+cudaError_t launch_rv_predict(const double *params, const double *t, int64_t n_sys, int n_pl,
+                              int n_obs, double t0, double *v_out, cudaStream_t st);
+cudaError_t launch_kepler_f64(const double *M, const double *e, int64_t n, double *E,
+                              cudaStream_t st);
+cudaError_t launch_kepler_f32(const float *M, const float *e, int64_t n, float *E,
+                              cudaStream_t st);
+
+// Shared-memory bytes a uniform kernel needs for a tile.
+size_t smem_chi2_f64(int n_pl, const Tile &tile);
+size_t smem_chi2_mixed(int n_pl, const Tile &tile);
+size_t smem_grad(int n_pl, const Tile &tile, bool f64);
+
+// Launch shape for a problem (kc_api.cu): the tuned table, else a heuristic.
+enum class Kind { Chi2F64 = 0, Chi2Mixed = 1, GradF64 = 2, GradMixed = 3 };
+Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
+Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
+int obs_tile_for(Kind kind, int n_obs);
+
+}  // namespace kc

@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/kc.h declares, and rejects bad arguments before launching anything.
+No call here reaches a kernel, so these run without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "kc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0812_2976_gb300 import _lib, build
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kc_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for want in ("kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
+                 "kc_rv_predict", "kc_kepler_solve", "kc_status_string", "kc_last_error",
+                 "kc_version"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header(lib):
+    from paper_0812_2976_gb300 import _lib
+    assert set(declared_functions()) == set(_lib.SIGNATURES)
+
+
+def test_status_strings(lib):
+    assert lib.kc_status_string(0) == b"ok"
+    assert lib.kc_status_string(1) == b"invalid argument"
+    assert lib.kc_version() >= 100
+
+
+def test_bad_arguments_rejected_on_host(lib):
+    p = ctypes.c_void_p(64)        # never dereferenced: checks fail first
+    # n_pl out of range
+    assert lib.kc_chi2_eval(p, p, p, p, 4, 0, 8, p, None) == 1
+    assert b"n_pl" in lib.kc_last_error()
+    assert lib.kc_chi2_eval(p, p, p, p, 4, 9, 8, p, None) == 1
+    # negative sizes
+    assert lib.kc_chi2_eval(p, p, p, p, -1, 2, 8, p, None) == 1
+    assert lib.kc_chi2_eval(p, p, p, p, 4, 2, -3, p, None) == 1
+    # NULL inputs / outputs
+    assert lib.kc_chi2_eval(None, p, p, p, 4, 2, 8, p, None) == 1
+    assert lib.kc_chi2_eval_mixed(p, p, p, p, 4, 2, 8, None, None, None) == 1
+    assert lib.kc_chi2_grad(p, p, p, p, 4, 2, 8, 0.0, 0.0, 1, None, None, None) == 1
+    # misaligned double pointer
+    assert lib.kc_chi2_eval(ctypes.c_void_p(68), p, p, p, 4, 2, 8, p, None) == 1
+    assert b"aligned" in lib.kc_last_error()
+    # bad mode, non-finite epoch
+    assert lib.kc_chi2_eval_ex(p, p, p, p, 4, 2, 8, 0.0, 0.0, 7, p, None, None) == 1
+    assert lib.kc_chi2_eval_ex(p, p, p, p, 4, 2, 8, float("nan"), 0.0, 1, p, None, None) == 1
+    assert lib.kc_kepler_solve(p, p, -1, 0, p, None) == 1
+    assert lib.kc_rv_predict(p, p, 2, 0, 4, 0.0, p, None) == 1
+
+
+def test_empty_batches_are_no_ops(lib):
+    p = ctypes.c_void_p(64)
+    assert lib.kc_chi2_eval(p, p, p, p, 0, 2, 8, p, None) == 0
+    assert lib.kc_chi2_grad(p, p, p, p, 0, 3, 8, 0.0, 0.0, 0, None, p, None) == 0
+    assert lib.kc_kepler_solve(p, p, 0, 1, p, None) == 0
+    assert lib.kc_rv_predict(p, p, 0, 2, 8, 0.0, p, None) == 0
+    assert lib.kc_last_error() == b""
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_0812_2976_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libkc.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()
+
+
+def test_tile_table_host_logic(lib):
+    from paper_0812_2976_gb300 import _lib
+    t = _lib.KcTile()
+    # default heuristic for the paper-shaped batch
+    assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
+    assert t.block in (64, 128, 256) and t.threads_per_system >= 1
+    default = (t.threads_per_system, t.block)
+    # pin, read back, same size class (power-of-two bucket), then remove
+    pin = _lib.KcTile(16, 128)
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(pin)) == 0
+    assert lib.kc_get_tile(0, 1, 5000, 4, 300, ctypes.byref(t)) == 0
+    assert (t.threads_per_system, t.block) == (16, 128)
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
+    assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
+    assert (t.threads_per_system, t.block) == default
+    # inadmissible tiles are refused
+    for bad in ((3, 128), (64, 32), (256, 128), (64, 256)):
+        kern = 1 if bad == (64, 256) else 0
+        assert lib.kc_set_tile(kern, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
+    assert lib.kc_get_tile(0, 1, 4096, 0, 256, ctypes.byref(t)) == 1

@@ -1,0 +1,277 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (relative error |d chi2| / max(chi2_oracle, 1)):
+  FP64 path   <= 1e-12
+  mixed path  <= 1e-5, Kepler residual <= 4e-6 rad
+  gradient    mixed <= 1e-3 per component, FP64 <= 1e-9, each normalised by
+              max(|g|, 1e-3 ||g||) of the oracle's gradient of that system.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+RESID_TOL = 4e-6
+GRAD_MIXED_TOL = 1e-3
+GRAD_F64_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def kc():
+    import paper_0812_2976_gb300 as kc
+    from paper_0812_2976_gb300 import build
+    build.build()
+    kc._lib.load()
+    return kc
+
+
+def dev(*arrs):
+    return [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+            for a in arrs]
+
+
+def rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    return np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+def grad_err(got, ref):
+    scale = np.maximum(np.abs(ref), 1e-3 * np.linalg.norm(ref, axis=1, keepdims=True))
+    return np.abs(np.asarray(got, dtype=np.float64) - ref) / scale
+
+
+def observed(oracle, w):
+    """v_obs = truth model (oracle) + seeded noise."""
+    return oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
+
+
+# ------------------------------------------------------------ configs 0-1
+
+def test_config0_fp64_and_mixed(kc, oracle_mod):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(0)
+    v = observed(oracle_mod, w)
+    ref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    got = kc.kc_chi2_eval(P, T, V, S).cpu().numpy()
+    assert rel_err(got, ref).max() <= FP64_TOL
+    got32, resid = kc.kc_chi2_eval_mixed(P, T, V, S, max_kepler_resid=True)
+    assert rel_err(got32.cpu().numpy(), ref).max() <= MIXED_TOL
+    assert float(resid.max()) <= RESID_TOL
+
+
+def test_config1_paper_batch(kc, oracle_mod):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1)
+    v = observed(oracle_mod, w)
+    ref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    got = kc.kc_chi2_eval(P, T, V, S).cpu().numpy()
+    e64 = rel_err(got, ref)
+    assert e64.max() <= FP64_TOL, e64.max()
+    got32, resid = kc.kc_chi2_eval_mixed(P, T, V, S, max_kepler_resid=True)
+    e32 = rel_err(got32.cpu().numpy(), ref)
+    assert e32.max() <= MIXED_TOL, e32.max()
+    assert float(resid.max()) <= RESID_TOL
+
+
+# ------------------------------------------------------------ config 2
+
+def test_config2_grid_sweep_full_size_sampled(kc, oracle_mod):
+    """The full 2^20-system launch; the oracle checks a sample of systems,
+    including the most eccentric ones, and every system's Kepler residual
+    is bounded."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(2)
+    v = observed(oracle_mod, w)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    got32, resid = kc.kc_chi2_eval_mixed(P, T, V, S, max_kepler_resid=True)
+    got32 = got32.cpu().numpy()
+    resid = resid.cpu().numpy()
+    assert np.all(np.isfinite(got32))
+    assert resid.max() <= RESID_TOL, resid.max()
+    rng = np.random.default_rng(0)
+    emax = w.params[:, 2::5][:, :4].max(axis=1)
+    idx = np.unique(np.concatenate([rng.choice(w.n_sys, 1500, replace=False),
+                                    np.argsort(emax)[-500:], [0, w.n_sys - 1]]))
+    ref = oracle_mod.chi2(w.params[idx], w.t, v, w.sigma, w.n_pl)
+    e = rel_err(got32[idx], ref)
+    assert e.max() <= MIXED_TOL, e.max()
+
+
+# ------------------------------------------------------------ config 3
+
+def test_config3_gradient_full_size_sampled(kc, oracle_mod):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(3)
+    v = observed(oracle_mod, w)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    chi, grad = kc.kc_chi2_grad(P, T, V, S, t0=w.t0, mode="mixed")
+    chi = chi.cpu().numpy()
+    grad = grad.cpu().numpy()
+    idx = np.unique(np.concatenate([np.random.default_rng(1).choice(w.n_sys, 400, replace=False),
+                                    [0, w.n_sys - 1]]))
+    ref, gref = oracle_mod.chi2(w.params[idx], w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
+    assert rel_err(chi[idx], ref).max() <= MIXED_TOL
+    ge = grad_err(grad[idx], gref)
+    assert ge.max() <= GRAD_MIXED_TOL, ge.max()
+    # FP64 adjoint on the sampled systems
+    c64, g64 = kc.kc_chi2_grad(dev(w.params[idx])[0], T, V, S, t0=w.t0, mode="fp64")
+    assert rel_err(c64.cpu().numpy(), ref).max() <= FP64_TOL
+    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+
+
+def test_autograd_function_matches_adjoint(kc, oracle_mod):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(3, n_sys=64)
+    v = observed(oracle_mod, w)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    weights = torch.linspace(0.5, 2.0, 64, device="cuda", dtype=torch.float64)
+    Pg = P.clone().requires_grad_(True)
+    (kc.chi2(Pg, T, V, S, t0=w.t0, mode="fp64") * weights).sum().backward()
+    _, gref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
+    gref = gref * weights.cpu().numpy()[:, None]
+    assert grad_err(Pg.grad.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+
+
+# ------------------------------------------------------------ shapes, edges
+
+@pytest.mark.parametrize("n_pl", [1, 2, 3, 5, 6, 7, 8])
+def test_planet_counts_ragged_tail_many_tiles(kc, oracle_mod, n_pl):
+    """n_sys not a multiple of any tile, several CTAs, every n_pl."""
+    rng = np.random.default_rng(100 + n_pl)
+    n_sys, n_obs = 777, 301
+    t = np.sort(rng.uniform(2450000, 2455000, n_obs))
+    sig = rng.uniform(1, 5, n_obs)
+    cols = []
+    for _ in range(n_pl):
+        cols += [np.exp(rng.uniform(0, np.log(4000), n_sys)), rng.uniform(1, 100, n_sys),
+                 rng.uniform(0, 0.95, n_sys), rng.uniform(0, 2 * np.pi, n_sys),
+                 rng.uniform(0, 2 * np.pi, n_sys)]
+    params = np.stack(cols + [rng.uniform(-10, 10, n_sys)], axis=1)
+    v = rng.normal(0, 40, n_obs)
+    ref, gref = oracle_mod.chi2(params, t, v, sig, n_pl, t0=2450000.0, jitter=1.5, grad=True)
+    P, T, V, S = dev(params, t, v, sig)
+    c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, jitter=1.5, mode="fp64").cpu().numpy()
+    assert rel_err(c64, ref).max() <= FP64_TOL
+    c32 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, jitter=1.5, mode="mixed").cpu().numpy()
+    assert rel_err(c32, ref).max() <= MIXED_TOL
+    _, g32 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, jitter=1.5, mode="mixed")
+    assert grad_err(g32.cpu().numpy(), gref).max() <= GRAD_MIXED_TOL
+    _, g64 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, jitter=1.5, mode="fp64")
+    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+
+
+def test_many_observations_span_several_smem_tiles(kc, oracle_mod):
+    rng = np.random.default_rng(7)
+    n_sys, n_obs, n_pl = 40, 9000, 2
+    t = np.sort(rng.uniform(2450000, 2460000, n_obs))
+    sig = rng.uniform(1, 5, n_obs)
+    w = synth_rows(rng, n_sys, n_pl)
+    v = rng.normal(0, 40, n_obs)
+    ref = oracle_mod.chi2(w, t, v, sig, n_pl)
+    P, T, V, S = dev(w, t, v, sig)
+    assert rel_err(kc.kc_chi2_eval(P, T, V, S).cpu().numpy(), ref).max() <= FP64_TOL
+    assert rel_err(kc.kc_chi2_eval_mixed(P, T, V, S).cpu().numpy(), ref).max() <= MIXED_TOL
+
+
+def synth_rows(rng, n_sys, n_pl):
+    cols = []
+    for _ in range(n_pl):
+        cols += [np.exp(rng.uniform(0, np.log(4000), n_sys)), rng.uniform(1, 100, n_sys),
+                 rng.uniform(0, 0.9, n_sys), rng.uniform(0, 2 * np.pi, n_sys),
+                 rng.uniform(0, 2 * np.pi, n_sys)]
+    return np.stack(cols + [rng.uniform(-10, 10, n_sys)], axis=1)
+
+
+def test_empty_and_invalid(kc, oracle_mod):
+    rng = np.random.default_rng(8)
+    par = synth_rows(rng, 10, 2)
+    par[3, 2] = 1.0       # e = 1
+    par[5, 5] = -2.0      # P < 0
+    par[7, -1] = np.nan   # gamma
+    t = np.sort(rng.uniform(0, 100, 16))
+    v = rng.normal(0, 5, 16)
+    sig = np.ones(16)
+    P, T, V, S = dev(par, t, v, sig)
+    for mode in ("fp64", "mixed"):
+        out = kc.kc_chi2_eval_ex(P, T, V, S, mode=mode).cpu().numpy()
+        assert np.all(np.isnan(out[[3, 5, 7]]))
+        ok = np.setdiff1d(np.arange(10), [3, 5, 7])
+        assert np.all(np.isfinite(out[ok]))
+        # no observations: chi2 = 0 for valid systems, NaN for invalid ones
+        out0 = kc.kc_chi2_eval_ex(P, T[:0], V[:0], S[:0], mode=mode).cpu().numpy()
+        assert np.all(out0[ok] == 0.0) and np.all(np.isnan(out0[[3, 5, 7]]))
+        # a non-positive uncertainty poisons every system
+        S_bad = S.clone()
+        S_bad[4] = 0.0
+        assert np.all(np.isnan(kc.kc_chi2_eval_ex(P, T, V, S_bad, mode=mode).cpu().numpy()))
+    # empty batch
+    empty = kc.kc_chi2_eval(P[:0], T, V, S)
+    assert empty.numel() == 0
+
+
+def test_noise_free_truth_gives_zero(kc, oracle_mod):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1, n_sys=8)
+    v = oracle_mod.predict(w.truth, w.t, w.n_pl)[0]
+    P, T, V, S = dev(np.tile(w.truth, (8, 1)), w.t, v, w.sigma)
+    wsum = np.sum(1.0 / w.sigma ** 2)
+    c64 = kc.kc_chi2_eval(P, T, V, S).cpu().numpy()
+    c32 = kc.kc_chi2_eval_mixed(P, T, V, S).cpu().numpy()
+    assert np.all(c64 <= wsum * 1e-9 ** 2)
+    assert np.all(c32 <= wsum * 1e-3 ** 2)
+
+
+def test_m0_period_invariance(kc):
+    rng = np.random.default_rng(9)
+    par = synth_rows(rng, 300, 4)
+    t = np.sort(rng.uniform(2450000, 2454000, 256))
+    v = rng.normal(0, 40, 256)
+    sig = rng.uniform(1, 5, 256)
+    shifted = par.copy()
+    shifted[:, 4:20:5] += 2 * np.pi
+    P, T, V, S = dev(par, t, v, sig)
+    P2 = dev(shifted)[0]
+    a = kc.kc_chi2_eval(P, T, V, S).cpu().numpy()
+    b = kc.kc_chi2_eval(P2, T, V, S).cpu().numpy()
+    assert rel_err(b, a).max() <= 1e-12
+    a32 = kc.kc_chi2_eval_mixed(P, T, V, S).cpu().numpy()
+    b32 = kc.kc_chi2_eval_mixed(P2, T, V, S).cpu().numpy()
+    assert rel_err(b32, a32.astype(np.float64)).max() <= MIXED_TOL
+
+
+# ------------------------------------------------------------ Kepler, predict
+
+def test_kepler_solve_vs_oracle(kc, oracle_mod):
+    e = np.repeat(np.linspace(0.0, 0.95, 96), 401)
+    M = np.tile(np.linspace(-np.pi, np.pi, 401), 96)
+    Eref = oracle_mod.kepler_E(M, e)
+    E64 = kc.kc_kepler_solve(*dev(M, e), mode="fp64").cpu().numpy()
+    assert np.max(np.abs(E64 - Eref) * (1 - e * np.cos(Eref))) <= 1e-14
+    Mf = torch.tensor(M, dtype=torch.float32, device="cuda")
+    ef = torch.tensor(e, dtype=torch.float32, device="cuda")
+    E32 = kc.kc_kepler_solve(Mf, ef, mode="mixed").cpu().numpy().astype(np.float64)
+    m32 = Mf.cpu().numpy().astype(np.float64)
+    e32 = ef.cpu().numpy().astype(np.float64)
+    # the solver works on M reduced to [-pi, pi]: compare modulo 2 pi
+    resid = np.abs(np.remainder(E32 - e32 * np.sin(E32) - m32 + np.pi, 2 * np.pi) - np.pi)
+    assert resid.max() <= RESID_TOL, resid.max()
+    # M outside [-pi, pi] is reduced first
+    Mbig = M + 2 * np.pi * 7
+    E64b = kc.kc_kepler_solve(*dev(Mbig, e), mode="fp64").cpu().numpy()
+    wrapped = np.abs(np.remainder(E64b - Eref + np.pi, 2 * np.pi) - np.pi)
+    assert np.max(wrapped) <= 1e-12
+
+
+def test_rv_predict_vs_oracle(kc, oracle_mod):
+    rng = np.random.default_rng(11)
+    par = synth_rows(rng, 50, 3)
+    t = np.sort(rng.uniform(2450000, 2456000, 123))
+    for t0 in (0.0, 2450000.0):
+        ref = oracle_mod.predict(par, t, 3, t0)
+        got = kc.kc_rv_predict(*dev(par, t), t0=t0).cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-9
