@@ -54,7 +54,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="kc", choices=["kc", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[1, 2])
+    ap.add_argument("--config", type=int, default=1, choices=[1, 2, 4],
+                    help="1: paper-shaped batch (default), 2: 2^20-system sweep, "
+                         "4: ragged batch (forward + gradient, one persistent launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the built-in tile heuristic instead of the autotuner")
@@ -161,6 +163,8 @@ def run_reference(args):
     import oracle
     from paper_0812_2976_gb300 import synth
     oracle.build()
+    if args.config == 4:
+        return run_reference_ragged(args)
     w = synth.uniform(args.config, n_sys=None if args.config == 1 else 4096)
     v = oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
     per_step = 256                                  # systems per timed step
@@ -190,6 +194,42 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_reference_ragged(args):
+    """The oracle on the ragged workload: each step a 200-system sample."""
+    import oracle
+    from paper_0812_2976_gb300 import synth
+    w = synth.ragged()
+    cores = oracle.max_threads()
+    per_step = 200
+    rng = np.random.default_rng(0)
+    subs = []
+    for _ in range(args.warmup + args.steps):
+        sub = synth.subset_ragged(w, np.sort(rng.choice(w.n_sys, per_step, replace=False)))
+        v = oracle.predict_ragged(sub.truth, sub.par_off, sub.n_pl, sub.t, sub.obs_off) + sub.noise
+        subs.append((sub, v))
+    for sub, v in subs[:args.warmup]:
+        oracle.chi2_ragged(sub.params, sub.par_off, sub.n_pl, sub.t, v, sub.sigma, sub.obs_off,
+                           grad=True)
+    evals, t0 = 0, time.perf_counter()
+    for sub, v in subs[args.warmup:]:
+        oracle.chi2_ragged(sub.params, sub.par_off, sub.n_pl, sub.t, v, sub.sigma, sub.obs_off,
+                           grad=True)
+        evals += sub.evals()
+    el = time.perf_counter() - t0
+    value = evals / el
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)",
+        "value": value, "unit": "planet-obs evals/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "ragged", "n_sys_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "planet-obs evals/s", "cores": cores,
+                         "kind": "oracle", "sample": f"{per_step} random systems per step"},
+        "e2e": {"value": value, "unit": "planet-obs evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def run_kc(args):
@@ -351,10 +391,153 @@ def run_kc(args):
         torch.distributed.destroy_process_group()
 
 
+def time_steps(fn, steps, stream, flush):
+    """Sum of per-step CUDA-event times of fn() with a cold L2 each step."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i, (a, b) in enumerate(ev):
+        flush.fill_(i & 0xFF)
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+
+def run_kc_ragged(args):
+    """Config 4: 200000 systems with their own n_obs ~ U[16,1024] and
+    n_pl ~ U{1..6}; one step = forward chi2 + gradient of every system in
+    one persistent, graph-replayed launch (kc_plan_run)."""
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_0812_2976_gb300 as kc
+    from paper_0812_2976_gb300 import build, synth
+    build.build()
+    kc._lib.load()
+    w = synth.ragged(seed=None if rank == 0 else synth.SEED_BASE + 4 + 1000 * rank)
+    stream = torch.cuda.current_stream(dev)
+    T = torch.tensor(w.t, device=dev)
+    S = torch.tensor(w.sigma, device=dev)
+    V = kc.kc_rv_predict_ragged(torch.tensor(w.truth, device=dev), torch.tensor(w.par_off),
+                                torch.tensor(w.n_pl), T, torch.tensor(w.obs_off))
+    V += torch.tensor(w.noise, device=dev)
+    P = torch.tensor(w.params, device=dev)
+    evals = w.evals()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=True)
+    plan.set_observations(T, V, S)
+    shape = plan.autotune(P) if not args.no_tune else None
+    chi, grad = plan.run(P)
+    for _ in range(max(args.warmup, 3)):
+        plan.run(P, chi, grad)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    if sampler:
+        sampler.start()
+    t_sum = time_steps(lambda: plan.run(P, chi, grad), args.steps, stream, flush)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_sum = float(tt.item())
+    value = evals * args.steps * world / t_sum
+
+    # forward only, and the padded uniform-size baseline (same kernel, every
+    # system padded to n_pl = 6 with K = 0 and n_obs = 1024 with zero weight)
+    fplan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed")
+    fplan.set_observations(T, V, S)
+    if not args.no_tune:
+        fplan.autotune(P)
+    fchi = fplan.run(P)
+    fwd_s = time_steps(lambda: fplan.run(P, fchi), args.steps, stream, flush)
+    del fplan
+    pw, pv = synth.pad_ragged(w, V.cpu().numpy(), n_pl=6, n_obs=1024)
+    pplan = kc.RaggedPlan(pw.obs_off, pw.n_pl, mode="mixed", want_grad=True)
+    pT, pV, pS = (torch.tensor(pw.t, device=dev), torch.tensor(pv, device=dev),
+                  torch.tensor(pw.sigma, device=dev))
+    pplan.set_observations(pT, pV, pS)
+    PP = torch.tensor(pw.params, device=dev)
+    if not args.no_tune:
+        pplan.autotune(PP)
+    pchi, pgrad = pplan.run(PP)
+    pad_steps = max(3, args.steps // 4)
+    pad_s = time_steps(lambda: pplan.run(PP, pchi, pgrad), pad_steps, stream, flush)
+    del pplan, pT, pV, pS
+
+    # end to end: host parameters in, host chi2 + gradient out
+    hP = torch.tensor(w.params).pin_memory()
+    hchi = torch.empty_like(chi, device="cpu").pin_memory()
+    hgrad = torch.empty_like(grad, device="cpu").pin_memory()
+    dP = torch.empty_like(P)
+
+    def e2e_step():
+        dP.copy_(hP, non_blocking=True)
+        plan.run(dP, chi, grad)
+        hchi.copy_(chi, non_blocking=True)
+        hgrad.copy_(grad, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    e2e_s = time_steps(e2e_step, args.steps, stream, flush)
+    if rank != 0:
+        return
+    line = {
+        "metric": "planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)",
+        "value": value, "unit": "planet-obs evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_sum / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+ds (mixed)", "data": "synthetic",
+        "config": {"workload": "ragged", "n_sys": w.n_sys, "evals": evals,
+                   "n_obs_total": int(w.obs_off[-1]), "l2": "flushed between steps",
+                   "launch": {"block": shape[0], "ctas_per_sm": shape[1], "how": "autotuned"}
+                   if shape else "default"},
+        "forward_only": {"value": evals / (fwd_s / args.steps), "unit": "planet-obs evals/s"},
+        "padded_baseline": {"value": evals / (pad_s / pad_steps),
+                            "unit": "planet-obs evals/s (useful)",
+                            "padded_evals": int(pw.n_sys * 6 * 1024),
+                            "ms_per_step": 1e3 * pad_s / pad_steps},
+        "e2e": {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
+                "h2d_bytes_per_step": hP.numel() * 8,
+                "d2h_bytes_per_step": (hchi.numel() + hgrad.numel()) * 4},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        idx = np.arange(0, w.n_sys, max(1, w.n_sys // 2000))
+        sub = synth.subset_ragged(w, idx)
+        vsub = oracle.predict_ragged(sub.truth, sub.par_off, sub.n_pl, sub.t,
+                                     sub.obs_off) + sub.noise
+        t0c = time.perf_counter()
+        oracle.chi2_ragged(sub.params, sub.par_off, sub.n_pl, sub.t, vsub, sub.sigma,
+                           sub.obs_off, grad=True)
+        el = time.perf_counter() - t0c
+        line["cpu_baseline"] = {"value": sub.evals() / el, "unit": "planet-obs evals/s",
+                                "cores": oracle.max_threads(), "kind": "oracle",
+                                "sample": f"{idx.size} systems (every {idx[1] - idx[0]}th), "
+                                          f"chi2 + gradient, {el:.1f} s wall"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == 4:
+        run_kc_ragged(args)
     else:
         run_kc(args)
 

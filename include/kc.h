@@ -30,8 +30,9 @@
  *    return KC_ERR_ARG before anything is launched; a failed launch returns
  *    KC_ERR_CUDA.  kc_last_error() gives a message for the calling thread.
  *  - Physically invalid parameters (P <= 0, e outside [0, 1), non-finite
- *    values) give NaN for that system; a non-positive variance gives NaN for
- *    every system.  Nothing traps: every device loop has a fixed trip count.
+ *    values) give NaN for that system; a non-positive or NaN variance gives
+ *    NaN for every system, an infinite one a zero weight.  Nothing traps:
+ *    every device loop has a fixed trip count.
  *  - n_sys == 0 is a no-op.  n_obs == 0 gives chi2 = 0 (NaN if invalid).
  *  - Calls are thread-safe; concurrent calls on different streams do not
  *    share device memory.
@@ -120,12 +121,74 @@ kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys,
                         int32_t n_pl, int32_t n_obs, double t0, double *v_out,
                         kc_stream stream);
 
+/* FP64 model velocities of a ragged batch (device arrays): system s has
+ * n_pl[s] planets at params[par_off[s]] and its own times
+ * t[obs_off[s] .. obs_off[s+1]); v_out has the layout of t. */
+kc_status kc_rv_predict_ragged(const double *params, const int64_t *par_off,
+                               const int32_t *n_pl, const double *t,
+                               const int64_t *obs_off, int64_t n_sys, double t0,
+                               double *v_out, kc_stream stream);
+
 /* Elementwise Kepler solve with the same device solver the chi2 kernels use
  * (Sec. 4.3): E_out[i] with E - e sin E = M for M[i] in any range and
  * 0 <= e[i] < 1.  KC_FP64: M, e, E_out are double.  KC_MIXED: float.
  * E_out is reduced to the branch of M reduced to [-pi, pi]. */
 kc_status kc_kepler_solve(const void *M, const void *e, int64_t n,
                           kc_mode mode, void *E_out, kc_stream stream);
+
+/* ------------------------------------------------------------- ragged */
+
+/* A plan for a ragged batch: systems with their own planet count and their
+ * own observations, evaluated by one persistent kernel that takes whole
+ * systems from a device work queue (longest first) and is replayed as a CUDA
+ * graph.  The observations are fixed for the plan (as the paper treats them,
+ * Sec. 4.1); the parameters change from run to run.
+ *   obs_off [n_sys+1] host int64: system s owns observations
+ *                     obs_off[s] .. obs_off[s+1] (obs_off[0] == 0,
+ *                     non-decreasing; empty systems allowed).
+ *   n_pl    [n_sys]   host int32 in 1 .. KC_MAX_PLANETS.
+ * Parameters are packed: system s's 5*n_pl[s]+1 values (same layout as the
+ * uniform calls) follow those of system s-1.  The plan copies the
+ * descriptors to the current device and owns that memory, the converted
+ * observations and its work queue until kc_plan_destroy.  Creation
+ * allocates and synchronises; KC_ERR_NOMEM if the device is out of memory. */
+typedef struct kc_plan kc_plan;
+
+kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off,
+                                const int32_t *n_pl, int64_t n_sys, double t0,
+                                double jitter, kc_mode mode, int want_grad);
+
+/* Total number of packed parameters (sum of 5*n_pl[s]+1) and of
+ * observations of the plan. */
+kc_status kc_plan_sizes(const kc_plan *plan, int64_t *n_params,
+                        int64_t *n_obs);
+
+/* Converts the observations (device [n_obs] doubles t, v_obs, sigma) into
+ * the plan's own arrays, on `stream`.  Must precede kc_plan_run; later runs
+ * on other streams must be ordered after it by the caller. */
+kc_status kc_plan_set_observations(kc_plan *plan, const double *t,
+                                   const double *v_obs, const double *sigma,
+                                   kc_stream stream);
+
+/* chi2_out [n_sys] (float for KC_MIXED, double for KC_FP64) and, for a plan
+ * created with want_grad, grad_out laid out like the packed parameters
+ * (same type), else NULL.  The first run on a stream captures the queue
+ * reset and the kernel into a CUDA graph; later runs on that stream replay
+ * it (with the new pointers).  When `stream` is itself being captured the
+ * two operations are recorded into the caller's graph instead.  Runs of
+ * one plan must not overlap on the device (they share the work queue). */
+kc_status kc_plan_run(kc_plan *plan, const double *params, void *chi2_out,
+                      void *grad_out, kc_stream stream);
+
+/* Times persistent launch shapes (threads per CTA x CTAs per SM) on these
+ * parameters and keeps the fastest for later runs.  Blocking; not during
+ * stream capture.  Outputs are overwritten.  *block / *ctas_per_sm (may
+ * be NULL) receive the choice. */
+kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out,
+                           void *grad_out, int32_t *block, int32_t *ctas_per_sm,
+                           kc_stream stream);
+
+void kc_plan_destroy(kc_plan *plan);
 
 /* ------------------------------------------------------------ tiling */
 

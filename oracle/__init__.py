@@ -72,6 +72,8 @@ def _load():
         lib.kco_predict.restype = ctypes.c_int
         lib.kco_predict.argtypes = [d, d, i64, ctypes.c_int, i64,
                                     ctypes.c_double, d]
+        lib.kco_predict_ragged.restype = ctypes.c_int
+        lib.kco_predict_ragged.argtypes = [d, i64p, i32p, d, i64p, i64, ctypes.c_double, d]
         lib.kco_kepler_batch.argtypes = [d, d, i64, d, i32p]
         lib.kco_mean_anomaly_batch.argtypes = [d, ctypes.c_double, d, d, i64, d]
         lib.kco_true_anomaly_batch.argtypes = [d, d, i64, d]
@@ -187,3 +189,19 @@ def chi2_ragged(params, par_off, n_pl, t, v, sigma, obs_off, t0: float = 0.0,
     if rc != 0:
         raise ValueError("oracle.chi2_ragged: bad sizes")
     return (out, g) if grad else out
+
+
+def predict_ragged(params, par_off, n_pl, t, obs_off, t0: float = 0.0) -> np.ndarray:
+    """Model velocities of a ragged batch, laid out like t (Eq. 2)."""
+    params, t = _f64(params), _f64(t)
+    par_off = np.ascontiguousarray(par_off, dtype=np.int64)
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    n_pl = np.ascontiguousarray(n_pl, dtype=np.int32)
+    out = np.empty_like(t)
+    rc = _load().kco_predict_ragged(_p(params), _p(par_off, ctypes.c_int64),
+                                    _p(n_pl, ctypes.c_int32), _p(t),
+                                    _p(obs_off, ctypes.c_int64), n_pl.size, float(t0),
+                                    _p(out))
+    if rc != 0:
+        raise ValueError("oracle.predict_ragged: bad sizes")
+    return out

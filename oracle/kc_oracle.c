@@ -36,7 +36,8 @@
  *
  * Parameter layout (one system): (P, K, e, omega, M0) for each planet j, then
  * gamma; 5*n_pl + 1 doubles.  Invalid parameters (P <= 0, e outside [0,1),
- * non-finite values) or a non-positive variance give NaN for that system.
+ * non-finite values) or a non-positive (or NaN) variance give NaN for that
+ * system; an infinite variance is a zero weight.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC
  * (no -ffast-math: the compensated sums need IEEE semantics).
@@ -203,7 +204,7 @@ static double kco_system(const double *par, int n_pl, const double *t,
         double wk = 1.0 / var;
         double V = gamma, r;
         double g[16][5];
-        if (!(var > 0.0) || !isfinite(var)) {
+        if (!(var > 0.0)) {              /* var = +inf: weight 0 (Eq. 5) */
             if (grad) for (q = 0; q < n_par; ++q) grad[q] = NAN;
             return NAN;
         }
@@ -285,6 +286,33 @@ int kco_predict(const double *params, const double *t, int64_t n_sys, int n_pl,
             double V = par[5 * n_pl];
             for (j = 0; j < n_pl; ++j) V += kco_planet_velocity(par + 5 * j, t[k], t0);
             out[s * n_obs + k] = valid ? V : NAN;
+        }
+    }
+    return 0;
+}
+
+/* Model velocities of a ragged batch: system s (n_pl[s] planets at
+ * params[par_off[s]]) at its own times t[obs_off[s] .. obs_off[s+1]);
+ * out has the layout of t. */
+int kco_predict_ragged(const double *params, const int64_t *par_off,
+                       const int32_t *n_pl, const double *t,
+                       const int64_t *obs_off, int64_t n_sys, double t0,
+                       double *out)
+{
+    int64_t s;
+    for (s = 0; s < n_sys; ++s)
+        if (n_pl[s] < 1 || n_pl[s] > 16 || obs_off[s + 1] < obs_off[s]) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (s = 0; s < n_sys; ++s) {
+        const double *par = params + par_off[s];
+        int J = n_pl[s], j;
+        int64_t k;
+        int valid = isfinite(par[5 * J]);
+        for (j = 0; j < J; ++j) valid = valid && kco_planet_valid(par + 5 * j);
+        for (k = obs_off[s]; k < obs_off[s + 1]; ++k) {
+            double V = par[5 * J];
+            for (j = 0; j < J; ++j) V += kco_planet_velocity(par + 5 * j, t[k], t0);
+            out[k] = valid ? V : NAN;
         }
     }
     return 0;

@@ -22,8 +22,8 @@ from ._lib import KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
 __all__ = [
     "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
-    "kc_rv_predict", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
-    "chi2", "n_planets", "library_path",
+    "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
+    "RaggedPlan", "chi2", "n_planets", "library_path",
 ]
 
 library_path = _lib.LIB_PATH
@@ -171,6 +171,25 @@ def kc_rv_predict(params, t, t0: float = 0.0, out=None, stream=None) -> torch.Te
     return out
 
 
+def kc_rv_predict_ragged(params, par_off, n_pl, t, obs_off, t0: float = 0.0, out=None,
+                         stream=None) -> torch.Tensor:
+    """FP64 model velocities of a ragged batch, laid out like t
+    (kc_rv_predict_ragged).  par_off/obs_off: int64, n_pl: int32 CUDA tensors."""
+    params = _dev_f64("params", params, 1)
+    t = _dev_f64("t", t, 1)
+    par_off = par_off.to(device=params.device, dtype=torch.int64).contiguous()
+    obs_off = obs_off.to(device=params.device, dtype=torch.int64).contiguous()
+    n_pl = n_pl.to(device=params.device, dtype=torch.int32).contiguous()
+    if out is None:
+        out = torch.empty_like(t)
+    lib = _lib.load()
+    _lib.check(lib.kc_rv_predict_ragged(params.data_ptr(), par_off.data_ptr(), n_pl.data_ptr(),
+                                        t.data_ptr(), obs_off.data_ptr(), n_pl.numel(),
+                                        float(t0), out.data_ptr(), _stream(stream)),
+               "kc_rv_predict_ragged")
+    return out
+
+
 def kc_kepler_solve(M, e, mode="fp64", out=None, stream=None) -> torch.Tensor:
     """Elementwise E with E - e sin E = M (kc_kepler_solve)."""
     m = _mode(mode)
@@ -229,6 +248,83 @@ def kc_get_tile(kernel, mode, n_sys: int, n_pl: int, n_obs: int):
     _lib.check(lib.kc_get_tile(_kernel(kernel), _mode(mode), n_sys, n_pl, n_obs,
                                ctypes.byref(t)), "kc_get_tile")
     return t.threads_per_system, t.block
+
+
+class RaggedPlan:
+    """Ragged batch (include/kc.h: kc_plan_*): systems with their own planet
+    count and observations, evaluated by one persistent, graph-replayed
+    kernel.  ``obs_off`` [n_sys+1] and ``n_pl`` [n_sys] are host arrays;
+    parameters are packed per system (5*n_pl[s]+1 values each)."""
+
+    def __init__(self, obs_off, n_pl, t0: float = 0.0, jitter: float = 0.0, mode="mixed",
+                 want_grad: bool = False):
+        import numpy as np
+        self._obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+        self._n_pl = np.ascontiguousarray(n_pl, dtype=np.int32)
+        self.n_sys = int(self._n_pl.size)
+        self.mode = _mode(mode)
+        self.want_grad = bool(want_grad)
+        self._lib = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.kc_plan_create_ragged(
+            ctypes.byref(h), self._obs_off.ctypes.data, self._n_pl.ctypes.data, self.n_sys,
+            float(t0), float(jitter), self.mode, int(self.want_grad)), "kc_plan_create_ragged")
+        self._h = h
+        n_par, n_obs = ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(self._lib.kc_plan_sizes(h, ctypes.byref(n_par), ctypes.byref(n_obs)),
+                   "kc_plan_sizes")
+        self.n_params, self.n_obs = n_par.value, n_obs.value
+        self._keep = None
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.mode == KC_FP64 else torch.float32
+
+    def set_observations(self, t, v_obs, sigma, stream=None) -> None:
+        t, v_obs, sigma = _obs(t, v_obs, sigma)
+        if t.numel() != self.n_obs:
+            raise ValueError(f"expected {self.n_obs} observations, got {t.numel()}")
+        _lib.check(self._lib.kc_plan_set_observations(
+            self._h, t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), _stream(stream)),
+            "kc_plan_set_observations")
+        self._keep = (t, v_obs, sigma)
+
+    def _outputs(self, params, chi2_out, grad_out):
+        params = _dev_f64("params", params, 1)
+        if params.numel() != self.n_params:
+            raise ValueError(f"expected {self.n_params} packed parameters")
+        if chi2_out is None:
+            chi2_out = torch.empty(self.n_sys, dtype=self.dtype, device=params.device)
+        if self.want_grad and grad_out is None:
+            grad_out = torch.empty(self.n_params, dtype=self.dtype, device=params.device)
+        return params, chi2_out, grad_out
+
+    def run(self, params, chi2_out=None, grad_out=None, stream=None):
+        """chi2 [n_sys] (and the packed gradient if the plan wants it)."""
+        params, chi2_out, grad_out = self._outputs(params, chi2_out, grad_out)
+        _lib.check(self._lib.kc_plan_run(self._h, params.data_ptr(), chi2_out.data_ptr(),
+                                         _ptr(grad_out), _stream(stream)), "kc_plan_run")
+        return (chi2_out, grad_out) if self.want_grad else chi2_out
+
+    def autotune(self, params, stream=None):
+        """Pick the persistent launch shape; returns (block, ctas_per_sm)."""
+        params, chi2_out, grad_out = self._outputs(params, None, None)
+        b, k = ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(self._lib.kc_plan_autotune(self._h, params.data_ptr(), chi2_out.data_ptr(),
+                                              _ptr(grad_out), ctypes.byref(b), ctypes.byref(k),
+                                              _stream(stream)), "kc_plan_autotune")
+        return b.value, k.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.kc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _Chi2Fn(torch.autograd.Function):

@@ -44,7 +44,16 @@ SIGNATURES = {
     "kc_chi2_grad": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _i32, _d,
                             _d, _st]),
     "kc_rv_predict": (_i32, [_d, _d, _i64, _i32, _i32, _f64, _d, _st]),
+    "kc_rv_predict_ragged": (_i32, [_d, _d, _d, _d, _d, _i64, _f64, _d, _st]),
     "kc_kepler_solve": (_i32, [_d, _d, _i64, _i32, _d, _st]),
+    "kc_plan_create_ragged": (_i32, [ctypes.POINTER(ctypes.c_void_p), _d, _d, _i64, _f64,
+                                     _f64, _i32, _i32]),
+    "kc_plan_sizes": (_i32, [ctypes.c_void_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "kc_plan_set_observations": (_i32, [ctypes.c_void_p, _d, _d, _d, _st]),
+    "kc_plan_run": (_i32, [ctypes.c_void_p, _d, _d, _d, _st]),
+    "kc_plan_autotune": (_i32, [ctypes.c_void_p, _d, _d, _d, ctypes.POINTER(_i32),
+                                ctypes.POINTER(_i32), _st]),
+    "kc_plan_destroy": (None, [ctypes.c_void_p]),
     "kc_set_tile": (_i32, [_i32, _i32, _i64, _i32, _i32, _tile_p]),
     "kc_get_tile": (_i32, [_i32, _i32, _i64, _i32, _i32, _tile_p]),
     "kc_autotune": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _i32, _i32, _tile_p,

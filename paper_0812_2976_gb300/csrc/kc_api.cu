@@ -11,12 +11,13 @@
 #include <vector>
 
 #include "kc_internal.h"
+#include "kc_ragged.h"
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
-kc_status fail(kc_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+namespace kc {
 
 kc_status fail(kc_status st, const char *fmt, ...) {
   char buf[512];
@@ -37,6 +38,14 @@ kc_status cuda_status(cudaError_t e, const char *what) {
   if (e == cudaSuccess) return ok();
   return fail(KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+}  // namespace kc
+
+using kc::cuda_status;
+using kc::fail;
+using kc::ok;
+
+namespace {
 
 kc_status check_uniform(const double *params, const double *t, const double *v,
                         const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
@@ -228,6 +237,22 @@ kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys, in
   return cuda_status(kc::launch_rv_predict(params, t, n_sys, n_pl, n_obs, t0, v_out,
                                            reinterpret_cast<cudaStream_t>(stream)),
                      "kc_rv_predict");
+}
+
+kc_status kc_rv_predict_ragged(const double *params, const int64_t *par_off,
+                               const int32_t *n_pl, const double *t, const int64_t *obs_off,
+                               int64_t n_sys, double t0, double *v_out, kc_stream stream) {
+  if (n_sys < 0) return fail(KC_ERR_ARG, "kc_rv_predict_ragged: n_sys < 0");
+  if (n_sys == 0) return ok();
+  if (!params || !par_off || !n_pl || !t || !obs_off || !v_out)
+    return fail(KC_ERR_ARG, "kc_rv_predict_ragged: NULL pointer");
+  if (((uintptr_t)params | (uintptr_t)t | (uintptr_t)v_out | (uintptr_t)par_off |
+       (uintptr_t)obs_off) & 7)
+    return fail(KC_ERR_ARG, "kc_rv_predict_ragged: pointer not 8-byte aligned");
+  if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_rv_predict_ragged: t0 must be finite");
+  return cuda_status(kc::launch_predict_ragged(params, par_off, n_pl, t, obs_off, n_sys, t0,
+                                               v_out, reinterpret_cast<cudaStream_t>(stream)),
+                     "kc_rv_predict_ragged");
 }
 
 kc_status kc_kepler_solve(const void *M, const void *e, int64_t n, kc_mode mode, void *E_out,

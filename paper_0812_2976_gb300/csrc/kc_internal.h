@@ -60,4 +60,9 @@ Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 int obs_tile_for(Kind kind, int n_obs);
 
+// Thread-local error reporting of the C ABI (kc_api.cu).
+kc_status fail(kc_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+kc_status ok();
+kc_status cuda_status(cudaError_t e, const char *what);
+
 }  // namespace kc

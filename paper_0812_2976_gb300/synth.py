@@ -244,3 +244,43 @@ def subset_ragged(w: RaggedWorkload, idx: np.ndarray) -> RaggedWorkload:
     return RaggedWorkload(n_pl, par_off, w.params[pcols], w.truth[pcols],
                           obs_off, w.t[ocols], w.sigma[ocols], w.noise[ocols],
                           w.t0, w.jitter)
+
+
+def pad_ragged(w: RaggedWorkload, v_obs: np.ndarray, n_pl: Optional[int] = None,
+               n_obs: Optional[int] = None):
+    """The same batch padded to a uniform size: every system gets n_pl
+    planets (the added ones with K = 0, so they contribute nothing) and n_obs
+    observations (the added ones with sigma = inf, i.e. zero weight).
+    Returns (padded workload, padded v_obs)."""
+    J = int(w.n_pl.max()) if n_pl is None else int(n_pl)
+    cnt = np.diff(w.obs_off)
+    N = int(cnt.max()) if n_obs is None else int(n_obs)
+    S = w.n_sys
+    npar = 5 * J + 1
+    params = np.zeros((S, npar))
+    truth = np.zeros((S, npar))
+    params[:, 0:5 * J:5] = 1.0                # P = 1 d for the empty planets
+    truth[:, 0:5 * J:5] = 1.0
+    for Jo in np.unique(w.n_pl):
+        idx = np.nonzero(w.n_pl == Jo)[0]
+        cols = w.par_off[idx, None] + np.arange(5 * Jo + 1)[None, :]
+        params[idx, :5 * Jo] = w.params[cols[:, :5 * Jo]]
+        params[idx, -1] = w.params[cols[:, -1]]
+        truth[idx, :5 * Jo] = w.truth[cols[:, :5 * Jo]]
+        truth[idx, -1] = w.truth[cols[:, -1]]
+    t = np.empty((S, N))
+    sg = np.full((S, N), np.inf)
+    vv = np.zeros((S, N))
+    nz = np.zeros((S, N))
+    k = np.arange(N)[None, :]
+    valid = k < cnt[:, None]
+    src = w.obs_off[:-1, None] + np.minimum(k, np.maximum(cnt[:, None] - 1, 0))
+    has = cnt[:, None] > 0
+    t[:] = np.where(has, w.t[np.minimum(src, max(w.t.size - 1, 0))], EPOCH)
+    sg[valid] = w.sigma[src[valid]]
+    vv[valid] = v_obs[src[valid]]
+    nz[valid] = w.noise[src[valid]]
+    out = RaggedWorkload(np.full(S, J, np.int32), np.arange(S + 1, dtype=np.int64) * npar,
+                         params.ravel(), truth.ravel(), np.arange(S + 1, dtype=np.int64) * N,
+                         t.ravel(), sg.ravel(), nz.ravel(), w.t0, w.jitter)
+    return out, vv.ravel()

@@ -337,3 +337,30 @@ def test_gradient_circular_closed_form(oracle_mod):
     assert np.isclose(g[0, 5], np.sum(2 * wk * r), rtol=1e-12)
     assert np.isclose(g[0, 0], np.sum(2 * wk * r * -K * np.sin(ph) * (-TWO_PI * t / P ** 2)),
                       rtol=1e-11)
+
+
+def test_ragged_predict_matches_uniform(oracle_mod):
+    rng = np.random.default_rng(16)
+    rows = [_random_systems(rng, 1, J)[0] for J in (1, 3, 2)]
+    n_obs = [5, 0, 9]
+    t = np.sort(rng.uniform(2450000, 2452000, sum(n_obs)))
+    par = np.concatenate(rows)
+    par_off = np.concatenate([[0], np.cumsum([r.size for r in rows])])
+    obs_off = np.concatenate([[0], np.cumsum(n_obs)])
+    got = oracle_mod.predict_ragged(par, par_off, [1, 3, 2], t, obs_off)
+    for s, (r, J) in enumerate(zip(rows, (1, 3, 2))):
+        ts = t[obs_off[s]:obs_off[s + 1]]
+        if ts.size:
+            assert np.array_equal(got[obs_off[s]:obs_off[s + 1]], oracle_mod.predict(r, ts, J)[0])
+
+
+def test_infinite_uncertainty_is_zero_weight(oracle_mod):
+    rng = np.random.default_rng(17)
+    par = _random_systems(rng, 3, 2)
+    t = np.sort(rng.uniform(0, 500, 20))
+    v = rng.normal(0, 20, 20)
+    sig = rng.uniform(1, 5, 20)
+    base = oracle_mod.chi2(par, t, v, sig, 2)
+    t2 = np.append(t, 600.0)
+    out = oracle_mod.chi2(par, t2, np.append(v, 1e3), np.append(sig, np.inf), 2)
+    assert np.array_equal(out, base)
