@@ -57,11 +57,15 @@ def parse_args():
     ap.add_argument("--config", type=int, default=1, choices=[1, 2, 4],
                     help="1: paper-shaped batch (default), 2: 2^20-system sweep, "
                          "4: ragged batch (forward + gradient, one persistent launch)")
+    ap.add_argument("--n-sys", type=int, default=None,
+                    help="smaller batch of the same distribution (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the built-in tile heuristic instead of the autotuner")
     ap.add_argument("--tile", default=None,
                     help="pin threads_per_system,block for the mixed chi2 kernel")
+    ap.add_argument("--no-grad", action="store_true",
+                    help="config 4: time the forward plan only")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 / grid-sweep side measurements")
     return ap.parse_args()
@@ -248,8 +252,8 @@ def run_kc(args):
     kc._lib.load()
 
     # each rank its own batch of the same shape (a shard of a larger sweep)
-    w = synth.uniform(args.config, seed=synth.SEED_BASE + args.config + 1000 * rank
-                      if rank else None)
+    w = synth.uniform(args.config, n_sys=args.n_sys,
+                      seed=synth.SEED_BASE + args.config + 1000 * rank if rank else None)
     P = torch.tensor(w.params, device=dev)
     T = torch.tensor(w.t, device=dev)
     S = torch.tensor(w.sigma, device=dev)
@@ -421,7 +425,8 @@ def run_kc_ragged(args):
     from paper_0812_2976_gb300 import build, synth
     build.build()
     kc._lib.load()
-    w = synth.ragged(seed=None if rank == 0 else synth.SEED_BASE + 4 + 1000 * rank)
+    w = synth.ragged(n_sys=args.n_sys or synth.RAGGED_N_SYS,
+                     seed=None if rank == 0 else synth.SEED_BASE + 4 + 1000 * rank)
     stream = torch.cuda.current_stream(dev)
     T = torch.tensor(w.t, device=dev)
     S = torch.tensor(w.sigma, device=dev)
@@ -432,10 +437,12 @@ def run_kc_ragged(args):
     evals = w.evals()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=True)
+    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=not args.no_grad)
     plan.set_observations(T, V, S)
     shape = plan.autotune(P) if not args.no_tune else None
-    chi, grad = plan.run(P)
+    want_grad = not args.no_grad
+    res = plan.run(P)
+    chi, grad = res if want_grad else (res, None)
     for _ in range(max(args.warmup, 3)):
         plan.run(P, chi, grad)
     torch.cuda.synchronize(dev)
@@ -454,39 +461,21 @@ def run_kc_ragged(args):
         t_sum = float(tt.item())
     value = evals * args.steps * world / t_sum
 
-    # forward only, and the padded uniform-size baseline (same kernel, every
-    # system padded to n_pl = 6 with K = 0 and n_obs = 1024 with zero weight)
-    fplan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed")
-    fplan.set_observations(T, V, S)
-    if not args.no_tune:
-        fplan.autotune(P)
-    fchi = fplan.run(P)
-    fwd_s = time_steps(lambda: fplan.run(P, fchi), args.steps, stream, flush)
-    del fplan
-    pw, pv = synth.pad_ragged(w, V.cpu().numpy(), n_pl=6, n_obs=1024)
-    pplan = kc.RaggedPlan(pw.obs_off, pw.n_pl, mode="mixed", want_grad=True)
-    pT, pV, pS = (torch.tensor(pw.t, device=dev), torch.tensor(pv, device=dev),
-                  torch.tensor(pw.sigma, device=dev))
-    pplan.set_observations(pT, pV, pS)
-    PP = torch.tensor(pw.params, device=dev)
-    if not args.no_tune:
-        pplan.autotune(PP)
-    pchi, pgrad = pplan.run(PP)
-    pad_steps = max(3, args.steps // 4)
-    pad_s = time_steps(lambda: pplan.run(PP, pchi, pgrad), pad_steps, stream, flush)
-    del pplan, pT, pV, pS
-
+    extras = {}
+    if not args.no_extras:
+        extras = ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev)
     # end to end: host parameters in, host chi2 + gradient out
     hP = torch.tensor(w.params).pin_memory()
     hchi = torch.empty_like(chi, device="cpu").pin_memory()
-    hgrad = torch.empty_like(grad, device="cpu").pin_memory()
+    hgrad = torch.empty_like(grad, device="cpu").pin_memory() if want_grad else None
     dP = torch.empty_like(P)
 
     def e2e_step():
         dP.copy_(hP, non_blocking=True)
         plan.run(dP, chi, grad)
         hchi.copy_(chi, non_blocking=True)
-        hgrad.copy_(grad, non_blocking=True)
+        if want_grad:
+            hgrad.copy_(grad, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -494,7 +483,8 @@ def run_kc_ragged(args):
     if rank != 0:
         return
     line = {
-        "metric": "planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)",
+        "metric": ("planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)"
+                   if want_grad else "planet-obs evals/s (chi2, ragged n_pl 1-6, n_obs 16-1024)"),
         "value": value, "unit": "planet-obs evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_sum / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -503,17 +493,13 @@ def run_kc_ragged(args):
                    "n_obs_total": int(w.obs_off[-1]), "l2": "flushed between steps",
                    "launch": {"block": shape[0], "ctas_per_sm": shape[1], "how": "autotuned"}
                    if shape else "default"},
-        "forward_only": {"value": evals / (fwd_s / args.steps), "unit": "planet-obs evals/s"},
-        "padded_baseline": {"value": evals / (pad_s / pad_steps),
-                            "unit": "planet-obs evals/s (useful)",
-                            "padded_evals": int(pw.n_sys * 6 * 1024),
-                            "ms_per_step": 1e3 * pad_s / pad_steps},
         "e2e": {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
                 "h2d_bytes_per_step": hP.numel() * 8,
-                "d2h_bytes_per_step": (hchi.numel() + hgrad.numel()) * 4},
+                "d2h_bytes_per_step": (hchi.numel() + (hgrad.numel() if want_grad else 0)) * 4},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()
@@ -523,13 +509,48 @@ def run_kc_ragged(args):
                                      sub.obs_off) + sub.noise
         t0c = time.perf_counter()
         oracle.chi2_ragged(sub.params, sub.par_off, sub.n_pl, sub.t, vsub, sub.sigma,
-                           sub.obs_off, grad=True)
+                           sub.obs_off, grad=want_grad)
         el = time.perf_counter() - t0c
         line["cpu_baseline"] = {"value": sub.evals() / el, "unit": "planet-obs evals/s",
                                 "cores": oracle.max_threads(), "kind": "oracle",
                                 "sample": f"{idx.size} systems (every {idx[1] - idx[0]}th), "
-                                          f"chi2 + gradient, {el:.1f} s wall"}
+                                          f"chi2{' + gradient' if want_grad else ''}, "
+                                          f"{el:.1f} s wall"}
     print(json.dumps(line), flush=True)
+
+
+def ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev):
+    """Forward-only plan, and the padded uniform-size baseline: the same
+    kernel with every system padded to n_pl = 6 (K = 0) and n_obs = 1024
+    (zero weight), throughput counted in useful evaluations."""
+    import torch
+    out = {}
+    fplan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed")
+    fplan.set_observations(T, V, S)
+    if not args.no_tune:
+        fplan.autotune(P)
+    fchi = fplan.run(P)
+    fwd_s = time_steps(lambda: fplan.run(P, fchi), args.steps, stream, flush)
+    out["forward_only"] = {"value": evals / (fwd_s / args.steps), "unit": "planet-obs evals/s"}
+    del fplan
+    pw, pv = synth.pad_ragged(w, V.cpu().numpy(), n_pl=6, n_obs=1024)
+    pplan = kc.RaggedPlan(pw.obs_off, pw.n_pl, mode="mixed", want_grad=not args.no_grad)
+    pT, pV, pS = (torch.tensor(pw.t, device=dev), torch.tensor(pv, device=dev),
+                  torch.tensor(pw.sigma, device=dev))
+    pplan.set_observations(pT, pV, pS)
+    PP = torch.tensor(pw.params, device=dev)
+    if not args.no_tune:
+        pplan.autotune(PP)
+    res = pplan.run(PP)
+    pchi, pgrad = res if not args.no_grad else (res, None)
+    pad_steps = max(3, args.steps // 4)
+    pad_s = time_steps(lambda: pplan.run(PP, pchi, pgrad), pad_steps, stream, flush)
+    out["padded_baseline"] = {"value": evals / (pad_s / pad_steps),
+                              "unit": "planet-obs evals/s (useful)",
+                              "padded_evals": int(pw.n_sys * 6 * 1024),
+                              "ms_per_step": 1e3 * pad_s / pad_steps}
+    del pplan
+    return out
 
 
 def main():

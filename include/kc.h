@@ -172,11 +172,12 @@ kc_status kc_plan_set_observations(kc_plan *plan, const double *t,
 
 /* chi2_out [n_sys] (float for KC_MIXED, double for KC_FP64) and, for a plan
  * created with want_grad, grad_out laid out like the packed parameters
- * (same type), else NULL.  The first run on a stream captures the queue
- * reset and the kernel into a CUDA graph; later runs on that stream replay
- * it (with the new pointers).  When `stream` is itself being captured the
- * two operations are recorded into the caller's graph instead.  Runs of
- * one plan must not overlap on the device (they share the work queue). */
+ * (same type), else NULL.  The first run captures the queue reset and the
+ * kernel into a CUDA graph (on a stream private to the plan); every run
+ * launches that graph on `stream`, retargeted to the given pointers.  When
+ * `stream` is itself being captured the two operations are recorded into
+ * the caller's graph instead.  Runs of one plan must not overlap on the
+ * device (they share the work queue). */
 kc_status kc_plan_run(kc_plan *plan, const double *params, void *chi2_out,
                       void *grad_out, kc_stream stream);
 
@@ -194,7 +195,7 @@ void kc_plan_destroy(kc_plan *plan);
 
 /* Launch shape of the uniform-batch kernels: each system is handled by
  * threads_per_system consecutive threads (a power of two, 1..block; at most
- * 32 for the gradient kernel), `block` threads per CTA (64..256, a multiple
+ * 32 for the gradient kernel), `block` threads per CTA (32..256, a multiple
  * of 32 and of threads_per_system). */
 typedef struct kc_tile {
     int32_t threads_per_system;

@@ -36,6 +36,7 @@ kc_status ok() {
 
 kc_status cuda_status(cudaError_t e, const char *what) {
   if (e == cudaSuccess) return ok();
+  cudaGetLastError();   // a failed API call leaves its error as the "last" one: clear it
   return fail(KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -282,7 +283,7 @@ kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
 
 bool tile_ok(kc_kernel kernel, const kc_tile &t) {
   const int G = t.threads_per_system, B = t.block;
-  if (B < 64 || B > 256 || (B & 31)) return false;
+  if (B < 32 || B > 256 || (B & 31)) return false;
   if (G < 1 || G > B || (G & (G - 1)) || (B % G)) return false;
   if (kernel == KC_KERNEL_GRAD && G > 32) return false;
   return true;
@@ -359,7 +360,7 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   float best_t = 1e30f;
   Tile best_tile = kc::default_tile(kind, n_sys, n_pl, n_obs);
   cudaError_t err = cudaSuccess;
-  for (int B : {128, 256}) {
+  for (int B : {32, 64, 128, 256}) {
     for (int G = 1; G <= B; G <<= 1) {
       const kc_tile cand{G, B};
       if (!tile_ok(kernel, cand)) continue;

@@ -32,7 +32,7 @@ struct kc_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t kernel_node = nullptr;
-  cudaStream_t graph_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;      // private stream the graph is captured on
   const double *g_params = nullptr;
   void *g_chi2 = nullptr, *g_grad = nullptr;
   std::mutex mu;
@@ -46,10 +46,11 @@ struct kc_plan {
     exec = nullptr;
     graph = nullptr;
     kernel_node = nullptr;
-    graph_stream = nullptr;
   }
   void release() {
     drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     for (void *p : {(void *)d_obs_off, (void *)d_par_off, (void *)d_order, (void *)d_n_pl,
                     (void *)d_t_ref, d_obs_a, d_obs_b, (void *)d_queue})
       if (p) cudaFree(p);
@@ -67,8 +68,12 @@ kc_status launch_direct(kc_plan *p, const double *params, void *chi2, void *grad
   return cuda_status(e, "kc_plan_run");
 }
 
-kc_status capture(kc_plan *p, const double *params, void *chi2, void *grad, cudaStream_t st) {
+// Records the queue reset and the kernel into a graph on the plan's private
+// stream (the caller's stream may be the legacy default stream, which cannot
+// be captured); the graph is then launched on whatever stream runs the plan.
+kc_status capture(kc_plan *p, const double *params, void *chi2, void *grad) {
   p->drop_graph();
+  cudaStream_t st = p->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: begin capture");
   cudaError_t e1 = cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), st);
@@ -100,7 +105,6 @@ kc_status capture(kc_plan *p, const double *params, void *chi2, void *grad, cuda
   p->graph = g;
   p->exec = ex;
   p->kernel_node = kn;
-  p->graph_stream = st;
   p->g_params = params;
   p->g_chi2 = chi2;
   p->g_grad = grad;
@@ -192,6 +196,7 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
   alloc(&p->d_obs_a, obs_bytes_a);
   alloc(&p->d_obs_b, obs_bytes_b);
   alloc((void **)&p->d_queue, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaGetLastError();
     p->release();
@@ -258,8 +263,8 @@ kc_status kc_plan_run(kc_plan *plan, const double *params, void *chi2_out, void 
   cudaError_t e = cudaStreamIsCapturing(st, &cap);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: stream");
   if (cap != cudaStreamCaptureStatusNone) return launch_direct(plan, params, chi2_out, grad_out, st);
-  if (!plan->exec || plan->graph_stream != st) {
-    kc_status s = capture(plan, params, chi2_out, grad_out, st);
+  if (!plan->exec) {
+    kc_status s = capture(plan, params, chi2_out, grad_out);
     if (s != KC_OK) return s;
   } else if (plan->g_params != params || plan->g_chi2 != chi2_out || plan->g_grad != grad_out) {
     kc_status s = retarget(plan, params, chi2_out, grad_out);

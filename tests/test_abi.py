@@ -105,7 +105,7 @@ def test_tile_table_host_logic(lib):
     assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
     assert (t.threads_per_system, t.block) == default
     # inadmissible tiles are refused
-    for bad in ((3, 128), (64, 32), (256, 128), (64, 256)):
+    for bad in ((3, 128), (64, 32), (256, 128), (64, 256), (8, 16)):
         kern = 1 if bad == (64, 256) else 0
         assert lib.kc_set_tile(kern, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
     assert lib.kc_get_tile(0, 1, 4096, 0, 256, ctypes.byref(t)) == 1
