@@ -63,7 +63,7 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true",
                     help="use the built-in tile heuristic instead of the autotuner")
     ap.add_argument("--tile", default=None,
-                    help="pin threads_per_system,block for the mixed chi2 kernel")
+                    help="pin threads_per_system,block[,split] for the mixed chi2 kernel")
     ap.add_argument("--no-grad", action="store_true",
                     help="config 4: time the forward plan only")
     ap.add_argument("--no-extras", action="store_true",
@@ -266,8 +266,8 @@ def run_kc(args):
 
     tile_kind = "heuristic"
     if args.tile:
-        g, b = (int(x) for x in args.tile.split(","))
-        kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, (g, b))
+        kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs,
+                       tuple(int(x) for x in args.tile.split(",")))
         tile_kind = "pinned"
     tile = kc.kc_get_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs)
     if not args.no_tune and not args.tile:
@@ -381,7 +381,8 @@ def run_kc(args):
         "data": "synthetic",
         "config": {"workload": w.shape.name, "n_sys": w.n_sys, "n_pl": w.n_pl,
                    "n_obs": w.n_obs, "per_rank": True, "l2": "flushed between steps",
-                   "tile": {"threads_per_system": tile[0], "block": tile[1], "how": tile_kind}},
+                   "tile": {"threads_per_system": tile[0], "block": tile[1],
+                            "split": tile[2], "how": tile_kind}},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": args.steps,

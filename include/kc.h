@@ -196,10 +196,15 @@ void kc_plan_destroy(kc_plan *plan);
 /* Launch shape of the uniform-batch kernels: each system is handled by
  * threads_per_system consecutive threads (a power of two, 1..block; at most
  * 32 for the gradient kernel), `block` threads per CTA (32..256, a multiple
- * of 32 and of threads_per_system). */
+ * of 32 and of threads_per_system).  split = 1 (mixed chi2 only) runs a
+ * separate preparation pass first: every per-(system, planet) constant and
+ * the converted observations go to stream-ordered scratch from a library
+ * memory pool, and the main kernel (programmatic dependent launch) only
+ * reads them, which pays off for small batches. */
 typedef struct kc_tile {
     int32_t threads_per_system;
     int32_t block;
+    int32_t split;
 } kc_tile;
 
 typedef enum kc_kernel { KC_KERNEL_CHI2 = 0, KC_KERNEL_GRAD = 1 } kc_kernel;

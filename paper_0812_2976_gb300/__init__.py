@@ -218,7 +218,8 @@ def _kernel(kernel) -> int:
 
 def kc_autotune(params, t, v_obs, sigma, kernel="chi2", mode="mixed", stream=None):
     """Time every admissible tile on this problem, keep the fastest for
-    problems of its size class; returns ((threads_per_system, block), ms)."""
+    problems of its size class; returns ((threads_per_system, block, split),
+    ms)."""
     params = _dev_f64("params", params, 2)
     t, v_obs, sigma = _obs(t, v_obs, sigma)
     best = _lib.KcTile()
@@ -228,26 +229,28 @@ def kc_autotune(params, t, v_obs, sigma, kernel="chi2", mode="mixed", stream=Non
                                sigma.data_ptr(), params.shape[0], n_planets(params), t.numel(),
                                _kernel(kernel), _mode(mode), ctypes.byref(best),
                                ctypes.byref(ms), _stream(stream)), "kc_autotune")
-    return (best.threads_per_system, best.block), ms.value
+    return (best.threads_per_system, best.block, best.split), ms.value
 
 
 def kc_set_tile(kernel, mode, n_sys: int, n_pl: int, n_obs: int, tile=None) -> None:
-    """Pin (threads_per_system, block) for a size class; None restores the default."""
+    """Pin (threads_per_system, block[, split]) for a size class; None
+    restores the default."""
     lib = _lib.load()
     ptr = None
     if tile is not None:
-        ptr = ctypes.byref(_lib.KcTile(int(tile[0]), int(tile[1])))
+        split = int(tile[2]) if len(tile) > 2 else 0
+        ptr = ctypes.byref(_lib.KcTile(int(tile[0]), int(tile[1]), split))
     _lib.check(lib.kc_set_tile(_kernel(kernel), _mode(mode), n_sys, n_pl, n_obs, ptr),
                "kc_set_tile")
 
 
 def kc_get_tile(kernel, mode, n_sys: int, n_pl: int, n_obs: int):
-    """(threads_per_system, block) the library would launch for this problem."""
+    """(threads_per_system, block, split) the library would launch."""
     lib = _lib.load()
     t = _lib.KcTile()
     _lib.check(lib.kc_get_tile(_kernel(kernel), _mode(mode), n_sys, n_pl, n_obs,
                                ctypes.byref(t)), "kc_get_tile")
-    return t.threads_per_system, t.block
+    return t.threads_per_system, t.block, t.split
 
 
 class RaggedPlan:

@@ -30,7 +30,8 @@ KC_KERNEL_CHI2, KC_KERNEL_GRAD = 0, 1
 
 class KcTile(ctypes.Structure):
     """struct kc_tile of include/kc.h."""
-    _fields_ = [("threads_per_system", ctypes.c_int32), ("block", ctypes.c_int32)]
+    _fields_ = [("threads_per_system", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("split", ctypes.c_int32)]
 
 
 _tile_p = ctypes.POINTER(KcTile)

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -38,6 +39,39 @@ kc_status cuda_status(cudaError_t e, const char *what) {
   if (e == cudaSuccess) return ok();
   cudaGetLastError();   // a failed API call leaves its error as the "last" one: clear it
   return fail(KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+}  // namespace
+
+// One memory pool per device for the library's stream-ordered scratch; it
+// keeps up to 256 MiB cached between calls so repeated calls do not go back
+// to the driver.
+cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it == g_pools.end()) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&pool, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = 256ull << 20;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      g_pools[dev] = pool;
+    } else {
+      pool = it->second;
+    }
+  }
+  return cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 256, pool, st);
 }
 
 }  // namespace kc
@@ -281,11 +315,13 @@ kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
   return mode == KC_FP64 ? kc::Kind::GradF64 : kc::Kind::GradMixed;
 }
 
-bool tile_ok(kc_kernel kernel, const kc_tile &t) {
+bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
   const int G = t.threads_per_system, B = t.block;
   if (B < 32 || B > 256 || (B & 31)) return false;
   if (G < 1 || G > B || (G & (G - 1)) || (B % G)) return false;
   if (kernel == KC_KERNEL_GRAD && G > 32) return false;
+  if (t.split != 0 && (t.split != 1 || kernel != KC_KERNEL_CHI2 || mode != KC_MIXED))
+    return false;
   return true;
 }
 
@@ -303,8 +339,8 @@ kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_p
     kc::g_tiles.erase(key);
     return ok();
   }
-  if (!tile_ok(kernel, *tile)) return fail(KC_ERR_ARG, "kc_set_tile: inadmissible tile");
-  kc::g_tiles[key] = Tile{tile->threads_per_system, tile->block, 0};
+  if (!tile_ok(kernel, mode, *tile)) return fail(KC_ERR_ARG, "kc_set_tile: inadmissible tile");
+  kc::g_tiles[key] = Tile{tile->threads_per_system, tile->block, 0, tile->split};
   return ok();
 }
 
@@ -317,6 +353,7 @@ kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_p
   const Tile t = kc::choose_tile(kind_of(kernel, mode), n_sys, n_pl, n_obs);
   tile->threads_per_system = t.G;
   tile->block = t.block;
+  tile->split = t.split;
   return ok();
 }
 
@@ -359,17 +396,20 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   };
   float best_t = 1e30f;
   Tile best_tile = kc::default_tile(kind, n_sys, n_pl, n_obs);
+  const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
+  const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
+  for (int split = 0; split <= 1; ++split)
   for (int B : {32, 64, 128, 256}) {
     for (int G = 1; G <= B; G <<= 1) {
-      const kc_tile cand{G, B};
-      if (!tile_ok(kernel, cand)) continue;
+      const kc_tile cand{G, B, split};
+      if (!tile_ok(kernel, mode, cand)) continue;
       if (n_obs > 0 && G > n_obs) continue;
-      Tile tile{G, B, kc::obs_tile_for(kind, n_obs)};
+      Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
       err = launch(tile);                       // warm-up (and smem attribute)
       if (err != cudaSuccess) break;
       float tmin = 1e30f;
-      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+      for (int rep = 0; rep < 5 && err == cudaSuccess; ++rep) {
         cudaEventRecord(e0, s);
         err = launch(tile);
         cudaEventRecord(e1, s);
@@ -379,6 +419,9 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
         tmin = ms < tmin ? ms : tmin;
       }
       if (err != cudaSuccess) break;
+      if (verbose)
+        fprintf(stderr, "kc_autotune: kind %d n_sys %lld G %3d block %3d split %d: %9.2f us\n",
+                (int)kind, (long long)n_sys, G, B, split, 1e3 * tmin);
       if (tmin < best_t) {
         best_t = tmin;
         best_tile = tile;
@@ -399,6 +442,7 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   if (best) {
     best->threads_per_system = best_tile.G;
     best->block = best_tile.block;
+    best->split = best_tile.split;
   }
   if (best_ms) *best_ms = best_t;
   return ok();

@@ -15,6 +15,7 @@
 // and the per-planet constants are computed once per (system, planet) in
 // FP64 and kept in shared memory.  Partial chi2 of the G threads are
 // combined with warp shuffles (and shared memory when G > 32).
+#include <algorithm>
 #include <cmath>
 
 #include "kc_device.cuh"
@@ -73,9 +74,23 @@ __device__ inline double inv_variance(double sigma, double jitter2) {
 // warps so that the double-precision setup runs on every SM sub-partition.
 __device__ inline int setup_slot(int tid, int nwarps) { return (tid & 31) * nwarps + (tid >> 5); }
 
-template <int J>
+// Prepared inputs of the split variant: per-(system, planet) constants,
+// per-system gamma (NaN if invalid) and converted observations, written by
+// prep_mixed_kernel into stream-ordered scratch.
+struct MixedPrep {
+  const PlanetF *pl;     // [n_sys * n_pl]
+  const float *gam;      // [n_sys]
+  const float4 *obs;     // [n_obs] (tau_hi, tau_lo, v_hi, v_lo)
+  const float *w;        // [n_obs]
+};
+
+// PRE = false: each CTA computes its planets' constants (FP64) and converts
+// the observations itself.  PRE = true (split variant): both come from
+// prep_mixed_kernel, launched just before with programmatic dependent
+// launch; the CTA waits for it, then only copies.
+template <int J, bool PRE>
 __global__ void __launch_bounds__(256, 2)
-chi2_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ out,
+chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__restrict__ out,
                   float *__restrict__ resid_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int block = blockDim.x;
@@ -95,17 +110,31 @@ chi2_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ out,
   const double dref = t_ref - a.t0;
   const float jit2 = d2f(a.jitter2);
 
-  // per-(system, planet) constants, once, in FP64 (Eqs. 4/6 phase offset)
-  for (int i = setup_slot(tid, nwarps); i < ST * J; i += block) {
-    const int sl = i / J, j = i - sl * J;
-    const int64_t s = sys0 + sl;
-    PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, dref);
-    pl_s[i] = q;
-  }
-  for (int i = tid; i < ST; i += block) {
-    const int64_t s = sys0 + i;
-    gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
+  if (PRE) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int i = tid; i < ST * J; i += block) {
+      const int64_t s = sys0 + i / J;
+      PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (s < a.n_sys) q = prep.pl[sys0 * J + i];
+      pl_s[i] = q;
+    }
+    for (int i = tid; i < ST; i += block) {
+      const int64_t s = sys0 + i;
+      gam_s[i] = s < a.n_sys ? prep.gam[s] : 0.0f;
+    }
+  } else {
+    // per-(system, planet) constants, once, in FP64 (Eqs. 4/6 phase offset)
+    for (int i = setup_slot(tid, nwarps); i < ST * J; i += block) {
+      const int sl = i / J, j = i - sl * J;
+      const int64_t s = sys0 + sl;
+      PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, dref);
+      pl_s[i] = q;
+    }
+    for (int i = tid; i < ST; i += block) {
+      const int64_t s = sys0 + i;
+      gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
+    }
   }
 
   const int sl = tid / G, c = tid - sl * G;
@@ -119,13 +148,18 @@ chi2_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ out,
     __syncthreads();
     // stage: tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jit^2)
     for (int k = tid; k < nk; k += block) {
-      float th, tl, vh, vl;
-      split_d(a.t[k0 + k] - t_ref, th, tl);
-      split_d(a.v[k0 + k], vh, vl);
-      obs_s[k] = make_float4(th, tl, vh, vl);
-      const float sg = d2f(a.sigma[k0 + k]);
-      const float var = __fmaf_rn(sg, sg, jit2);
-      w_s[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+      if (PRE) {
+        obs_s[k] = prep.obs[k0 + k];
+        w_s[k] = prep.w[k0 + k];
+      } else {
+        float th, tl, vh, vl;
+        split_d(a.t[k0 + k] - t_ref, th, tl);
+        split_d(a.v[k0 + k], vh, vl);
+        obs_s[k] = make_float4(th, tl, vh, vl);
+        const float sg = d2f(a.sigma[k0 + k]);
+        const float var = __fmaf_rn(sg, sg, jit2);
+        w_s[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+      }
     }
     __syncthreads();
     const float gam = gam_s[sl];
@@ -178,6 +212,37 @@ chi2_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ out,
     // 0 * gamma turns an invalid system into NaN even when n_obs == 0
     out[s] = kahan_value(acc) + 0.0f * gam_s[sl];
     if (resid_out) resid_out[s] = rmax;
+  }
+}
+
+// Split variant, first pass: every per-(system, planet) setup, gamma and
+// observation conversion of the batch, spread over the whole grid (so the
+// FP64 setup runs at full pipe occupancy instead of at each CTA's start).
+__global__ void __launch_bounds__(256)
+prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ gam,
+                  float4 *__restrict__ obs, float *__restrict__ w) {
+  // let the dependent main kernel be scheduled as this grid drains; its
+  // griddepcontrol.wait still waits for this grid's completion
+  asm volatile("griddepcontrol.launch_dependents;");
+  const int J = a.n_pl, npar = 5 * J + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+  const float jit2 = d2f(a.jitter2);
+  for (int64_t i = tid; i < a.n_sys * J; i += nth) {
+    const int64_t s = i / J;
+    pl[i] = planet_setup_mixed(a.params + s * npar + 5 * (i - s * J), dref);
+  }
+  for (int64_t s = tid; s < a.n_sys; s += nth) gam[s] = d2f(system_gamma(a.params + s * npar, J));
+  for (int64_t k = tid; k < a.n_obs; k += nth) {
+    float th, tl, vh, vl;
+    split_d(a.t[k] - t_ref, th, tl);
+    split_d(a.v[k], vh, vl);
+    obs[k] = make_float4(th, tl, vh, vl);
+    const float sg = d2f(a.sigma[k]);
+    const float var = __fmaf_rn(sg, sg, jit2);
+    w[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
   }
 }
 
@@ -370,16 +435,69 @@ size_t smem_chi2_f64(int n_pl, const Tile &t) {
     default: return cudaErrorInvalidValue; \
   }
 
+size_t mixed_prep_bytes(int64_t n_sys, int n_pl, int n_obs) {
+  return align_up(sizeof(PlanetF) * n_sys * n_pl, 256) + align_up(sizeof(float) * n_sys, 256) +
+         align_up(sizeof(float4) * n_obs, 256) + align_up(sizeof(float) * n_obs, 256);
+}
+
+cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, void *scratch,
+                                       float *out, float *resid, cudaStream_t st) {
+  unsigned char *base = static_cast<unsigned char *>(scratch);
+  PlanetF *pl = reinterpret_cast<PlanetF *>(base);
+  base += align_up(sizeof(PlanetF) * a.n_sys * a.n_pl, 256);
+  float *gam = reinterpret_cast<float *>(base);
+  base += align_up(sizeof(float) * a.n_sys, 256);
+  float4 *obs = reinterpret_cast<float4 *>(base);
+  base += align_up(sizeof(float4) * a.n_obs, 256);
+  float *w = reinterpret_cast<float *>(base);
+  const int64_t items = std::max<int64_t>(a.n_sys * a.n_pl, std::max<int64_t>(a.n_obs, 1));
+  int prep_grid = (int)std::min<int64_t>((items + 255) / 256, 152 * 8);
+  prep_mixed_kernel<<<prep_grid, 256, 0, st>>>(a, pl, gam, obs, w);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  MixedPrep prep{pl, gam, obs, w};
+  const size_t smem = smem_chi2_mixed(a.n_pl, tile);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(a.n_sys, tile.block / tile.G));
+  cfg.blockDim = dim3(tile.block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define KC_LAUNCH(JJ)                                                                      \
+  err = set_smem(chi2_mixed_kernel<JJ, true>, smem);                                       \
+  if (err == cudaSuccess)                                                                  \
+    err = cudaLaunchKernelEx(&cfg, chi2_mixed_kernel<JJ, true>, a, prep, tile.G, tile.obs_tile, \
+                             out, resid);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out, float *resid,
                               cudaStream_t st) {
+  if (tile.split) {
+    // stream-ordered scratch from the library's pool (kept cached between calls)
+    void *scratch = nullptr;
+    cudaError_t err = scratch_alloc(&scratch, mixed_prep_bytes(a.n_sys, a.n_pl, a.n_obs), st);
+    if (err != cudaSuccess) return err;
+    err = launch_chi2_mixed_prepared(a, tile, scratch, out, resid, st);
+    cudaError_t err2 = cudaFreeAsync(scratch, st);
+    return err != cudaSuccess ? err : err2;
+  }
   const size_t smem = smem_chi2_mixed(a.n_pl, tile);
   const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  const MixedPrep none{nullptr, nullptr, nullptr, nullptr};
   cudaError_t err = cudaSuccess;
-#define KC_LAUNCH(JJ)                                                                  \
-  err = set_smem(chi2_mixed_kernel<JJ>, smem);                                         \
-  if (err == cudaSuccess)                                                              \
-    chi2_mixed_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
-                                                          resid);
+#define KC_LAUNCH(JJ)                                                                   \
+  err = set_smem(chi2_mixed_kernel<JJ, false>, smem);                                   \
+  if (err == cudaSuccess)                                                               \
+    chi2_mixed_kernel<JJ, false><<<grid, tile.block, smem, st>>>(a, none, tile.G,         \
+                                                                 tile.obs_tile, out, resid);
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;

@@ -4,6 +4,8 @@
 // replay, launch-shape autotuning).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -166,12 +168,16 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
     par_off[s + 1] = par_off[s] + 5 * (int64_t)n_pl[s] + 1;
     work[s] = (int64_t)n_pl[s] * std::max<int64_t>(n, 1);
   }
-  // longest processing time first: big systems start early, small ones fill
-  // the tail
+  // Planet count first (descending), then work (descending): warps running
+  // at the same time mostly execute the same unrolled body (one per planet
+  // count), and the queue still ends with the smallest systems (1 planet,
+  // few observations), which fill the tail.
   std::vector<int64_t> order(n_sys);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t a, int64_t b) { return work[a] > work[b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (n_pl[a] != n_pl[b]) return n_pl[a] > n_pl[b];
+    return work[a] > work[b];
+  });
 
   kc_plan *p = new kc_plan();
   cudaGetDevice(&p->device);
@@ -288,6 +294,8 @@ kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out, 
   cudaEventCreate(&e1);
   float best = 1e30f;
   int best_block = plan->block, best_k = std::max(1, plan->grid / sms);
+  const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
+  const bool verbose = env && env[0] == '1';
   kc_status status = KC_OK;
   for (int b : {64, 128, 256}) {
     const int kmax = kc::ragged_max_blocks_per_sm(plan->mode, plan->grad, b);
@@ -305,6 +313,8 @@ kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out, 
         cudaEventElapsedTime(&ms, e0, e1);
         tmin = std::min(tmin, ms);
       }
+      if (verbose)
+        fprintf(stderr, "kc_plan_autotune: block %3d ctas/SM %d: %9.2f us\n", b, k, 1e3 * tmin);
       if (status == KC_OK && tmin < best) {
         best = tmin;
         best_block = b;

@@ -6,8 +6,10 @@
 // observations, Sec. 4.1).  A ragged batch (n_obs 16..1024, n_pl 1..6 per
 // system) varies the work per system by ~400x, so a static split of
 // systems over threads leaves most SMs idle at the end.  Here:
-//  - a plan orders the systems by decreasing work (n_pl * n_obs; longest
-//    processing time first) and keeps that order on the device;
+//  - a plan orders the systems by planet count, then by decreasing work
+//    (n_pl * n_obs), and keeps that order on the device: big systems start
+//    first, the smallest fill the tail, and warps running together mostly
+//    share one unrolled body;
 //  - each warp of a persistent grid takes the next system from an atomic
 //    counter and evaluates it with its 32 lanes over the observations, the
 //    planet count being warp-uniform so the planet loop is fully unrolled
@@ -178,9 +180,20 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
   float g[GRAD ? NP : 1];
 #pragma unroll
   for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.0f;
+  // the next observation is loaded while this one is evaluated
+  float4 o_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 wt_next = make_float2(0.f, 0.f);
+  if (lane < n) {
+    o_next = oa[o0 + lane];
+    wt_next = ob[o0 + lane];
+  }
   for (int k = lane; k < n; k += 32) {
-    const float4 o = oa[o0 + k];
-    const float2 wt = ob[o0 + k];
+    const float4 o = o_next;
+    const float2 wt = wt_next;
+    if (k + 32 < n) {
+      o_next = oa[o0 + k + 32];
+      wt_next = ob[o0 + k + 32];
+    }
     float sEj[J], cEj[J];
     Kahan V = {0.0f, 0.0f};
 #pragma unroll
@@ -239,8 +252,11 @@ __device__ __forceinline__ void body_f64(const RPlanetD *pl, double gam, const O
   double g[GRAD ? NP : 1];
 #pragma unroll
   for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.0;
+  ObsR64 o_next = {0.0, 0.0, 0.0, 0.0};
+  if (lane < n) o_next = od[o0 + lane];
   for (int k = lane; k < n; k += 32) {
-    const ObsR64 o = od[o0 + k];
+    const ObsR64 o = o_next;
+    if (k + 32 < n) o_next = od[o0 + k + 32];
     double sEj[J], cEj[J];
     double V = gam;
 #pragma unroll

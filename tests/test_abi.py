@@ -95,17 +95,20 @@ def test_tile_table_host_logic(lib):
     # default heuristic for the paper-shaped batch
     assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
     assert t.block in (64, 128, 256) and t.threads_per_system >= 1
-    default = (t.threads_per_system, t.block)
+    default = (t.threads_per_system, t.block, t.split)
     # pin, read back, same size class (power-of-two bucket), then remove
-    pin = _lib.KcTile(16, 128)
+    pin = _lib.KcTile(16, 128, 1)
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(pin)) == 0
     assert lib.kc_get_tile(0, 1, 5000, 4, 300, ctypes.byref(t)) == 0
-    assert (t.threads_per_system, t.block) == (16, 128)
+    assert (t.threads_per_system, t.block, t.split) == (16, 128, 1)
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
     assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
-    assert (t.threads_per_system, t.block) == default
+    assert (t.threads_per_system, t.block, t.split) == default
     # inadmissible tiles are refused
-    for bad in ((3, 128), (64, 32), (256, 128), (64, 256), (8, 16)):
-        kern = 1 if bad == (64, 256) else 0
+    for bad in ((3, 128, 0), (64, 32, 0), (256, 128, 0), (64, 256, 0), (8, 16, 0), (8, 64, 2)):
+        kern = 1 if bad[:2] == (64, 256) else 0
         assert lib.kc_set_tile(kern, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
+    # the split variant exists for the mixed chi2 kernel only
+    assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
+    assert lib.kc_set_tile(1, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
     assert lib.kc_get_tile(0, 1, 4096, 0, 256, ctypes.byref(t)) == 1
