@@ -112,6 +112,34 @@ kc_status kc_chi2_grad(const double *params, const double *t,
                        double jitter, kc_mode mode, void *chi2_out,
                        void *grad_out, kc_stream stream);
 
+/* Allocation-free form of kc_chi2_eval_mixed (with t0 and jitter as in
+ * kc_chi2_eval_ex).  The paper has no counterpart: this exists for callers
+ * that must not allocate device memory while they evaluate (all memory
+ * reserved up front, or no allocator calls allowed at that point).  It runs
+ * the two-pass variant of the mixed kernel with its intermediate data in a
+ * fixed array of KC_NOALLOC_SCRATCH_BYTES compiled into libkc.so, which every
+ * GPU that loads the library keeps until the process exits; the call itself
+ * never calls cudaMalloc, cudaFree or a memory pool.
+ *  - Limit: 32 B per (system, planet), 4 B per system and 20 B per
+ *    observation (each part rounded up to 256 B) must fit in the array,
+ *    e.g. 4096 systems x 4 planets x 256 observations uses ~540 KB.  Larger
+ *    problems return KC_ERR_ARG with the byte counts, before any launch.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents:
+ *    calls that overlap on the GPU (different streams, or other host
+ *    threads) race and must be serialised by the caller.  Nothing in the
+ *    array needs to start at zero: each call writes all it reads.
+ *  - Results equal kc_chi2_eval_mixed's within rounding (same arithmetic,
+ *    possibly a different summation order). */
+#define KC_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+kc_status kc_chi2_eval_mixed_noalloc(const double *params, const double *t,
+                                     const double *v_obs, const double *sigma,
+                                     int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                                     double t0, double jitter, float *out,
+                                     float *max_kepler_resid, kc_stream stream);
+
 /* -------------------------------------------------------- model, Kepler */
 
 /* FP64 model velocities V(t_k) = gamma + sum_j v_j(t_k) (Eq. 2):

@@ -22,6 +22,7 @@ from ._lib import KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
 __all__ = [
     "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
+    "kc_chi2_eval_mixed_noalloc",
     "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
     "RaggedPlan", "chi2", "n_planets", "library_path",
 ]
@@ -134,6 +135,24 @@ def kc_chi2_eval_mixed(params, t, v_obs, sigma, out=None, max_kepler_resid=None,
         n_planets(params), t.numel(), out.data_ptr(), _ptr(resid), _stream(stream)),
         "kc_chi2_eval_mixed")
     return (out, resid) if resid is not None else out
+
+
+def kc_chi2_eval_mixed_noalloc(params, t, v_obs, sigma, out, t0: float = 0.0,
+                               jitter: float = 0.0, max_kepler_resid=None, stream=None):
+    """Mixed chi2 without any device allocation by the library
+    (kc_chi2_eval_mixed_noalloc): for callers that must not allocate while
+    evaluating.  ``out`` (float32 [n_sys]) and the optional float32
+    ``max_kepler_resid`` must be provided by the caller; intermediate data
+    go to a fixed array inside libkc.so, so problems are limited to
+    KC_NOALLOC_SCRATCH_BYTES of it and overlapping calls must be serialised."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_eval_mixed_noalloc(
+        params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), params.shape[0],
+        n_planets(params), t.numel(), float(t0), float(jitter), out.data_ptr(),
+        _ptr(max_kepler_resid), _stream(stream)), "kc_chi2_eval_mixed_noalloc")
+    return out
 
 
 def kc_chi2_grad(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,

@@ -42,6 +42,8 @@ SIGNATURES = {
     "kc_chi2_eval_mixed": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _d, _d, _st]),
     "kc_chi2_eval_ex": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _i32,
                                _d, _d, _st]),
+    "kc_chi2_eval_mixed_noalloc": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _d,
+                                          _d, _st]),
     "kc_chi2_grad": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _i32, _d,
                             _d, _st]),
     "kc_rv_predict": (_i32, [_d, _d, _i64, _i32, _i32, _f64, _d, _st]),
