@@ -224,11 +224,14 @@ void kc_plan_destroy(kc_plan *plan);
 /* Launch shape of the uniform-batch kernels: each system is handled by
  * threads_per_system consecutive threads (a power of two, 1..block; at most
  * 32 for the gradient kernel), `block` threads per CTA (32..256, a multiple
- * of 32 and of threads_per_system).  split = 1 (mixed chi2 only) runs a
- * separate preparation pass first: every per-(system, planet) constant and
- * the converted observations go to stream-ordered scratch from a library
- * memory pool, and the main kernel (programmatic dependent launch) only
- * reads them, which pays off for small batches. */
+ * of 32 and of threads_per_system).  split (mixed chi2 only) selects a
+ * two-pass variant for small batches: a preparation pass first writes every
+ * per-(system, planet) constant and the converted observations to
+ * stream-ordered scratch from a library memory pool, then the main kernel
+ * (programmatic dependent launch) only reads them.  split = 1: CTAs as
+ * above.  split = 2: one warp per (system, chunk of observations);
+ * threads_per_system = 32 x chunks (32..1024), any block; the last warp of a
+ * system merges the chunks' partial sums in chunk order. */
 typedef struct kc_tile {
     int32_t threads_per_system;
     int32_t block;

@@ -318,10 +318,12 @@ kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
 bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
   const int G = t.threads_per_system, B = t.block;
   if (B < 32 || B > 256 || (B & 31)) return false;
+  if (t.split < 0 || t.split > 2) return false;
+  if (t.split != 0 && (kernel != KC_KERNEL_CHI2 || mode != KC_MIXED)) return false;
+  if (t.split == 2)     // one warp per chunk: G = 32 x chunks, chunks <= 32
+    return G >= 32 && G <= 1024 && !(G & (G - 1));
   if (G < 1 || G > B || (G & (G - 1)) || (B % G)) return false;
   if (kernel == KC_KERNEL_GRAD && G > 32) return false;
-  if (t.split != 0 && (t.split != 1 || kernel != KC_KERNEL_CHI2 || mode != KC_MIXED))
-    return false;
   return true;
 }
 
@@ -399,12 +401,13 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
   const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
-  for (int split = 0; split <= 1; ++split)
+  for (int split = 0; split <= 2; ++split)
   for (int B : {32, 64, 128, 256}) {
-    for (int G = 1; G <= B; G <<= 1) {
+    for (int G = 1; G <= (split == 2 ? 1024 : B); G <<= 1) {
       const kc_tile cand{G, B, split};
       if (!tile_ok(kernel, mode, cand)) continue;
       if (n_obs > 0 && G > n_obs) continue;
+      if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
       Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
       err = launch(tile);                       // warm-up (and smem attribute)
       if (err != cudaSuccess) break;

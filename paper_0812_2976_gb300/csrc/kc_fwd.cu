@@ -218,9 +218,10 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
 // Split variant, first pass: every per-(system, planet) setup, gamma and
 // observation conversion of the batch, spread over the whole grid (so the
 // FP64 setup runs at full pipe occupancy instead of at each CTA's start).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(64)
 prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ gam,
-                  float4 *__restrict__ obs, float *__restrict__ w) {
+                  float4 *__restrict__ obs, float *__restrict__ w,
+                  unsigned *__restrict__ counters) {
   // let the dependent main kernel be scheduled as this grid drains; its
   // griddepcontrol.wait still waits for this grid's completion
   asm volatile("griddepcontrol.launch_dependents;");
@@ -234,7 +235,10 @@ prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ g
     const int64_t s = i / J;
     pl[i] = planet_setup_mixed(a.params + s * npar + 5 * (i - s * J), dref);
   }
-  for (int64_t s = tid; s < a.n_sys; s += nth) gam[s] = d2f(system_gamma(a.params + s * npar, J));
+  for (int64_t s = tid; s < a.n_sys; s += nth) {
+    gam[s] = d2f(system_gamma(a.params + s * npar, J));
+    if (counters) counters[s] = 0u;
+  }
   for (int64_t k = tid; k < a.n_obs; k += nth) {
     float th, tl, vh, vl;
     split_d(a.t[k] - t_ref, th, tl);
@@ -243,6 +247,94 @@ prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ g
     const float sg = d2f(a.sigma[k]);
     const float var = __fmaf_rn(sg, sg, jit2);
     w[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+  }
+}
+
+// Split variant 2: one warp per (system, chunk of observations).  A system's
+// G threads form G/32 warps, each taking a contiguous chunk of the
+// observations, so the batch becomes many small independent units (no CTA
+// barrier, no per-CTA staging) and the grid's tail is short.  Each warp
+// writes its partial chi2 (a Kahan pair) and max residual; the last warp of
+// a system to finish (per-system counter, zeroed by the preparation pass)
+// merges the partials in chunk order, so the result does not depend on the
+// order in which warps finish.
+struct ChunkScratch {
+  float2 *part;          // [n_sys * chunks] (big, small)
+  float *part_resid;     // [n_sys * chunks]
+  unsigned *count;       // [n_sys]
+};
+
+template <int J>
+__global__ void __launch_bounds__(256)
+chi2_mixed_chunk_kernel(UniformArgs a, MixedPrep prep, ChunkScratch cs, int chunks,
+                        float *__restrict__ out, float *__restrict__ resid_out) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int64_t unit = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (unit >= a.n_sys * chunks) return;               // whole warps only
+  const int64_t s = unit / chunks;
+  const int c = (int)(unit - s * chunks);
+  const int len = (a.n_obs + chunks - 1) / chunks;
+  const int k0 = c * len, k1 = min(a.n_obs, k0 + len);
+  PlanetF q[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) q[j] = prep.pl[s * J + j];
+  const float gam = prep.gam[s];
+  const bool want_resid = resid_out != nullptr;
+  Kahan acc = {0.0f, 0.0f};
+  float rmax = 0.0f;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float4 o = prep.obs[k];
+    const float wk = prep.w[k];
+    Kahan V = {0.0f, 0.0f};
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const float M = mean_anomaly_mixed(o.x, o.y, q[j]);
+      float sE, cE;
+      const float E = kepler_f32(M, q[j].e, sE, cE);
+      if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
+      kahan_add(V, velocity_mixed(q[j], sE, cE));
+    }
+    const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+    kahan_add(acc, wk * r * r);
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+    rmax = fmaxf(rmax, shfl_xor(rmax, m));
+  }
+  unsigned done = 0;
+  if (lane == 0) {
+    cs.part[unit] = make_float2(acc.big, acc.small);
+    cs.part_resid[unit] = rmax;
+    __threadfence();                                    // partial visible before the count
+    done = atomicAdd(cs.count + s, 1u);
+  }
+  done = __shfl_sync(0xffffffffu, done, 0);
+  if (done != (unsigned)(chunks - 1)) return;           // not the last chunk of s
+  __threadfence();
+  // merge the chunks' partials in chunk order (lane c holds chunk c)
+  Kahan m = {0.0f, 0.0f};
+  float rm = 0.0f;
+  if (lane < chunks) {
+    const float2 p = __ldcg(cs.part + s * chunks + lane);
+    m.big = p.x;
+    m.small = p.y;
+    rm = __ldcg(cs.part_resid + s * chunks + lane);
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    Kahan o = {__shfl_down_sync(0xffffffffu, m.big, d), __shfl_down_sync(0xffffffffu, m.small, d)};
+    const float ro = __shfl_down_sync(0xffffffffu, rm, d);
+    if ((lane & (2 * d - 1)) == 0 && lane + d < 32) {
+      kahan_merge(m, o);
+      rm = fmaxf(rm, ro);
+    }
+  }
+  if (lane == 0) {
+    out[s] = kahan_value(m) + 0.0f * gam;
+    if (resid_out) resid_out[s] = rm;
   }
 }
 
@@ -440,6 +532,17 @@ size_t mixed_prep_bytes(int64_t n_sys, int n_pl, int n_obs) {
          align_up(sizeof(float4) * n_obs, 256) + align_up(sizeof(float) * n_obs, 256);
 }
 
+size_t mixed_chunk_bytes(int64_t n_sys, int chunks) {
+  return align_up(sizeof(float2) * n_sys * chunks, 256) +
+         align_up(sizeof(float) * n_sys * chunks, 256) + align_up(sizeof(unsigned) * n_sys, 256);
+}
+
+size_t mixed_scratch_bytes(int64_t n_sys, int n_pl, int n_obs, const Tile &tile) {
+  size_t b = mixed_prep_bytes(n_sys, n_pl, n_obs);
+  if (tile.split == 2) b += mixed_chunk_bytes(n_sys, tile.G / 32);
+  return b;
+}
+
 cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, void *scratch,
                                        float *out, float *resid, cudaStream_t st) {
   unsigned char *base = static_cast<unsigned char *>(scratch);
@@ -450,13 +553,26 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
   float4 *obs = reinterpret_cast<float4 *>(base);
   base += align_up(sizeof(float4) * a.n_obs, 256);
   float *w = reinterpret_cast<float *>(base);
+  base += align_up(sizeof(float) * a.n_obs, 256);
+  const int chunks = tile.split == 2 ? tile.G / 32 : 0;
+  ChunkScratch cs{nullptr, nullptr, nullptr};
+  if (chunks > 0) {
+    cs.part = reinterpret_cast<float2 *>(base);
+    base += align_up(sizeof(float2) * a.n_sys * chunks, 256);
+    cs.part_resid = reinterpret_cast<float *>(base);
+    base += align_up(sizeof(float) * a.n_sys * chunks, 256);
+    cs.count = reinterpret_cast<unsigned *>(base);
+  }
+  // The setup is a chain of dependent FP64 operations on a pipe of ~2 lanes
+  // per SM per clock, so the items are spread thinly over every SM (64-thread
+  // CTAs, one item per thread) rather than packed into a few full CTAs.
   const int64_t items = std::max<int64_t>(a.n_sys * a.n_pl, std::max<int64_t>(a.n_obs, 1));
-  int prep_grid = (int)std::min<int64_t>((items + 255) / 256, 152 * 8);
-  prep_mixed_kernel<<<prep_grid, 256, 0, st>>>(a, pl, gam, obs, w);
+  const int prep_grid = (int)std::min<int64_t>((items + 63) / 64, 152 * 16);
+  prep_mixed_kernel<<<prep_grid, 64, 0, st>>>(a, pl, gam, obs, w, cs.count);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   MixedPrep prep{pl, gam, obs, w};
-  const size_t smem = smem_chi2_mixed(a.n_pl, tile);
+  const size_t smem = chunks > 0 ? 0 : smem_chi2_mixed(a.n_pl, tile);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid_for(a.n_sys, tile.block / tile.G));
   cfg.blockDim = dim3(tile.block);
@@ -467,6 +583,16 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (chunks > 0) {
+    const int64_t threads = a.n_sys * chunks * 32;
+    cfg.gridDim = dim3((unsigned)((threads + tile.block - 1) / tile.block));
+#define KC_LAUNCH(JJ) \
+  err = cudaLaunchKernelEx(&cfg, chi2_mixed_chunk_kernel<JJ>, a, prep, cs, chunks, out, resid);
+    KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+    if (err != cudaSuccess) return err;
+    return cudaGetLastError();
+  }
 #define KC_LAUNCH(JJ)                                                                      \
   err = set_smem(chi2_mixed_kernel<JJ, true>, smem);                                       \
   if (err == cudaSuccess)                                                                  \
@@ -483,7 +609,8 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out
   if (tile.split) {
     // stream-ordered scratch from the library's pool (kept cached between calls)
     void *scratch = nullptr;
-    cudaError_t err = scratch_alloc(&scratch, mixed_prep_bytes(a.n_sys, a.n_pl, a.n_obs), st);
+    cudaError_t err =
+        scratch_alloc(&scratch, mixed_scratch_bytes(a.n_sys, a.n_pl, a.n_obs, tile), st);
     if (err != cudaSuccess) return err;
     err = launch_chi2_mixed_prepared(a, tile, scratch, out, resid, st);
     cudaError_t err2 = cudaFreeAsync(scratch, st);

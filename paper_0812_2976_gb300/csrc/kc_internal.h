@@ -17,7 +17,7 @@ struct Tile {
   int G;
   int block;
   int obs_tile;
-  int split = 0;   // mixed chi2 only: separate preparation pass (see kc_fwd.cu)
+  int split = 0;   // mixed chi2 only: 1, 2 = two-pass variants (see kc_fwd.cu)
 };
 
 struct UniformArgs {
@@ -37,9 +37,10 @@ struct UniformArgs {
 cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st);
 
 // Forward chi2 (kc_fwd.cu).  launch_chi2_mixed_prepared runs the split
-// variant on caller-provided scratch of mixed_prep_bytes() bytes (256-byte
+// variant on caller-provided scratch of mixed_scratch_bytes() bytes (256-byte
 // aligned).
 size_t mixed_prep_bytes(int64_t n_sys, int n_pl, int n_obs);
+size_t mixed_scratch_bytes(int64_t n_sys, int n_pl, int n_obs, const Tile &tile);
 cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, void *scratch,
                                        float *out, float *resid, cudaStream_t st);
 cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,

@@ -81,6 +81,8 @@ extern "C" kc_status kc_chi2_eval_mixed_noalloc(const double *params, const doub
   // call writes every byte the main kernel then reads.
   const kc::UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
   kc::Tile tile = kc::choose_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);
+  if (tile.G > tile.block || tile.split == 2)
+    tile = kc::default_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);
   tile.split = 1;
   return kc::cuda_status(kc::launch_chi2_mixed_prepared(a, tile, scratch, out, max_kepler_resid,
                                                         reinterpret_cast<cudaStream_t>(stream)),

@@ -108,7 +108,12 @@ def test_tile_table_host_logic(lib):
     for bad in ((3, 128, 0), (64, 32, 0), (256, 128, 0), (64, 256, 0), (8, 16, 0), (8, 64, 2)):
         kern = 1 if bad[:2] == (64, 256) else 0
         assert lib.kc_set_tile(kern, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
-    # the split variant exists for the mixed chi2 kernel only
+    # split = 2: threads_per_system = 32 x chunks, may exceed the block
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(512, 64, 2))) == 0
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(16, 64, 2))) == 1
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(2048, 64, 2))) == 1
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
+    # the split variants exist for the mixed chi2 kernel only
     assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
     assert lib.kc_set_tile(1, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
     assert lib.kc_get_tile(0, 1, 4096, 0, 256, ctypes.byref(t)) == 1

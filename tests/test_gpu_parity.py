@@ -277,7 +277,8 @@ def test_rv_predict_vs_oracle(kc, oracle_mod):
         assert np.max(np.abs(got - ref)) <= 1e-9
 
 
-@pytest.mark.parametrize("tile", [(8, 64, 1), (32, 32, 1), (64, 256, 1), (1, 128, 1)])
+@pytest.mark.parametrize("tile", [(8, 64, 1), (32, 32, 1), (64, 256, 1), (1, 128, 1),
+                                  (32, 128, 2), (128, 64, 2), (256, 256, 2), (1024, 32, 2)])
 def test_split_variant_matches_oracle(kc, oracle_mod, tile):
     """The two-pass (preparation + main) variant of the mixed kernel, pinned
     through the tile table, on the paper-shaped batch and on a ragged tail."""
