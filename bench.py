@@ -120,10 +120,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_0812_2976_gb300 import dist as kdist
+    return kdist.env()
 
 
 def peaks():
@@ -301,9 +299,8 @@ def run_kc(args):
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
     t_sum = sum(kernel_ms) / 1e3
     if world > 1:
-        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_sum = float(tt.item())
+        from paper_0812_2976_gb300 import dist as kdist
+        t_sum = kdist.max_over_ranks(t_sum, device=dev)
     value = evals * args.steps * world / t_sum
     ms_per_step = 1e3 * t_sum / args.steps
 
@@ -457,9 +454,8 @@ def run_kc_ragged(args):
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     if world > 1:
-        tt = torch.tensor([t_sum], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_sum = float(tt.item())
+        from paper_0812_2976_gb300 import dist as kdist
+        t_sum = kdist.max_over_ranks(t_sum, device=dev)
     value = evals * args.steps * world / t_sum
 
     extras = {}

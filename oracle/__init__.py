@@ -47,38 +47,59 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
-        d = ctypes.POINTER(ctypes.c_double)
-        i64 = ctypes.c_int64
-        i32p = ctypes.POINTER(ctypes.c_int32)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.kco_set_threads.argtypes = [ctypes.c_int]
-        lib.kco_max_threads.restype = ctypes.c_int
-        lib.kco_mean_anomaly.restype = ctypes.c_double
-        lib.kco_mean_anomaly.argtypes = [ctypes.c_double] * 4
-        lib.kco_kepler_E.restype = ctypes.c_double
-        lib.kco_kepler_E.argtypes = [ctypes.c_double, ctypes.c_double,
-                                     ctypes.POINTER(ctypes.c_int)]
-        lib.kco_true_anomaly.restype = ctypes.c_double
-        lib.kco_true_anomaly.argtypes = [ctypes.c_double, ctypes.c_double]
-        lib.kco_planet_velocity.restype = ctypes.c_double
-        lib.kco_planet_velocity.argtypes = [d, ctypes.c_double, ctypes.c_double]
-        lib.kco_chi2.restype = ctypes.c_int
-        lib.kco_chi2.argtypes = [d, d, d, d, i64, ctypes.c_int, i64,
-                                 ctypes.c_double, ctypes.c_double, d, d]
-        lib.kco_chi2_ragged.restype = ctypes.c_int
-        lib.kco_chi2_ragged.argtypes = [d, i64p, i32p, d, d, d, i64p, i64,
-                                        ctypes.c_double, ctypes.c_double, d, d]
-        lib.kco_predict.restype = ctypes.c_int
-        lib.kco_predict.argtypes = [d, d, i64, ctypes.c_int, i64,
-                                    ctypes.c_double, d]
-        lib.kco_predict_ragged.restype = ctypes.c_int
-        lib.kco_predict_ragged.argtypes = [d, i64p, i32p, d, i64p, i64, ctypes.c_double, d]
-        lib.kco_kepler_batch.argtypes = [d, d, i64, d, i32p]
-        lib.kco_mean_anomaly_batch.argtypes = [d, ctypes.c_double, d, d, i64, d]
-        lib.kco_true_anomaly_batch.argtypes = [d, d, i64, d]
-        _lib = lib
-        return lib
+        _lib = bind(ctypes.CDLL(build()))
+        return _lib
+
+
+def compile_variant(source: str, path: str):
+    """Compile another version of the oracle's C source (used by the tests
+    that plant mistakes to check that the pins catch them) and return it
+    bound like the real one; install it with ``use(lib)``."""
+    src = path + ".c"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", *_CFLAGS, src, "-o", path, "-lm"], check=True)
+    return bind(ctypes.CDLL(path))
+
+
+def use(lib) -> None:
+    """Make every function of this module call ``lib`` (None: the real one)."""
+    global _lib
+    _lib = lib
+
+
+def bind(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    d = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.kco_set_threads.argtypes = [ctypes.c_int]
+    lib.kco_max_threads.restype = ctypes.c_int
+    lib.kco_mean_anomaly.restype = ctypes.c_double
+    lib.kco_mean_anomaly.argtypes = [ctypes.c_double] * 4
+    lib.kco_kepler_E.restype = ctypes.c_double
+    lib.kco_kepler_E.argtypes = [ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(ctypes.c_int)]
+    lib.kco_true_anomaly.restype = ctypes.c_double
+    lib.kco_true_anomaly.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.kco_planet_velocity.restype = ctypes.c_double
+    lib.kco_planet_velocity.argtypes = [d, ctypes.c_double, ctypes.c_double]
+    lib.kco_chi2.restype = ctypes.c_int
+    lib.kco_chi2.argtypes = [d, d, d, d, i64, ctypes.c_int, i64,
+                             ctypes.c_double, ctypes.c_double, d, d]
+    lib.kco_chi2_ragged.restype = ctypes.c_int
+    lib.kco_chi2_ragged.argtypes = [d, i64p, i32p, d, d, d, i64p, i64,
+                                    ctypes.c_double, ctypes.c_double, d, d]
+    lib.kco_predict.restype = ctypes.c_int
+    lib.kco_predict.argtypes = [d, d, i64, ctypes.c_int, i64,
+                                ctypes.c_double, d]
+    lib.kco_predict_ragged.restype = ctypes.c_int
+    lib.kco_predict_ragged.argtypes = [d, i64p, i32p, d, i64p, i64, ctypes.c_double, d]
+    lib.kco_kepler_batch.argtypes = [d, d, i64, d, i32p]
+    lib.kco_mean_anomaly_batch.argtypes = [d, ctypes.c_double, d, d, i64, d]
+    lib.kco_true_anomaly_batch.argtypes = [d, d, i64, d]
+    return lib
 
 
 def _f64(a) -> np.ndarray:
