@@ -9,8 +9,10 @@ velocities, residuals, per-system reduction) through the C ABI.
 
 Timing: W warm-up steps, then K timed steps bracketed by a barrier and
 device synchronisation.  Each step's kernel is timed with CUDA events on the
-launching stream; a 256 MiB buffer is rewritten between steps (outside the
-events) so every step starts with a cold L2.  Multi-GPU (torchrun): every
+launching stream.  Between steps (outside the events) a 256 MiB buffer is
+written and then a second 256 MiB buffer is read, so every step starts with
+a cold L2 holding no dirty lines (otherwise the write-back of the flush
+buffer lands inside the next timed kernel).  Multi-GPU (torchrun): every
 rank evaluates its own batch of the same shape (weak scaling, no
 data-path collective); the slowest rank's time is reported.
 
@@ -46,6 +48,73 @@ FALLBACK_SM_MHZ = 2070.0
 #   residual + weighted square + chi2 Kahan sum 10 (shared by n_pl planets).
 def mixed_flops_per_eval(n_pl: int) -> float:
     return 17 + 2 + 3 * 22 + 27 + 10 + 8 + 4 + 10.0 / n_pl
+
+
+# FP64 path, FP64 FLOPs per planet-observation evaluation (FMA = 2), from its
+# algorithm: mean anomaly 14, sin/cos (Cody-Waite + Taylor) 41, Danby step
+# with a Newton reciprocal 30, last-step update 10, velocity with a Newton
+# reciprocal 16, accumulation 2 (the FP32 presolve is not counted).
+F64_FLOPS_PER_EVAL = 14 + 41 + 30 + 10 + 16 + 2
+# Measured FP64 FMA rate of this GPU per SM per clock.
+FP64_PER_SM_CLK = 1.8
+
+
+def sm_mhz_for_peaks():
+    pk, _ = peaks()
+    return pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
+
+
+def kepler_throughput(kc, dev, stream, n=1 << 24):
+    """Solutions of Kepler's equation per second (the paper's Table 2 also
+    reports this), FP32 and FP64, on n random (M, e) pairs, e <= 0.95."""
+    import torch
+    g = torch.Generator(device=dev).manual_seed(7)
+    M = (torch.rand(n, device=dev, generator=g, dtype=torch.float64) * 2 - 1) * 3.141592653589793
+    e = torch.rand(n, device=dev, generator=g, dtype=torch.float64) * 0.95
+    out = {}
+    for mode, Mx, ex in (("mixed", M.float(), e.float()), ("fp64", M, e)):
+        E = torch.empty_like(Mx)
+        for _ in range(3):
+            kc.kc_kepler_solve(Mx, ex, mode=mode, out=E, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            kc.kc_kepler_solve(Mx, ex, mode=mode, out=E, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        out["fp32" if mode == "mixed" else "fp64"] = 10 * n / (a.elapsed_time(b) / 1e3)
+    out["unit"] = "Kepler solutions/s"
+    return out
+
+
+def grid_sweep_throughput(kc, synth, dev, stream, args):
+    """Mixed chi2 on the 2^20-system sweep (config 2), autotuned."""
+    import torch
+    w = synth.uniform(2)
+    P = torch.tensor(w.params, device=dev)
+    T = torch.tensor(w.t, device=dev)
+    S = torch.tensor(w.sigma, device=dev)
+    V = kc.kc_rv_predict(torch.tensor(w.truth[None, :], device=dev), T)[0]
+    V += torch.tensor(w.noise, device=dev)
+    out = torch.empty(w.n_sys, dtype=torch.float32, device=dev)
+    if not args.no_tune:
+        kc.kc_autotune(P, T, V, S, kernel="chi2", mode="mixed", stream=stream)
+    for _ in range(2):
+        kc.kc_chi2_eval_mixed(P, T, V, S, out=out, stream=stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 5
+    a.record(stream)
+    for _ in range(steps):
+        kc.kc_chi2_eval_mixed(P, T, V, S, out=out, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    sec = a.elapsed_time(b) / 1e3 / steps
+    evals = w.n_sys * w.n_pl * w.n_obs
+    val = evals / sec
+    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    return {"value": val, "unit": "planet-obs evals/s", "ms_per_step": 1e3 * sec,
+            "n_sys": w.n_sys, "roofline_frac": val * mixed_flops_per_eval(w.n_pl) / 1e12 / peak,
+            "inputs": "176 MB of parameters > L2"}
 
 
 def parse_args():
@@ -258,7 +327,7 @@ def run_kc(args):
     truth = torch.tensor(w.truth[None, :], device=dev)
     V = kc.kc_rv_predict(truth, T, t0=w.t0)[0] + torch.tensor(w.noise, device=dev)
     out = torch.empty(w.n_sys, dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream(dev)
     evals = w.n_sys * w.n_pl * w.n_obs
 
@@ -353,8 +422,16 @@ def run_kc(args):
             b.record(stream)
         torch.cuda.synchronize(dev)
         f_s = sum(a.elapsed_time(b) for a, b in f_ev) / 1e3
-        extras["fp64"] = {"value": evals * len(f_ev) / f_s, "unit": "planet-obs evals/s",
-                          "ms_per_step": 1e3 * f_s / len(f_ev)}
+        f64_val = evals * len(f_ev) / f_s
+        f64_peak = 2 * FP64_PER_SM_CLK * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+        extras["fp64"] = {"value": f64_val, "unit": "planet-obs evals/s",
+                          "ms_per_step": 1e3 * f_s / len(f_ev),
+                          "roofline": {"bound": "fp64", "achieved": f64_val * F64_FLOPS_PER_EVAL
+                                       / 1e12, "peak": f64_peak, "unit": "TFLOP/s",
+                                       "frac": f64_val * F64_FLOPS_PER_EVAL / 1e12 / f64_peak,
+                                       "flops_per_eval": F64_FLOPS_PER_EVAL}}
+        extras["kepler_only"] = kepler_throughput(kc, dev, stream)
+        extras["grid_sweep"] = grid_sweep_throughput(kc, synth, dev, stream, args)
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
@@ -377,7 +454,7 @@ def run_kc(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+ds (mixed)",
         "data": "synthetic",
         "config": {"workload": w.shape.name, "n_sys": w.n_sys, "n_pl": w.n_pl,
-                   "n_obs": w.n_obs, "per_rank": True, "l2": "flushed between steps",
+                   "n_obs": w.n_obs, "per_rank": True, "l2": "flushed between steps (write 256 MiB, then read 256 MiB)",
                    "tile": {"threads_per_system": tile[0], "block": tile[1],
                             "split": tile[2], "how": tile_kind}},
         "roofline": roofline,
@@ -391,6 +468,21 @@ def run_kc(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+class L2Flush:
+    """Evicts L2 between timed steps: write one buffer larger than L2, then
+    read another, so no dirty line is left for the next kernel to write
+    back."""
+
+    def __init__(self, dev, nbytes=256 << 20):
+        import torch
+        self.a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.b = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+
+    def fill_(self, v):
+        self.a.fill_(v)
+        self.b.sum()
 
 
 def time_steps(fn, steps, stream, flush):
@@ -433,7 +525,7 @@ def run_kc_ragged(args):
     V += torch.tensor(w.noise, device=dev)
     P = torch.tensor(w.params, device=dev)
     evals = w.evals()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = L2Flush(dev)
 
     plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=not args.no_grad)
     plan.set_observations(T, V, S)
@@ -487,7 +579,7 @@ def run_kc_ragged(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+ds (mixed)", "data": "synthetic",
         "config": {"workload": "ragged", "n_sys": w.n_sys, "evals": evals,
-                   "n_obs_total": int(w.obs_off[-1]), "l2": "flushed between steps",
+                   "n_obs_total": int(w.obs_off[-1]), "l2": "flushed between steps (write 256 MiB, then read 256 MiB)",
                    "launch": {"block": shape[0], "ctas_per_sm": shape[1], "how": "autotuned"}
                    if shape else "default"},
         "e2e": {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",

@@ -106,6 +106,18 @@ __device__ __forceinline__ float rcp_fast(float x) {
   return y;
 }
 
+// 1/x in double for normal, finite x: the MUFU double-precision seed and
+// two Newton steps (error ~1 ulp).  IEEE division costs more FP64-pipe
+// instructions, which are the bound of the FP64 path.
+__device__ __forceinline__ double rcp_f64(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // sin and cos to about one ulp for |x| <= 8, on the FMA pipe.
 // Cody & Waite (1980) reduction x = q pi/2 + r, |r| <= pi/4, with pi/2 split
 // into two floats (q <= 5, so q * hi is exact inside the FMA), then the
@@ -136,6 +148,48 @@ __device__ __forceinline__ void sincos_accurate(float x, float &s, float &c) {
   const float c0 = swap ? sr : cr;
   s = __uint_as_float(__float_as_uint(s0) ^ ((q & 2u) << 30));
   c = __uint_as_float(__float_as_uint(c0) ^ (((q + 1u) & 2u) << 30));
+}
+
+// sin and cos in double precision for |x| <= 8: the same Cody & Waite
+// reduction (pi/2 as two doubles) and the Taylor series of sin to r^17
+// (truncation 8e-20 at pi/4) and of cos to r^16 (2e-18).  No branches, so
+// the FP64-pipe cost is fixed: 3 + 9 + 9 operations.
+constexpr double kRoundMagicD = 6755399441055744.0;           // 1.5 * 2^52
+constexpr double kTwoOverPiD = 0.6366197723675814;
+constexpr double kPiO2HiD = 1.5707963267948966;               // RN(pi/2)
+constexpr double kPiO2LoD = 6.123233995736766e-17;            // pi/2 - hi
+
+__device__ __forceinline__ void sincos_f64(double x, double &s, double &c) {
+  const double k = fma(x, kTwoOverPiD, kRoundMagicD);
+  const unsigned q = (unsigned)__double2loint(k);             // low bits: q mod 4
+  const double qf = k - kRoundMagicD;
+  double r = fma(-qf, kPiO2HiD, x);
+  r = fma(-qf, kPiO2LoD, r);
+  const double r2 = r * r;
+  double ps = fma(r2, 1.0 / 355687428096000.0, -1.0 / 1307674368000.0);   // 1/17!, -1/15!
+  ps = fma(r2, ps, 1.0 / 6227020800.0);                                    // 1/13!
+  ps = fma(r2, ps, -1.0 / 39916800.0);                                     // -1/11!
+  ps = fma(r2, ps, 1.0 / 362880.0);                                        // 1/9!
+  ps = fma(r2, ps, -1.0 / 5040.0);
+  ps = fma(r2, ps, 1.0 / 120.0);
+  ps = fma(r2, ps, -1.0 / 6.0);
+  const double sr = fma(r * r2, ps, r);
+  double pc = fma(r2, 1.0 / 20922789888000.0, -1.0 / 87178291200.0);     // 1/16!, -1/14!
+  pc = fma(r2, pc, 1.0 / 479001600.0);                                     // 1/12!
+  pc = fma(r2, pc, -1.0 / 3628800.0);                                      // -1/10!
+  pc = fma(r2, pc, 1.0 / 40320.0);
+  pc = fma(r2, pc, -1.0 / 720.0);
+  pc = fma(r2, pc, 1.0 / 24.0);
+  pc = fma(r2, pc, -0.5);
+  const double cr = fma(r2, pc, 1.0);
+  // quadrant swap and signs on the integer halves (keeps them off the FP64 pipe)
+  const bool swap = q & 1u;
+  const int sh = __double2hiint(sr), sl = __double2loint(sr);
+  const int ch = __double2hiint(cr), cl = __double2loint(cr);
+  const int s_hi = swap ? ch : sh, s_lo = swap ? cl : sl;
+  const int c_hi = swap ? sh : ch, c_lo = swap ? sl : cl;
+  s = __hiloint2double(s_hi ^ (int)((q & 2u) << 30), s_lo);
+  c = __hiloint2double(c_hi ^ (int)(((q + 1u) & 2u) << 30), c_lo);
 }
 
 // ------------------------------------------------ compensated sums
@@ -202,7 +256,7 @@ __device__ __forceinline__ double danby_delta_f64(double E, double M, double e, 
   const double h = 0.5 * f * es;
   const double D2 = fma(f1, f1, -h);
   const double Q = fma(f * f * f1, (e * (1.0 / 6.0)) * c, D2 * (D2 - h));
-  return -(f * D2 * D2) / (f1 * Q);
+  return -(f * D2 * D2) * rcp_f64(f1 * Q);
 }
 
 // Paper's starting guess (Sec. 4.3): E0 = M + 0.85 e sign(sin M); M is
@@ -245,7 +299,7 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
     Ef += danby_delta_f32(Ef, Mf, ef, sin_fast(Ef), cos_fast(Ef));
   const double E = f2d(Ef);
   double s, c;
-  sincos(E, &s, &c);
+  sincos_f64(E, s, c);
   const double d = danby_delta_f64(E, M, e, s, c);
   const double hd2 = 0.5 * d * d;
   sE = fma(d, c, fma(-hd2, s, s));
@@ -398,7 +452,7 @@ __device__ __forceinline__ float velocity_mixed(const PlanetF &q, float sE, floa
 
 __device__ __forceinline__ double velocity_f64(const PlanetD &q, double sE, double cE) {
   const double D = fma(-q.e, cE, 1.0);
-  return fma(q.A, cE - q.e, -(q.B * sE)) / D + q.C;
+  return fma(fma(q.A, cE - q.e, -(q.B * sE)), rcp_f64(D), q.C);
 }
 
 // ------------------------------------------------ warp helpers

@@ -468,9 +468,14 @@ __device__ inline double reduce_pi<double>(double M) {
 }
 template <>
 __device__ inline float reduce_pi<float>(float M) {
-  // reduce in double so that large |M| keeps its phase
-  const double m = (double)M;
-  return (float)(m - kTwoPi * rint(m * kInvTwoPi));
+  // Cody-Waite with 2 pi split into two floats (|M| < 2^22 on the fast path)
+  if (fabsf(M) <= 3.14159265f) return M;
+  if (!(fabsf(M) < 4194304.0f)) {                      // rare: reduce in double
+    const double m = (double)M;
+    return (float)(m - kTwoPi * rint(m * kInvTwoPi));
+  }
+  const float q = round_small(M * 0.159154943091895336f);
+  return __fmaf_rn(-q, -1.74845553e-7f, __fmaf_rn(-q, 6.28318548202514648f, M));
 }
 
 __global__ void kepler_f64_kernel(const double *__restrict__ M, const double *__restrict__ e,
