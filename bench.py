@@ -117,6 +117,40 @@ def grid_sweep_throughput(kc, synth, dev, stream, args):
             "inputs": "176 MB of parameters > L2"}
 
 
+def gradient_throughput(kc, synth, dev, stream, args):
+    """Config 3 (65536 systems, n_pl 3, n_obs 512, t0 = 2450000): chi2 and
+    its gradient in one adjoint launch, and the free-jitter log-likelihood
+    with its gradient, mixed precision."""
+    import torch
+    w = synth.uniform(3)
+    P = torch.tensor(w.params, device=dev)
+    T = torch.tensor(w.t, device=dev)
+    S = torch.tensor(w.sigma, device=dev)
+    V = kc.kc_rv_predict(torch.tensor(w.truth[None, :], device=dev), T, t0=w.t0)[0]
+    V += torch.tensor(w.noise, device=dev)
+    PJ = torch.cat([P, torch.full((w.n_sys, 1), 1.5, dtype=P.dtype, device=dev)], dim=1)
+    if not args.no_tune:
+        kc.kc_autotune(P, T, V, S, kernel="grad", mode="mixed", stream=stream)
+    evals = w.n_sys * w.n_pl * w.n_obs
+    out = {"n_sys": w.n_sys, "unit": "planet-obs evals/s"}
+    for name, fn in (("chi2_grad", lambda: kc.kc_chi2_grad(P, T, V, S, t0=w.t0, mode="mixed",
+                                                           stream=stream)),
+                     ("nll_grad", lambda: kc.kc_nll_grad(PJ, T, V, S, t0=w.t0, mode="mixed",
+                                                         stream=stream)),
+                     ("chi2_grad_fp64", lambda: kc.kc_chi2_grad(P, T, V, S, t0=w.t0,
+                                                                mode="fp64", stream=stream))):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2 if name.endswith("fp64") else 5
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = evals * reps / (a.elapsed_time(b) / 1e3)
+    return out
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,6 +466,7 @@ def run_kc(args):
                                        "flops_per_eval": F64_FLOPS_PER_EVAL}}
         extras["kepler_only"] = kepler_throughput(kc, dev, stream)
         extras["grid_sweep"] = grid_sweep_throughput(kc, synth, dev, stream, args)
+        extras["gradient"] = gradient_throughput(kc, synth, dev, stream, args)
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)

@@ -112,6 +112,28 @@ kc_status kc_chi2_grad(const double *params, const double *t,
                        double jitter, kc_mode mode, void *chi2_out,
                        void *grad_out, kc_stream stream);
 
+/* Free jitter: each system carries its own jitter sigma_j after gamma
+ * (params [n_sys][5*n_pl + 2]) and the statistic is the Gaussian negative
+ * log-likelihood whose exponent is Eq. 5's chi2 with that sigma_j,
+ *   nll = 1/2 sum_k [ r_k^2/(sigma_k^2 + sigma_j^2)
+ *                     + ln(2 pi (sigma_k^2 + sigma_j^2)) ],
+ * which, unlike chi2, has a finite optimum in sigma_j (the paper fixes
+ * sigma_j = 0 and keeps it as a variable, Sec. 2.2).  out [n_sys]: double
+ * for KC_FP64, float for KC_MIXED.  A non-positive or NaN variance makes the
+ * system NaN; an infinite one makes its nll infinite. */
+kc_status kc_nll_eval(const double *params, const double *t,
+                      const double *v_obs, const double *sigma, int64_t n_sys,
+                      int32_t n_pl, int32_t n_obs, double t0, kc_mode mode,
+                      void *out, kc_stream stream);
+
+/* nll and its gradient with respect to all 5*n_pl + 2 parameters (adjoint
+ * as kc_chi2_grad; d nll / d sigma_j = sigma_j sum_k w_k (1 - w_k r_k^2)
+ * with w_k = 1/(sigma_k^2 + sigma_j^2)).  nll_out may be NULL. */
+kc_status kc_nll_grad(const double *params, const double *t,
+                      const double *v_obs, const double *sigma, int64_t n_sys,
+                      int32_t n_pl, int32_t n_obs, double t0, kc_mode mode,
+                      void *nll_out, void *grad_out, kc_stream stream);
+
 /* Allocation-free form of kc_chi2_eval_mixed (with t0 and jitter as in
  * kc_chi2_eval_ex).  The paper has no counterpart: this exists for callers
  * that must not allocate device memory while they evaluate (all memory

@@ -88,6 +88,8 @@ def bind(lib):
     lib.kco_chi2.restype = ctypes.c_int
     lib.kco_chi2.argtypes = [d, d, d, d, i64, ctypes.c_int, i64,
                              ctypes.c_double, ctypes.c_double, d, d]
+    lib.kco_nll.restype = ctypes.c_int
+    lib.kco_nll.argtypes = [d, d, d, d, i64, ctypes.c_int, i64, ctypes.c_double, d, d]
     lib.kco_chi2_ragged.restype = ctypes.c_int
     lib.kco_chi2_ragged.argtypes = [d, i64p, i32p, d, d, d, i64p, i64,
                                     ctypes.c_double, ctypes.c_double, d, d]
@@ -186,6 +188,23 @@ def chi2(params, t, v, sigma, n_pl: int, t0: float = 0.0,
                           _p(g) if grad else None)
     if rc != 0:
         raise ValueError("oracle.chi2: bad sizes")
+    return (out, g) if grad else out
+
+
+def nll(params, t, v, sigma, n_pl: int, t0: float = 0.0, grad: bool = False):
+    """Negative log-likelihood with a free jitter per system (parameters
+    [n_sys, 5*n_pl+2]: planets, gamma, sigma_j):
+    1/2 sum_k [r_k^2/(sigma_k^2+sigma_j^2) + ln(2 pi (sigma_k^2+sigma_j^2))]."""
+    params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
+    n_par = 5 * n_pl + 2
+    params = params.reshape(-1, n_par)
+    n_sys = params.shape[0]
+    out = np.empty(n_sys)
+    g = np.empty((n_sys, n_par)) if grad else None
+    rc = _load().kco_nll(_p(params), _p(t), _p(v), _p(sigma), n_sys, int(n_pl), t.size,
+                         float(t0), _p(out), _p(g) if grad else None)
+    if rc != 0:
+        raise ValueError("oracle.nll: bad sizes")
     return (out, g) if grad else out
 
 

@@ -225,6 +225,58 @@ static double kco_system(const double *par, int n_pl, const double *t,
     return kco_sum_value(&chi2);
 }
 
+/* ------------------------------------------- free jitter, log-likelihood */
+
+/* Negative log-likelihood of one system whose jitter sigma_j is a free
+ * parameter, appended after gamma (5*n_pl + 2 values):
+ *   nll = 1/2 sum_k [ r_k^2/(sigma_k^2 + sigma_j^2) + ln(2 pi (sigma_k^2 + sigma_j^2)) ]
+ * (the Gaussian likelihood whose exponent is Eq. 5's chi2 with sigma_j
+ * included).  Gradient (when grad != NULL) with respect to all 5*n_pl + 2
+ * parameters; d nll / d sigma_j = sigma_j sum_k w_k (1 - w_k r_k^2). */
+static double kco_nll_system(const double *par, int n_pl, const double *t,
+                             const double *v, const double *sigma, int64_t n_obs,
+                             double t0, double *grad)
+{
+    int n_par = 5 * n_pl + 2;
+    double gamma = par[5 * n_pl], sj = par[5 * n_pl + 1];
+    kco_sum nll = {0.0, 0.0};
+    kco_sum gsum[5 * 16 + 2];
+    int j, q;
+    int64_t k;
+    int valid = isfinite(gamma) && isfinite(sj);
+    for (j = 0; j < n_pl; ++j) valid = valid && kco_planet_valid(par + 5 * j);
+    for (q = 0; q < n_par; ++q) { gsum[q].s = 0.0; gsum[q].c = 0.0; }
+    if (!valid) {
+        if (grad) for (q = 0; q < n_par; ++q) grad[q] = NAN;
+        return NAN;
+    }
+    for (k = 0; k < n_obs; ++k) {
+        double var = sigma[k] * sigma[k] + sj * sj;
+        double wk = 1.0 / var;
+        double V = gamma, r;
+        double g[16][5];
+        if (!(var > 0.0)) {
+            if (grad) for (q = 0; q < n_par; ++q) grad[q] = NAN;
+            return NAN;
+        }
+        for (j = 0; j < n_pl; ++j) {
+            if (grad) V += kco_planet_velocity_grad(par + 5 * j, t[k], t0, g[j]);
+            else      V += kco_planet_velocity(par + 5 * j, t[k], t0);
+        }
+        r = V - v[k];
+        kco_sum_add(&nll, 0.5 * (wk * r * r + log(KCO_TWO_PI * var)));
+        if (grad) {
+            double a = wk * r;
+            for (j = 0; j < n_pl; ++j)
+                for (q = 0; q < 5; ++q) kco_sum_add(&gsum[5 * j + q], a * g[j][q]);
+            kco_sum_add(&gsum[5 * n_pl], a);
+            kco_sum_add(&gsum[5 * n_pl + 1], sj * wk * (1.0 - wk * r * r));
+        }
+    }
+    if (grad) for (q = 0; q < n_par; ++q) grad[q] = kco_sum_value(&gsum[q]);
+    return kco_sum_value(&nll);
+}
+
 /* ------------------------------------------------------ public entry points */
 
 /* Uniform batch: all n_sys systems have n_pl planets and share the n_obs
@@ -241,6 +293,22 @@ int kco_chi2(const double *params, const double *t, const double *v,
     for (s = 0; s < n_sys; ++s)
         out[s] = kco_system(params + s * n_par, n_pl, t, v, sigma, n_obs, t0,
                             jitter, grad ? grad + s * n_par : NULL);
+    return 0;
+}
+
+/* Uniform batch with a free jitter per system: params [n_sys][5*n_pl+2],
+ * out [n_sys] negative log-likelihoods, grad (may be NULL) like params. */
+int kco_nll(const double *params, const double *t, const double *v,
+            const double *sigma, int64_t n_sys, int n_pl, int64_t n_obs,
+            double t0, double *out, double *grad)
+{
+    int64_t s;
+    int n_par = 5 * n_pl + 2;
+    if (n_pl < 1 || n_pl > 16 || n_obs < 0 || n_sys < 0) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (s = 0; s < n_sys; ++s)
+        out[s] = kco_nll_system(params + s * n_par, n_pl, t, v, sigma, n_obs, t0,
+                                grad ? grad + s * n_par : NULL);
     return 0;
 }
 

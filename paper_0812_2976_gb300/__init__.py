@@ -22,7 +22,7 @@ from ._lib import KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
 __all__ = [
     "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
-    "kc_chi2_eval_mixed_noalloc",
+    "kc_chi2_eval_mixed_noalloc", "kc_nll_eval", "kc_nll_grad", "nll",
     "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
     "RaggedPlan", "chi2", "n_planets", "library_path",
 ]
@@ -174,6 +174,51 @@ def kc_chi2_grad(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
         n_planets(params), t.numel(), float(t0), float(jitter), m, chi2_out.data_ptr(),
         grad_out.data_ptr(), _stream(stream)), "kc_chi2_grad")
     return chi2_out, grad_out
+
+
+def n_planets_nll(params: torch.Tensor) -> int:
+    """n_pl from a [n_sys, 5*n_pl+2] free-jitter parameter batch."""
+    n = params.shape[-1] - 2
+    if n <= 0 or n % 5:
+        raise ValueError("params must have 5*n_pl + 2 columns (planets, gamma, jitter)")
+    return n // 5
+
+
+def kc_nll_eval(params, t, v_obs, sigma, t0: float = 0.0, mode="mixed", out=None,
+                stream=None) -> torch.Tensor:
+    """Free-jitter negative log-likelihood [n_sys] (kc_nll_eval); params are
+    [n_sys, 5*n_pl+2] = planets, gamma, sigma_j."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    if out is None:
+        out = torch.empty(params.shape[0], dtype=torch.float64 if m == KC_FP64 else torch.float32,
+                          device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_nll_eval(params.data_ptr(), t.data_ptr(), v_obs.data_ptr(),
+                               sigma.data_ptr(), params.shape[0], n_planets_nll(params),
+                               t.numel(), float(t0), m, out.data_ptr(), _stream(stream)),
+               "kc_nll_eval")
+    return out
+
+
+def kc_nll_grad(params, t, v_obs, sigma, t0: float = 0.0, mode="mixed", nll_out=None,
+                grad_out=None, stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """(nll [n_sys], gradient [n_sys, 5*n_pl+2]) (kc_nll_grad)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    if nll_out is None:
+        nll_out = torch.empty(params.shape[0], dtype=dtype, device=params.device)
+    if grad_out is None:
+        grad_out = torch.empty(params.shape, dtype=dtype, device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_nll_grad(params.data_ptr(), t.data_ptr(), v_obs.data_ptr(),
+                               sigma.data_ptr(), params.shape[0], n_planets_nll(params),
+                               t.numel(), float(t0), m, nll_out.data_ptr(), grad_out.data_ptr(),
+                               _stream(stream)), "kc_nll_grad")
+    return nll_out, grad_out
 
 
 def kc_rv_predict(params, t, t0: float = 0.0, out=None, stream=None) -> torch.Tensor:
@@ -363,6 +408,29 @@ class _Chi2Fn(torch.autograd.Function):
         (grad,) = ctx.saved_tensors
         g = grad.to(torch.float64) * grad_chi2.to(torch.float64)[:, None]
         return g, None, None, None, None, None, None
+
+
+class _NllFn(torch.autograd.Function):
+    """Free-jitter nll with the adjoint kernel as backward."""
+
+    @staticmethod
+    def forward(ctx, params, t, v_obs, sigma, t0, mode):
+        val, grad = kc_nll_grad(params, t, v_obs, sigma, t0, mode)
+        ctx.save_for_backward(grad)
+        return val
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (grad,) = ctx.saved_tensors
+        return (grad.to(torch.float64) * grad_out.to(torch.float64)[:, None],
+                None, None, None, None, None)
+
+
+def nll(params, t, v_obs, sigma, t0: float = 0.0, mode="mixed") -> torch.Tensor:
+    """Differentiable free-jitter negative log-likelihood [n_sys]."""
+    if params.requires_grad and torch.is_grad_enabled():
+        return _NllFn.apply(params, t, v_obs, sigma, float(t0), mode)
+    return kc_nll_eval(params, t, v_obs, sigma, t0, mode)
 
 
 def chi2(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,

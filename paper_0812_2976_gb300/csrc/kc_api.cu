@@ -259,6 +259,56 @@ kc_status kc_chi2_grad(const double *params, const double *t, const double *v_ob
                      "kc_chi2_grad (mixed)");
 }
 
+// Tile for the free-jitter kernels: the tuned or default shape of the
+// fused kernel of that kind (they have no two-pass variant).
+static Tile nll_tile(Kind kind, int64_t n_sys, int32_t n_pl, int32_t n_obs) {
+  Tile tile = kc::choose_tile(kind, n_sys, n_pl, n_obs);
+  if (tile.split != 0 || tile.G > tile.block) tile = kc::default_tile(kind, n_sys, n_pl, n_obs);
+  tile.split = 0;
+  return tile;
+}
+
+kc_status kc_nll_eval(const double *params, const double *t, const double *v_obs,
+                      const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs, double t0,
+                      kc_mode mode, void *out, kc_stream stream) {
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, out, "kc_nll_eval");
+  if (st != KC_OK) return st;
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_nll_eval: bad mode");
+  if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_nll_eval: t0 must be finite");
+  if (n_sys == 0) return ok();
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == KC_FP64)
+    return cuda_status(kc::launch_nll_f64(a, nll_tile(Kind::Chi2F64, n_sys, n_pl, n_obs),
+                                          static_cast<double *>(out), s),
+                       "kc_nll_eval (fp64)");
+  return cuda_status(kc::launch_nll_mixed(a, nll_tile(Kind::Chi2Mixed, n_sys, n_pl, n_obs),
+                                          static_cast<float *>(out), s),
+                     "kc_nll_eval (mixed)");
+}
+
+kc_status kc_nll_grad(const double *params, const double *t, const double *v_obs,
+                      const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs, double t0,
+                      kc_mode mode, void *nll_out, void *grad_out, kc_stream stream) {
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, grad_out,
+                               "kc_nll_grad");
+  if (st != KC_OK) return st;
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_nll_grad: bad mode");
+  if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_nll_grad: t0 must be finite");
+  if (n_sys == 0) return ok();
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (mode == KC_FP64)
+    return cuda_status(kc::launch_grad_f64(a, nll_tile(Kind::GradF64, n_sys, n_pl, n_obs),
+                                           static_cast<double *>(nll_out),
+                                           static_cast<double *>(grad_out), s, true),
+                       "kc_nll_grad (fp64)");
+  return cuda_status(kc::launch_grad_mixed(a, nll_tile(Kind::GradMixed, n_sys, n_pl, n_obs),
+                                           static_cast<float *>(nll_out),
+                                           static_cast<float *>(grad_out), s, true),
+                     "kc_nll_grad (mixed)");
+}
+
 kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys, int32_t n_pl,
                         int32_t n_obs, double t0, double *v_out, kc_stream stream) {
   if (n_sys < 0 || n_obs < 0 || n_obs > KC_MAX_OBS)

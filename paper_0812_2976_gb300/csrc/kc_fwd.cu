@@ -28,11 +28,12 @@ namespace {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct MixedLayout {
-  size_t pl, gam, red, obs, w, total;
+  size_t pl, gam, s2, red, obs, w, total;
   __host__ __device__ MixedLayout(int ST, int J, int nwarps, int obs_tile) {
     pl = 0;
     gam = pl + sizeof(PlanetF) * ST * J;
-    red = align_up(gam + sizeof(float) * ST, 16);
+    s2 = gam + sizeof(float) * ST;
+    red = align_up(s2 + sizeof(float) * ST, 16);
     obs = align_up(red + sizeof(float) * 3 * nwarps, 16);
     w = obs + sizeof(float4) * obs_tile;
     total = align_up(w + sizeof(float) * obs_tile, 16);
@@ -44,11 +45,12 @@ struct ObsD {
 };
 
 struct F64Layout {
-  size_t pl, gam, red, obs, total;
+  size_t pl, gam, s2, red, obs, total;
   __host__ __device__ F64Layout(int ST, int J, int nwarps, int obs_tile) {
     pl = 0;
     gam = pl + sizeof(PlanetD) * ST * J;
-    red = align_up(gam + sizeof(double) * ST, 16);
+    s2 = gam + sizeof(double) * ST;
+    red = align_up(s2 + sizeof(double) * ST, 16);
     obs = align_up(red + sizeof(double) * 2 * nwarps, 16);
     total = align_up(obs + sizeof(ObsD) * obs_tile, 16);
   }
@@ -61,6 +63,22 @@ __device__ inline double system_gamma(const double *p, int J) {
     ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
   return ok ? p[5 * J] : __longlong_as_double(0x7ff8000000000000ll);
 }
+
+// Free jitter (the likelihood variant): sigma_j^2 of a system whose
+// parameters end with (gamma, sigma_j); NaN if sigma_j is not finite.
+__device__ inline double system_jitter2(const double *p, int J) {
+  const double sj = p[5 * J + 1];
+  return isfinite(sj) ? sj * sj : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+__device__ __forceinline__ float lg2_fast(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr float kLn2F = 0.693147180559945309f;
+constexpr double kLn2Pi = 1.8378770664093454836;      // ln(2 pi)
 
 // Inverse variance 1/(sigma_k^2 + sigma_jit^2) (Eq. 5); NaN if not positive.
 __device__ inline double inv_variance(double sigma, double jitter2) {
@@ -88,7 +106,10 @@ struct MixedPrep {
 // the observations itself.  PRE = true (split variant): both come from
 // prep_mixed_kernel, launched just before with programmatic dependent
 // launch; the CTA waits for it, then only copies.
-template <int J, bool PRE>
+// NLL = true (with PRE = false): every system carries its own jitter after
+// gamma and the kernel returns the negative log-likelihood
+//   1/2 sum_k [r_k^2/(sigma_k^2 + sigma_j^2) + ln(2 pi (sigma_k^2 + sigma_j^2))].
+template <int J, bool PRE, bool NLL = false>
 __global__ void __launch_bounds__(256, 2)
 chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__restrict__ out,
                   float *__restrict__ resid_out) {
@@ -99,13 +120,14 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   const MixedLayout L(ST, J, nwarps, obs_tile);
   PlanetF *pl_s = reinterpret_cast<PlanetF *>(smem + L.pl);
   float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float *s2_s = reinterpret_cast<float *>(smem + L.s2);
   float *red_s = reinterpret_cast<float *>(smem + L.red);
   float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
   float *w_s = reinterpret_cast<float *>(smem + L.w);
 
   const int tid = threadIdx.x;
   const int64_t sys0 = (int64_t)blockIdx.x * ST;
-  const int npar = 5 * J + 1;
+  const int npar = 5 * J + 1 + (NLL ? 1 : 0);
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   const double dref = t_ref - a.t0;
   const float jit2 = d2f(a.jitter2);
@@ -134,6 +156,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     for (int i = tid; i < ST; i += block) {
       const int64_t s = sys0 + i;
       gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
+      if (NLL) s2_s[i] = s < a.n_sys ? d2f(system_jitter2(a.params + s * npar, J)) : 0.0f;
     }
   }
 
@@ -158,17 +181,18 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
         obs_s[k] = make_float4(th, tl, vh, vl);
         const float sg = d2f(a.sigma[k0 + k]);
         const float var = __fmaf_rn(sg, sg, jit2);
-        w_s[k] = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+        // NLL keeps sigma_k^2: the weight depends on the system's own jitter
+        w_s[k] = NLL ? sg * sg : (var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000));
       }
     }
     __syncthreads();
     const float gam = gam_s[sl];
+    const float s2 = NLL ? s2_s[sl] : 0.0f;
     PlanetF q[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) q[j] = pl_s[sl * J + j];
     for (int k = c; k < nk; k += G) {
       const float4 o = obs_s[k];
-      const float wk = w_s[k];
       Kahan V = {0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < J; ++j) {
@@ -180,7 +204,13 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       }
       // residual V - v_obs with the model and the observation as float pairs
       const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-      kahan_add(acc, wk * r * r);
+      if (NLL) {
+        const float var = w_s[k] + s2;              // sigma_k^2 + sigma_j^2
+        const float wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
+        kahan_add(acc, __fmaf_rn(wk * r, r, lg2_fast(var) * kLn2F));
+      } else {
+        kahan_add(acc, w_s[k] * r * r);
+      }
     }
   }
 
@@ -210,7 +240,9 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   }
   if (c == 0 && s < a.n_sys) {
     // 0 * gamma turns an invalid system into NaN even when n_obs == 0
-    out[s] = kahan_value(acc) + 0.0f * gam_s[sl];
+    const float poison = 0.0f * gam_s[sl] + (NLL ? 0.0f * s2_s[sl] : 0.0f);
+    out[s] = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2Pi) + poison
+                 : kahan_value(acc) + poison;
     if (resid_out) resid_out[s] = rmax;
   }
 }
@@ -340,7 +372,7 @@ chi2_mixed_chunk_kernel(UniformArgs a, MixedPrep prep, ChunkScratch cs, int chun
 
 // ------------------------------------------------------------ FP64
 
-template <int J>
+template <int J, bool NLL = false>
 __global__ void __launch_bounds__(256, 2)
 chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
                 float *__restrict__ resid_out) {
@@ -350,12 +382,13 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   const F64Layout L(ST, J, block / 32, obs_tile);
   PlanetD *pl_s = reinterpret_cast<PlanetD *>(smem + L.pl);
   double *gam_s = reinterpret_cast<double *>(smem + L.gam);
+  double *s2_s = reinterpret_cast<double *>(smem + L.s2);
   double *red_s = reinterpret_cast<double *>(smem + L.red);
   ObsD *obs_s = reinterpret_cast<ObsD *>(smem + L.obs);
 
   const int tid = threadIdx.x;
   const int64_t sys0 = (int64_t)blockIdx.x * ST;
-  const int npar = 5 * J + 1;
+  const int npar = 5 * J + 1 + (NLL ? 1 : 0);
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   const double dref = t_ref - a.t0;
 
@@ -369,6 +402,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   for (int i = tid; i < ST; i += block) {
     const int64_t s = sys0 + i;
     gam_s[i] = s < a.n_sys ? system_gamma(a.params + s * npar, J) : 0.0;
+    if (NLL) s2_s[i] = s < a.n_sys ? system_jitter2(a.params + s * npar, J) : 0.0;
   }
 
   const int sl = tid / G, c = tid - sl * G;
@@ -382,7 +416,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
       ObsD o;
       o.tau = a.t[k0 + k] - t_ref;
       o.v = a.v[k0 + k];
-      o.w = inv_variance(a.sigma[k0 + k], a.jitter2);
+      o.w = NLL ? a.sigma[k0 + k] * a.sigma[k0 + k] : inv_variance(a.sigma[k0 + k], a.jitter2);
       o.pad = 0.0;
       obs_s[k] = o;
     }
@@ -402,7 +436,13 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
         V += velocity_f64(p, sE, cE);
       }
       const double r = V - o.v;
-      acc = fma(o.w * r, r, acc);
+      if (NLL) {
+        const double var = o.w + s2_s[sl];
+        const double wk = var > 0.0 ? 1.0 / var : __longlong_as_double(0x7ff8000000000000ll);
+        acc += fma(wk * r, r, log(var));
+      } else {
+        acc = fma(o.w * r, r, acc);
+      }
     }
   }
 
@@ -427,7 +467,8 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     }
   }
   if (c == 0 && s < a.n_sys) {
-    out[s] = acc + 0.0 * gam_s[sl];
+    const double poison = 0.0 * gam_s[sl] + (NLL ? 0.0 * s2_s[sl] : 0.0);
+    out[s] = NLL ? 0.5 * (acc + a.n_obs * kLn2Pi) + poison : acc + poison;
     if (resid_out) resid_out[s] = (float)rmax;
   }
 }
@@ -646,6 +687,38 @@ cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
   if (err == cudaSuccess)                                                            \
     chi2_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
                                                         resid);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nll_mixed(const UniformArgs &a, const Tile &tile, float *out, cudaStream_t st) {
+  const size_t smem = smem_chi2_mixed(a.n_pl, tile);
+  const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  const MixedPrep none{nullptr, nullptr, nullptr, nullptr};
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                       \
+  err = set_smem(chi2_mixed_kernel<JJ, false, true>, smem);                                 \
+  if (err == cudaSuccess)                                                                   \
+    chi2_mixed_kernel<JJ, false, true><<<grid, tile.block, smem, st>>>(a, none, tile.G,       \
+                                                                       tile.obs_tile, out,   \
+                                                                       nullptr);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nll_f64(const UniformArgs &a, const Tile &tile, double *out, cudaStream_t st) {
+  const size_t smem = smem_chi2_f64(a.n_pl, tile);
+  const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                      \
+  err = set_smem(chi2_f64_kernel<JJ, true>, smem);                                         \
+  if (err == cudaSuccess)                                                                  \
+    chi2_f64_kernel<JJ, true><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
+                                                              nullptr);
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;

@@ -77,6 +77,20 @@ __device__ inline double system_gamma_g(const double *p, int J) {
   return ok ? p[5 * J] : nan_d();
 }
 
+// Free jitter of a system whose parameters end with (gamma, sigma_j).
+__device__ inline double system_jitter_g(const double *p, int J) {
+  const double sj = p[5 * J + 1];
+  return isfinite(sj) ? sj : nan_d();
+}
+
+__device__ __forceinline__ float lg2_fast_g(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr double kLn2PiG = 1.8378770664093454836;      // ln(2 pi)
+
 __device__ inline double inv_variance_g(double sigma, double jitter2) {
   const double var = fma(sigma, sigma, jitter2);
   return (var > 0.0) ? 1.0 / var : nan_d();
@@ -104,11 +118,12 @@ __device__ __forceinline__ void velocity_partials(T e, T K, T cw, T sw, T beta, 
 }
 
 struct MixedGradLayout {
-  size_t pl, gam, obs, w, total;
+  size_t pl, gam, sj, obs, w, total;
   __host__ __device__ MixedGradLayout(int ST, int J, int obs_tile) {
     pl = 0;
     gam = pl + sizeof(GradPlanetF) * ST * J;
-    obs = align_up(gam + sizeof(float) * ST, 16);
+    sj = gam + sizeof(float) * ST;
+    obs = align_up(sj + sizeof(float) * ST, 16);
     w = obs + sizeof(float4) * obs_tile;
     total = align_up(w + sizeof(float2) * obs_tile, 16);
   }
@@ -119,28 +134,33 @@ struct ObsGD {
 };
 
 struct F64GradLayout {
-  size_t pl, gam, obs, total;
+  size_t pl, gam, sj, obs, total;
   __host__ __device__ F64GradLayout(int ST, int J, int obs_tile) {
     pl = 0;
     gam = pl + sizeof(GradPlanetD) * ST * J;
-    obs = align_up(gam + sizeof(double) * ST, 16);
+    sj = gam + sizeof(double) * ST;
+    obs = align_up(sj + sizeof(double) * ST, 16);
     total = align_up(obs + sizeof(ObsGD) * obs_tile, 16);
   }
 };
 
 // ------------------------------------------------------------ mixed
 
-template <int J>
+// NLL = true: the free-jitter negative log-likelihood (see kc_fwd.cu) and
+// its gradient, including d nll / d sigma_j = sigma_j sum_k w_k (1 - w_k r_k^2)
+// (the planet and gamma terms carry w_k r_k instead of 2 w_k r_k).
+template <int J, bool NLL = false>
 __global__ void __launch_bounds__(256, 2)
 grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_out,
                   float *__restrict__ grad_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NP = 5 * J + 1;
+  constexpr int NP = 5 * J + 1 + (NLL ? 1 : 0);
   const int block = blockDim.x;
   const int ST = block / G;
   const MixedGradLayout L(ST, J, obs_tile);
   GradPlanetF *pl_s = reinterpret_cast<GradPlanetF *>(smem + L.pl);
   float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float *sj_s = reinterpret_cast<float *>(smem + L.sj);
   float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
   float2 *wt_s = reinterpret_cast<float2 *>(smem + L.w);   // (w_k, t_k - t0)
 
@@ -162,14 +182,20 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
   for (int i = tid; i < ST; i += block) {
     const int64_t s = sys0 + i;
     gam_s[i] = s < a.n_sys ? (float)system_gamma_g(a.params + s * NP, J) : 0.0f;
+    if (NLL) sj_s[i] = s < a.n_sys ? d2f(system_jitter_g(a.params + s * NP, J)) : 0.0f;
   }
 
   const int sl = tid / G, c = tid - sl * G;
   const int64_t s = sys0 + sl;
   Kahan acc = {0.0f, 0.0f};
+  // d/dP terms carry (t - t0)/P^2 and cancel heavily across observations, so
+  // they are summed with compensation (plain FP32 sums lost up to ~3e-3)
+  Kahan gP[J];
   float g[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) g[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) gP[j] = Kahan{0.0f, 0.0f};
 
   for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
     const int nk = min(obs_tile, a.n_obs - k0);
@@ -182,11 +208,12 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
       obs_s[k] = make_float4(th, tl, vh, vl);
       const float sg = d2f(a.sigma[k0 + k]);
       const float var = __fmaf_rn(sg, sg, jit2);
-      wt_s[k] = make_float2(var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000),
+      wt_s[k] = make_float2(NLL ? sg * sg : (var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000)),
                             th + dref_f);
     }
     __syncthreads();
     const float gam = gam_s[sl];
+    const float sj = NLL ? sj_s[sl] : 0.0f;
     const GradPlanetF *q = pl_s + sl * J;
     for (int k = c; k < nk; k += G) {
       const float4 o = obs_s[k];
@@ -201,9 +228,19 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
         kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
       }
       const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-      const float wr = wt.x * r;
-      kahan_add(acc, wr * r);
-      const float a2 = 2.0f * wr;
+      float wk = wt.x, a2;
+      if (NLL) {
+        const float var = __fmaf_rn(sj, sj, wt.x);           // sigma_k^2 + sigma_j^2
+        wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
+        const float wr = wk * r;
+        kahan_add(acc, __fmaf_rn(wr, r, lg2_fast_g(var) * 0.693147180559945309f));
+        a2 = wr;
+        g[NP - 1] = __fmaf_rn(sj * wk, __fmaf_rn(-wr, r, 1.0f), g[NP - 1]);
+      } else {
+        const float wr = wk * r;
+        kahan_add(acc, wr * r);
+        a2 = 2.0f * wr;
+      }
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const GradPlanetF qj = q[j];
@@ -211,7 +248,7 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
         const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
         velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
         d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
-        g[5 * j + 0] = fmaf(a2, d.dP, g[5 * j + 0]);
+        kahan_add(gP[j], a2 * d.dP);
         g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
         g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
         g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
@@ -225,11 +262,21 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
     kahan_merge(acc, o);
 #pragma unroll
+    for (int j = 0; j < J; ++j) {
+      Kahan op = {shfl_xor(gP[j].big, m), shfl_xor(gP[j].small, m)};
+      kahan_merge(gP[j], op);
+    }
+#pragma unroll
     for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
   }
+#pragma unroll
+  for (int j = 0; j < J; ++j) g[5 * j] = kahan_value(gP[j]);
   if (c == 0 && s < a.n_sys) {
-    const float poison = 0.0f * gam_s[sl];     // NaN for an invalid system
-    if (chi2_out) chi2_out[s] = kahan_value(acc) + poison;
+    // NaN for an invalid system
+    const float poison = 0.0f * gam_s[sl] + (NLL ? 0.0f * sj_s[sl] : 0.0f);
+    if (chi2_out)
+      chi2_out[s] = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2PiG) + poison
+                        : kahan_value(acc) + poison;
 #pragma unroll
     for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
   }
@@ -237,17 +284,18 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
 
 // ------------------------------------------------------------ FP64
 
-template <int J>
+template <int J, bool NLL = false>
 __global__ void __launch_bounds__(256)
 grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_out,
                 double *__restrict__ grad_out) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NP = 5 * J + 1;
+  constexpr int NP = 5 * J + 1 + (NLL ? 1 : 0);
   const int block = blockDim.x;
   const int ST = block / G;
   const F64GradLayout L(ST, J, obs_tile);
   GradPlanetD *pl_s = reinterpret_cast<GradPlanetD *>(smem + L.pl);
   double *gam_s = reinterpret_cast<double *>(smem + L.gam);
+  double *sj_s = reinterpret_cast<double *>(smem + L.sj);
   ObsGD *obs_s = reinterpret_cast<ObsGD *>(smem + L.obs);
 
   const int tid = threadIdx.x;
@@ -265,6 +313,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
   for (int i = tid; i < ST; i += block) {
     const int64_t s = sys0 + i;
     gam_s[i] = s < a.n_sys ? system_gamma_g(a.params + s * NP, J) : 0.0;
+    if (NLL) sj_s[i] = s < a.n_sys ? system_jitter_g(a.params + s * NP, J) : 0.0;
   }
 
   const int sl = tid / G, c = tid - sl * G;
@@ -282,7 +331,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
       const double tk = a.t[k0 + k];
       o.tau = tk - t_ref;
       o.v = a.v[k0 + k];
-      o.w = inv_variance_g(a.sigma[k0 + k], a.jitter2);
+      o.w = NLL ? a.sigma[k0 + k] * a.sigma[k0 + k] : inv_variance_g(a.sigma[k0 + k], a.jitter2);
       o.dt = tk - a.t0;
       obs_s[k] = o;
     }
@@ -301,8 +350,18 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
         V += velocity_f64(p, sEj[j], cEj[j]);
       }
       const double r = V - o.v;
-      acc = fma(o.w * r, r, acc);
-      const double a2 = 2.0 * o.w * r;
+      double a2;
+      if (NLL) {
+        const double sj = sj_s[sl];
+        const double var = fma(sj, sj, o.w);
+        const double wk = var > 0.0 ? 1.0 / var : nan_d();
+        acc += fma(wk * r, r, log(var));
+        a2 = wk * r;
+        g[NP - 1] = fma(sj * wk, fma(-wk * r, r, 1.0), g[NP - 1]);
+      } else {
+        acc = fma(o.w * r, r, acc);
+        a2 = 2.0 * o.w * r;
+      }
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const GradPlanetD qj = q[j];
@@ -326,8 +385,8 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
     for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
   }
   if (c == 0 && s < a.n_sys) {
-    const double poison = 0.0 * gam_s[sl];
-    if (chi2_out) chi2_out[s] = acc + poison;
+    const double poison = 0.0 * gam_s[sl] + (NLL ? 0.0 * sj_s[sl] : 0.0);
+    if (chi2_out) chi2_out[s] = NLL ? 0.5 * (acc + a.n_obs * kLn2PiG) + poison : acc + poison;
 #pragma unroll
     for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
   }
@@ -361,37 +420,51 @@ size_t smem_grad(int n_pl, const Tile &t, bool f64) {
   }
 
 cudaError_t launch_grad_mixed(const UniformArgs &a, const Tile &tile, float *chi2, float *grad,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool nll) {
   if (tile.G > 32) return cudaErrorInvalidValue;
   const size_t smem = smem_grad(a.n_pl, tile, false);
   const int ST = tile.block / tile.G;
   const int grid = (int)((a.n_sys + ST - 1) / ST);
   cudaError_t err = cudaSuccess;
-#define KC_LAUNCH(JJ)                                                                   \
-  err = set_smem(grad_mixed_kernel<JJ>, smem);                                          \
-  if (err == cudaSuccess)                                                               \
-    grad_mixed_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2, \
-                                                          grad);
+#define KC_LAUNCH_NLL(JJ, NN)                                                                   \
+  err = set_smem(grad_mixed_kernel<JJ, NN>, smem);                                              \
+  if (err == cudaSuccess)                                                                       \
+    grad_mixed_kernel<JJ, NN><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2,     \
+                                                              grad);
+#define KC_LAUNCH(JJ)                      \
+  if (nll) {                               \
+    KC_LAUNCH_NLL(JJ, true)                \
+  } else {                                 \
+    KC_LAUNCH_NLL(JJ, false)               \
+  }
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
+#undef KC_LAUNCH_NLL
   if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2, double *grad,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool nll) {
   if (tile.G > 32) return cudaErrorInvalidValue;
   const size_t smem = smem_grad(a.n_pl, tile, true);
   const int ST = tile.block / tile.G;
   const int grid = (int)((a.n_sys + ST - 1) / ST);
   cudaError_t err = cudaSuccess;
-#define KC_LAUNCH(JJ)                                                                 \
-  err = set_smem(grad_f64_kernel<JJ>, smem);                                          \
-  if (err == cudaSuccess)                                                             \
-    grad_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2, \
-                                                        grad);
+#define KC_LAUNCH_NLL(JJ, NN)                                                                 \
+  err = set_smem(grad_f64_kernel<JJ, NN>, smem);                                              \
+  if (err == cudaSuccess)                                                                     \
+    grad_f64_kernel<JJ, NN><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, chi2,     \
+                                                            grad);
+#define KC_LAUNCH(JJ)                      \
+  if (nll) {                               \
+    KC_LAUNCH_NLL(JJ, true)                \
+  } else {                                 \
+    KC_LAUNCH_NLL(JJ, false)               \
+  }
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
+#undef KC_LAUNCH_NLL
   if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }

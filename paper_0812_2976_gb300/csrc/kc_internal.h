@@ -47,11 +47,15 @@ cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
                             float *resid, cudaStream_t st);
 cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out,
                               float *resid, cudaStream_t st);
-// Gradient (kc_grad.cu).
+// Gradient (kc_grad.cu); nll = true: the free-jitter log-likelihood variant
+// (parameters 5*n_pl + 2 per system).
 cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2,
-                            double *grad, cudaStream_t st);
+                            double *grad, cudaStream_t st, bool nll = false);
 cudaError_t launch_grad_mixed(const UniformArgs &a, const Tile &tile, float *chi2,
-                              float *grad, cudaStream_t st);
+                              float *grad, cudaStream_t st, bool nll = false);
+// Free-jitter negative log-likelihood, forward only (kc_fwd.cu).
+cudaError_t launch_nll_mixed(const UniformArgs &a, const Tile &tile, float *out, cudaStream_t st);
+cudaError_t launch_nll_f64(const UniformArgs &a, const Tile &tile, double *out, cudaStream_t st);
 // Model velocities and elementwise Kepler (kc_fwd.cu).
 cudaError_t launch_rv_predict(const double *params, const double *t, int64_t n_sys, int n_pl,
                               int n_obs, double t0, double *v_out, cudaStream_t st);

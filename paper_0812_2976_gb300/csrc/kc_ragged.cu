@@ -178,8 +178,11 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
   constexpr int NP = 5 * J + 1;
   Kahan acc = {0.0f, 0.0f};
   float g[GRAD ? NP : 1];
+  Kahan gP[GRAD ? J : 1];       // compensated d/dP sums (they cancel heavily)
 #pragma unroll
   for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < (GRAD ? J : 1); ++j) gP[j] = Kahan{0.0f, 0.0f};
   // the next observation is loaded while this one is evaluated
   float4 o_next = make_float4(0.f, 0.f, 0.f, 0.f);
   float2 wt_next = make_float2(0.f, 0.f);
@@ -215,7 +218,7 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
         const float invD = rcp_fast(__fmaf_rn(-q.base.e, cEj[j], 1.0f));
         partials_r(q.base.e, q.K, q.cw, q.sw, q.beta, sEj[j], cEj[j], invD, dK, dw, dM, de);
         const float dP = dM * (-kTwoPiF * wt.y * q.n2);
-        g[5 * j + 0] = __fmaf_rn(a2, dP, g[5 * j + 0]);
+        kahan_add(gP[GRAD ? j : 0], a2 * dP);
         g[5 * j + 1] = __fmaf_rn(a2, dK, g[5 * j + 1]);
         g[5 * j + 2] = __fmaf_rn(a2, de, g[5 * j + 2]);
         g[5 * j + 3] = __fmaf_rn(a2, dw, g[5 * j + 3]);
@@ -230,8 +233,17 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
     kahan_merge(acc, o);
     if (GRAD) {
 #pragma unroll
+      for (int j = 0; j < (GRAD ? J : 1); ++j) {
+        Kahan op = {shfl_xor(gP[j].big, m), shfl_xor(gP[j].small, m)};
+        kahan_merge(gP[j], op);
+      }
+#pragma unroll
       for (int i = 0; i < (GRAD ? NP : 1); ++i) g[i] += shfl_xor(g[i], m);
     }
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int j = 0; j < (GRAD ? J : 1); ++j) g[GRAD ? 5 * j : 0] = kahan_value(gP[j]);
   }
   if (lane == 0) {
     const float poison = 0.0f * gam;

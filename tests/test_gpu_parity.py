@@ -112,7 +112,7 @@ def test_config3_gradient_full_size_sampled(kc, oracle_mod):
     chi, grad = kc.kc_chi2_grad(P, T, V, S, t0=w.t0, mode="mixed")
     chi = chi.cpu().numpy()
     grad = grad.cpu().numpy()
-    idx = np.unique(np.concatenate([np.random.default_rng(1).choice(w.n_sys, 400, replace=False),
+    idx = np.unique(np.concatenate([np.random.default_rng(1).choice(w.n_sys, 3000, replace=False),
                                     [0, w.n_sys - 1]]))
     ref, gref = oracle_mod.chi2(w.params[idx], w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
     assert rel_err(chi[idx], ref).max() <= MIXED_TOL

@@ -364,3 +364,70 @@ def test_infinite_uncertainty_is_zero_weight(oracle_mod):
     t2 = np.append(t, 600.0)
     out = oracle_mod.chi2(par, t2, np.append(v, 1e3), np.append(sig, np.inf), 2)
     assert np.array_equal(out, base)
+
+
+# ------------------------------------------------ free jitter, log-likelihood
+
+def _with_jitter(par, sj):
+    return np.concatenate([par, np.full((par.shape[0], 1), sj)], axis=1)
+
+
+def test_nll_at_zero_jitter_is_half_chi2_plus_normalisation(oracle_mod):
+    rng = np.random.default_rng(18)
+    par = _random_systems(rng, 5, 3)
+    t = np.sort(rng.uniform(2450000, 2454000, 80))
+    v = rng.normal(0, 30, 80)
+    sig = rng.uniform(1, 5, 80)
+    chi = oracle_mod.chi2(par, t, v, sig, 3)
+    nll = oracle_mod.nll(_with_jitter(par, 0.0), t, v, sig, 3)
+    const = 0.5 * np.sum(np.log(2 * np.pi * sig ** 2))
+    assert np.allclose(nll, 0.5 * chi + const, rtol=1e-13)
+    # a jitter in the likelihood is the same as Eq. 5's sigma_j for the chi2 part
+    sj = 2.2
+    nll_j = oracle_mod.nll(_with_jitter(par, sj), t, v, sig, 3)
+    chi_j = oracle_mod.chi2(par, t, v, sig, 3, jitter=sj)
+    assert np.allclose(nll_j, 0.5 * chi_j + 0.5 * np.sum(np.log(2 * np.pi * (sig ** 2 + sj ** 2))),
+                       rtol=1e-13)
+    assert np.array_equal(oracle_mod.nll(_with_jitter(par, -sj), t, v, sig, 3), nll_j)
+
+
+def test_nll_jitter_derivative_vanishes_at_closed_form_optimum(oracle_mod):
+    """With equal uncertainties sigma, d nll/d sigma_j = 0 at
+    sigma_j^2 = mean(r^2) - sigma^2 (the Gaussian variance estimate)."""
+    rng = np.random.default_rng(19)
+    par = _random_systems(rng, 1, 2)
+    t = np.sort(rng.uniform(2450000, 2452000, 60))
+    r_true = rng.normal(0, 6, 60)
+    model = oracle_mod.predict(par, t, 2)[0]
+    v = model - r_true                         # residual V - v = r_true
+    sig = np.full(60, 2.0)
+    sj = np.sqrt(np.mean(r_true ** 2) - 4.0)
+    _, g = oracle_mod.nll(_with_jitter(par, sj), t, v, sig, 2, grad=True)
+    assert abs(g[0, -1]) < 1e-10 * np.sqrt(60)
+    _, g2 = oracle_mod.nll(_with_jitter(par, 1.5 * sj), t, v, sig, 2, grad=True)
+    assert g2[0, -1] > 0
+
+
+def test_nll_gradient_matches_central_differences(oracle_mod):
+    rng = np.random.default_rng(20)
+    n_pl = 2
+    par = _with_jitter(_random_systems(rng, 3, n_pl, e_max=0.8), 3.0)
+    t = np.sort(rng.uniform(2450000, 2454000, 50))
+    v = rng.normal(0, 40, 50)
+    sig = rng.uniform(1, 5, 50)
+    t0 = 2450000.0
+    _, g = oracle_mod.nll(par, t, v, sig, n_pl, t0=t0, grad=True)
+    for s in range(3):
+        fd = np.empty(par.shape[1])
+        for q in range(par.shape[1]):
+            h = 1e-6 * max(abs(par[s, q]), 1e-3)
+            if q % 5 == 0 and q < 5 * n_pl:
+                P = par[s, q]
+                h = 3e-4 * P * P / (2 * np.pi * np.max(np.abs(t - t0)))
+            p1, p2 = par[s].copy(), par[s].copy()
+            p1[q] += h
+            p2[q] -= h
+            fd[q] = (oracle_mod.nll(p1[None], t, v, sig, n_pl, t0=t0)[0]
+                     - oracle_mod.nll(p2[None], t, v, sig, n_pl, t0=t0)[0]) / (2 * h)
+        scale = np.maximum(np.abs(g[s]), 1e-3 * np.linalg.norm(g[s]))
+        assert np.max(np.abs(fd - g[s]) / scale) < 1e-5

@@ -44,6 +44,9 @@ MUTATIONS = [
      "kco_sum_add(&gsum[5 * j + q], a * g[q % 5][j % 5]);"),
     ("dchi2/dgamma factor", "kco_sum_add(&gsum[5 * n_pl], a);",
      "kco_sum_add(&gsum[5 * n_pl], 0.5 * a);"),
+    ("nll log term dropped", "0.5 * (wk * r * r + log(KCO_TWO_PI * var))", "0.5 * (wk * r * r)"),
+    ("nll jitter gradient sign", "sj * wk * (1.0 - wk * r * r)", "sj * wk * (1.0 + wk * r * r)"),
+    ("nll gradient factor", "double a = wk * r;", "double a = 2.0 * wk * r;"),
     ("prediction without gamma", "double V = par[5 * n_pl];\n            for (j = 0; j < n_pl; ++j) V +=",
      "double V = 0.0;\n            for (j = 0; j < n_pl; ++j) V +="),
 ]
