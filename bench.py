@@ -151,6 +151,24 @@ def gradient_throughput(kc, synth, dev, stream, args):
     return out
 
 
+def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):
+    """DE-MC (two-half differential evolution) over the batch's 4096 model
+    systems as a population: generations per second with graph replay."""
+    import torch
+    mc = kc.DEMCMC(P, T, V, S, mode="mixed", eps_scale=1e-6, hop_every=0, seed=5)
+    mc.run(3)                                        # includes the graph capture
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    mc.run(generations)
+    b.record()
+    torch.cuda.synchronize(dev)
+    sec = a.elapsed_time(b) / 1e3
+    return {"generations_per_s": generations / sec, "population": w.n_sys,
+            "planet_obs_evals_per_s": generations * w.n_sys * w.n_pl * w.n_obs / sec,
+            "acceptance": mc.acceptance}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,6 +485,7 @@ def run_kc(args):
         extras["kepler_only"] = kepler_throughput(kc, dev, stream)
         extras["grid_sweep"] = grid_sweep_throughput(kc, synth, dev, stream, args)
         extras["gradient"] = gradient_throughput(kc, synth, dev, stream, args)
+        extras["demcmc"] = demcmc_throughput(kc, w, P, T, V, S, dev)
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)

@@ -162,6 +162,33 @@ kc_status kc_chi2_eval_mixed_noalloc(const double *params, const double *t,
                                      double t0, double jitter, float *out,
                                      float *max_kepler_resid, kc_stream stream);
 
+/* --------------------------------------------------------- DE-MC step */
+
+/* One step of differential-evolution MCMC (ter Braak 2006; the population
+ * MCMC the paper proposes to drive the evaluator, Sec. 6) for chains
+ * first .. first+count-1 of a population of n_chains parameter vectors
+ * (states [n_chains][5*n_pl+1], device, updated in place; chi2 [n_chains]
+ * their current chi2, double for KC_FP64, float for KC_MIXED).  Chain i
+ * proposes x* = x_i + gamma (x_r1 - x_r2) + eps_i with partners
+ * (r1, r2) = partners[2c], partners[2c+1] (int32 [count][2]) and eps
+ * [count][5*n_pl+1], evaluates chi2(x*) with the kernels of
+ * kc_chi2_eval_ex (epoch t0, jitter, mode), and accepts iff
+ * ln u[c] < -(chi2(x*) - chi2(x_i))/2 (u [count] in (0, 1]; flat prior,
+ * invalid parameters are rejected).  For detailed balance with all chains of
+ * the range updated at once, the partners must come from chains outside the
+ * range (e.g. the other half of the population) and be distinct; partner
+ * indices outside [0, n_chains) make the proposal NaN (rejected).  The caller
+ * supplies the random draws and the workspaces proposals [count][5*n_pl+1]
+ * and chi2_prop [count] (chi2's type); accepted [count] (may be NULL)
+ * receives 1/0. */
+kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains,
+                         int32_t n_pl, const double *t, const double *v_obs,
+                         const double *sigma, int32_t n_obs, double t0,
+                         double jitter, kc_mode mode, int64_t first,
+                         int64_t count, double gamma, const int32_t *partners,
+                         const double *eps, const double *u, double *proposals,
+                         void *chi2_prop, int32_t *accepted, kc_stream stream);
+
 /* -------------------------------------------------------- model, Kepler */
 
 /* FP64 model velocities V(t_k) = gamma + sum_j v_j(t_k) (Eq. 2):
@@ -253,7 +280,9 @@ void kc_plan_destroy(kc_plan *plan);
  * (programmatic dependent launch) only reads them.  split = 1: CTAs as
  * above.  split = 2: one warp per (system, chunk of observations);
  * threads_per_system = 32 x chunks (32..1024), any block; the last warp of a
- * system merges the chunks' partial sums in chunk order. */
+ * system merges the chunks' partial sums in chunk order.  While the stream is
+ * being captured into a CUDA graph the split variants are replaced by the
+ * fused kernel (no allocation inside a graph). */
 typedef struct kc_tile {
     int32_t threads_per_system;
     int32_t block;

@@ -386,6 +386,49 @@ int kco_predict_ragged(const double *params, const int64_t *par_off,
     return 0;
 }
 
+/* One differential-evolution MCMC step (ter Braak 2006) for chains
+ * first .. first+count-1 (see the library's kc_demcmc_step): proposal
+ * x* = x_i + gamma (x_r1 - x_r2) + eps (evaluated in that order, no fused
+ * operations), chi2 of the proposals in FP64, acceptance iff
+ * ln u < -(chi2* - chi2_i)/2; accepted states and chi2 replace the current
+ * ones.  proposals [count][n_par], chi2_prop [count] and accepted [count]
+ * are outputs.  Partners outside [0, n_chains) give a NaN proposal. */
+int kco_demcmc_step(double *states, double *chi2, int64_t n_chains, int n_pl,
+                    const double *t, const double *v, const double *sigma,
+                    int64_t n_obs, double t0, double jitter, int64_t first,
+                    int64_t count, double gamma, const int32_t *partners,
+                    const double *eps, const double *u, double *proposals,
+                    double *chi2_prop, int32_t *accepted)
+{
+    int n_par = 5 * n_pl + 1, p;
+    int64_t c;
+    if (first < 0 || count < 0 || first + count > n_chains) return -1;
+    for (c = 0; c < count; ++c) {
+        int64_t i = first + c, r1 = partners[2 * c], r2 = partners[2 * c + 1];
+        for (p = 0; p < n_par; ++p) {
+            double x = NAN;
+            if (r1 >= 0 && r1 < n_chains && r2 >= 0 && r2 < n_chains) {
+                double d = states[r1 * n_par + p] - states[r2 * n_par + p];
+                x = (states[i * n_par + p] + gamma * d) + eps[c * n_par + p];
+            }
+            proposals[c * n_par + p] = x;
+        }
+    }
+    if (kco_chi2(proposals, t, v, sigma, count, n_pl, n_obs, t0, jitter, chi2_prop,
+                 NULL) != 0)
+        return -1;
+    for (c = 0; c < count; ++c) {
+        int64_t i = first + c;
+        int acc = log(u[c]) < -0.5 * (chi2_prop[c] - chi2[i]);
+        if (acc) {
+            for (p = 0; p < n_par; ++p) states[i * n_par + p] = proposals[c * n_par + p];
+            chi2[i] = chi2_prop[c];
+        }
+        accepted[c] = acc;
+    }
+    return 0;
+}
+
 /* Elementwise Kepler solve (E for each (M, e) pair). */
 void kco_kepler_batch(const double *M, const double *e, int64_t n, double *E,
                       int32_t *n_iter)

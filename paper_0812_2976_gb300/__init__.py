@@ -23,6 +23,7 @@ __all__ = [
     "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
     "kc_chi2_eval_mixed_noalloc", "kc_nll_eval", "kc_nll_grad", "nll",
+    "kc_demcmc_step", "DEMCMC",
     "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
     "RaggedPlan", "chi2", "n_planets", "library_path",
 ]
@@ -392,6 +393,155 @@ class RaggedPlan:
             self.close()
         except Exception:
             pass
+
+
+def kc_demcmc_step(states, chi2, t, v_obs, sigma, first: int, count: int, gamma: float,
+                   partners, eps, u, proposals=None, chi2_prop=None, accepted=None,
+                   t0: float = 0.0, jitter: float = 0.0, mode="mixed", stream=None):
+    """One DE-MC step of chains first .. first+count-1 in place
+    (kc_demcmc_step).  states: float64 [n_chains, 5*n_pl+1]; chi2: float32
+    ('mixed') or float64 ('fp64') [n_chains]; partners int32 [count, 2];
+    eps float64 [count, 5*n_pl+1]; u float64 [count].  Returns accepted
+    (int32 [count])."""
+    states = _dev_f64("states", states, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    if chi2.dtype != dtype or not chi2.is_cuda:
+        raise TypeError(f"chi2 must be a {dtype} CUDA tensor")
+    n_pl = n_planets(states)
+    npar = 5 * n_pl + 1
+    partners = partners.to(device=states.device, dtype=torch.int32).contiguous()
+    eps = _dev_f64("eps", eps, 2)
+    u = _dev_f64("u", u, 1)
+    if proposals is None:
+        proposals = torch.empty((count, npar), dtype=torch.float64, device=states.device)
+    if chi2_prop is None:
+        chi2_prop = torch.empty(count, dtype=dtype, device=states.device)
+    if accepted is None:
+        accepted = torch.empty(count, dtype=torch.int32, device=states.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_demcmc_step(
+        states.data_ptr(), chi2.data_ptr(), states.shape[0], n_pl, t.data_ptr(),
+        v_obs.data_ptr(), sigma.data_ptr(), t.numel(), float(t0), float(jitter), m, int(first),
+        int(count), float(gamma), partners.data_ptr(), eps.data_ptr(), u.data_ptr(),
+        proposals.data_ptr(), chi2_prop.data_ptr(), accepted.data_ptr(), _stream(stream)),
+        "kc_demcmc_step")
+    return accepted
+
+
+class DEMCMC:
+    """Differential-evolution MCMC (ter Braak 2006) over a population of
+    model systems on the GPU, chi2 as -2 ln L (flat prior).
+
+    Each generation updates the two halves of the population in turn, every
+    chain of a half proposing x + gamma (x_r1 - x_r2) + eps with r1 != r2
+    from the other half; gamma = 2.38/sqrt(2 d) except every ``hop_every``-th
+    generation where gamma = 1 (jumps between modes); eps ~ N(0, eps_scale^2
+    x^2) per parameter (``eps_scale`` a number or one value per parameter; 0
+    together with equal values in every chain holds a parameter fixed).
+    Random draws come from a torch generator on the device; the step itself
+    is kc_demcmc_step."""
+
+    def __init__(self, states, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
+                 mode="mixed", eps_scale: float = 1e-6, hop_every: int = 10, seed: int = 0):
+        self.states = _dev_f64("states", states, 2).clone()
+        n = self.states.shape[0]
+        if n < 8 or n % 2:
+            raise ValueError("DEMCMC needs an even population of at least 8 chains")
+        self.t, self.v, self.sigma = _obs(t, v_obs, sigma)
+        self.t0, self.jitter, self.mode = float(t0), float(jitter), mode
+        self.npar = self.states.shape[1]
+        self.half = n // 2
+        self.gamma = 2.38 / (2.0 * self.npar) ** 0.5
+        self.eps_scale = torch.as_tensor(eps_scale, dtype=torch.float64,
+                                         device=self.states.device).expand(self.npar).clone()
+        self.hop_every = int(hop_every)
+        self.gen = torch.Generator(device=self.states.device)
+        self.gen.manual_seed(seed)
+        self.chi2 = kc_chi2_eval_ex(self.states, self.t, self.v, self.sigma, self.t0,
+                                    self.jitter, mode)
+        dev = self.states.device
+        self._prop = torch.empty((self.half, self.npar), dtype=torch.float64, device=dev)
+        self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
+        self._acc = torch.empty(self.half, dtype=torch.int32, device=dev)
+        self.generation = 0
+        self._n_acc = torch.zeros((), dtype=torch.int64, device=dev)   # no host syncs
+        self.proposed = 0
+
+    def _partners(self, other: int):
+        h = self.half
+        r1 = torch.randint(0, h, (h,), generator=self.gen, device=self.states.device)
+        r2 = torch.randint(0, h - 1, (h,), generator=self.gen, device=self.states.device)
+        r2 = r2 + (r2 >= r1).to(r2.dtype)                 # r2 != r1
+        return (torch.stack([r1, r2], dim=1) + other).to(torch.int32)
+
+    def step(self) -> None:
+        """One generation (both halves)."""
+        gamma = 1.0 if self.hop_every and (self.generation + 1) % self.hop_every == 0 \
+            else self.gamma
+        for first, other in ((0, self.half), (self.half, 0)):
+            cur = self.states[first:first + self.half]
+            eps = torch.randn((self.half, self.npar), generator=self.gen, dtype=torch.float64,
+                              device=self.states.device) * (self.eps_scale * cur.abs())
+            u = torch.rand(self.half, generator=self.gen, dtype=torch.float64,
+                           device=self.states.device).clamp_min_(1e-300)
+            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, self.half,
+                           gamma, self._partners(other), eps, u, self._prop, self._cp,
+                           self._acc, self.t0, self.jitter, self.mode)
+            self._n_acc += self._acc.sum()
+            self.proposed += self.half
+        self.generation += 1
+
+    def run(self, generations: int, use_graph: bool = True) -> None:
+        """``generations`` generations; with use_graph, one generation is
+        captured into a CUDA graph (random draws included) and replayed,
+        which removes the per-launch host overhead for small populations.
+        The gamma = 1 generations are not captured (they run eagerly)."""
+        if not use_graph:
+            for _ in range(generations):
+                self.step()
+            return
+        if getattr(self, "_graph", None) is None:
+            self.step()                                   # warm-up outside capture
+            torch.cuda.synchronize()
+            side = torch.cuda.Stream(device=self.states.device)
+            side.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            g.register_generator_state(self.gen)          # replays advance self.gen
+            saved = (self.generation, self.proposed)
+            self.generation = 0                           # capture a regular generation
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(g, stream=side):
+                    self._graph_gen()
+            self.generation, self.proposed = saved
+            self._graph = g
+            generations -= 1
+        for _ in range(generations):
+            hop = self.hop_every and (self.generation + 1) % self.hop_every == 0
+            if hop:
+                self.step()
+            else:
+                self._graph.replay()
+                self.generation += 1
+                self.proposed += 2 * self.half
+
+    def _graph_gen(self) -> None:
+        for first, other in ((0, self.half), (self.half, 0)):
+            cur = self.states[first:first + self.half]
+            eps = torch.randn((self.half, self.npar), generator=self.gen, dtype=torch.float64,
+                              device=self.states.device) * (self.eps_scale * cur.abs())
+            u = torch.rand(self.half, generator=self.gen, dtype=torch.float64,
+                           device=self.states.device).clamp_min_(1e-300)
+            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, self.half,
+                           self.gamma, self._partners(other), eps, u, self._prop, self._cp,
+                           self._acc, self.t0, self.jitter, self.mode)
+            self._n_acc += self._acc.sum()
+
+    @property
+    def acceptance(self) -> float:
+        """Fraction of accepted proposals so far (synchronises)."""
+        return int(self._n_acc) / max(self.proposed, 1)
 
 
 class _Chi2Fn(torch.autograd.Function):

@@ -1,0 +1,96 @@
+// kc_demcmc.cu -- one generation step of differential-evolution Markov chain
+// Monte Carlo (DE-MC, ter Braak 2006) on the GPU, with chi2 from the fused
+// kernels as the likelihood: the population-MCMC use the paper proposes for
+// its evaluator (Sec. 6).
+//
+// Chain i of a population proposes x* = x_i + gamma (x_r1 - x_r2) + eps_i
+// with r1 != r2 two other chains, and accepts with probability
+// min(1, exp(-(chi2(x*) - chi2(x_i))/2)) (flat prior; invalid parameters give
+// NaN chi2 and are rejected).  To update many chains at once and keep
+// detailed balance, the population is split in two halves: a step updates
+// one half, drawing r1, r2 from the other half, whose states stay fixed
+// during the step (the ensemble parallelisation of Goodman & Weare as used by
+// Foreman-Mackey et al. 2013).  The random numbers are inputs, so the step is
+// a deterministic function of them.
+#include <cmath>
+
+#include "kc_internal.h"
+
+namespace kc {
+
+namespace {
+
+__device__ inline double nan_dm() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// x* = x_i + gamma (x_r1 - x_r2) + eps, written with explicit roundings so
+// that the result does not depend on FMA contraction.
+__global__ void demcmc_propose_kernel(const double *__restrict__ states, int64_t n_chains,
+                                      int n_par, int64_t first, int64_t count, double gamma,
+                                      const int32_t *__restrict__ partners,
+                                      const double *__restrict__ eps, double *__restrict__ prop) {
+  const int64_t total = count * n_par;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = idx / n_par;
+    const int p = (int)(idx - c * n_par);
+    const int64_t i = first + c;
+    const int64_t r1 = partners[2 * c], r2 = partners[2 * c + 1];
+    double x = nan_dm();      // out-of-range partners: NaN proposal, rejected
+    if (r1 >= 0 && r1 < n_chains && r2 >= 0 && r2 < n_chains) {
+      const double d = __dsub_rn(states[r1 * n_par + p], states[r2 * n_par + p]);
+      x = __dadd_rn(__dadd_rn(states[i * n_par + p], __dmul_rn(gamma, d)), eps[idx]);
+    }
+    prop[idx] = x;
+  }
+}
+
+// Metropolis decision in double precision: accept iff ln u < -(chi2* - chi2)/2.
+template <typename T>
+__global__ void demcmc_accept_kernel(double *__restrict__ states, T *__restrict__ chi2,
+                                     const double *__restrict__ prop,
+                                     const T *__restrict__ chi2_prop, int64_t first,
+                                     int64_t count, int n_par, const double *__restrict__ u,
+                                     int32_t *__restrict__ accepted) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = first + c;
+    const double delta = (double)chi2_prop[c] - (double)chi2[i];
+    const bool acc = log(u[c]) < -0.5 * delta;          // false when delta is NaN
+    if (acc) {
+      for (int p = 0; p < n_par; ++p) states[i * n_par + p] = prop[c * n_par + p];
+      chi2[i] = chi2_prop[c];
+    }
+    if (accepted) accepted[c] = acc ? 1 : 0;
+  }
+}
+
+int grid_elems(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_demcmc_propose(const double *states, int64_t n_chains, int n_par, int64_t first,
+                                  int64_t count, double gamma, const int32_t *partners,
+                                  const double *eps, double *prop, cudaStream_t st) {
+  demcmc_propose_kernel<<<grid_elems(count * n_par), 256, 0, st>>>(
+      states, n_chains, n_par, first, count, gamma, partners, eps, prop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_demcmc_accept(double *states, void *chi2, const double *prop,
+                                 const void *chi2_prop, int64_t first, int64_t count, int n_par,
+                                 const double *u, bool f64, int32_t *accepted, cudaStream_t st) {
+  if (f64)
+    demcmc_accept_kernel<double><<<grid_elems(count), 256, 0, st>>>(
+        states, (double *)chi2, prop, (const double *)chi2_prop, first, count, n_par, u,
+        accepted);
+  else
+    demcmc_accept_kernel<float><<<grid_elems(count), 256, 0, st>>>(
+        states, (float *)chi2, prop, (const float *)chi2_prop, first, count, n_par, u,
+        accepted);
+  return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -650,8 +650,20 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
   return cudaGetLastError();
 }
 
-cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out, float *resid,
-                              cudaStream_t st) {
+cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile_in, float *out,
+                              float *resid, cudaStream_t st) {
+  Tile tile = tile_in;
+  if (tile.split) {
+    // No stream-ordered allocation inside a graph being captured: the fused
+    // kernel (no scratch) stands in for the split variants there.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(st, &cs);
+    if (err != cudaSuccess) return err;
+    if (cs != cudaStreamCaptureStatusNone) {
+      if (tile.G > tile.block) tile = default_tile(Kind::Chi2Mixed, a.n_sys, a.n_pl, a.n_obs);
+      tile.split = 0;
+    }
+  }
   if (tile.split) {
     // stream-ordered scratch from the library's pool (kept cached between calls)
     void *scratch = nullptr;

@@ -1,0 +1,123 @@
+"""DE-MC step (kc_demcmc_step) and driver on the GPU vs the FP64 oracle.
+
+The random draws (partners, eps, u) and the current chi2 are the same
+inputs on both sides.  Proposals are exact arithmetic of the inputs and must
+match bit for bit; accept decisions must match wherever the Metropolis
+margin |ln u + (chi2* - chi2)/2| is above what the chi2 tolerance of the mode
+can move (1e-12 relative in FP64, 1e-5 mixed); the states then follow."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kc():
+    import paper_0812_2976_gb300 as kc
+    from paper_0812_2976_gb300 import build
+    build.build()
+    kc._lib.load()
+    return kc
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_step_matches_oracle(kc, oracle_mod, mode, tol):
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1, n_sys=512)
+    v = oracle_mod.predict(w.truth, w.t, w.n_pl)[0] + w.noise
+    states = w.params
+    chi = oracle_mod.chi2(states, w.t, v, w.sigma, w.n_pl)
+    rng = np.random.default_rng(40)
+    first, count, other = 256, 256, 0
+    r1 = rng.integers(0, 256, count)
+    r2 = (r1 + rng.integers(1, 256, count)) % 256
+    partners = np.stack([r1, r2], axis=1) + other
+    partners[7] = [600, 3]                                     # out of range: rejected
+    eps = rng.normal(0, 1e-4, (count, states.shape[1])) * np.abs(states[first:])
+    u = rng.uniform(0, 1, count)
+    gamma = 2.38 / np.sqrt(2 * states.shape[1])
+    ref = oracle_mod.demcmc_step(states, chi, w.t, v, w.sigma, w.n_pl, first, count, gamma,
+                                 partners, eps, u)
+    ref_states, ref_chi, ref_acc, ref_prop, ref_cp = ref
+    S = dev(states)
+    C = dev(chi, torch.float64 if mode == "fp64" else torch.float32)
+    prop = torch.empty((count, states.shape[1]), dtype=torch.float64, device="cuda")
+    cp = torch.empty(count, dtype=C.dtype, device="cuda")
+    acc = kc.kc_demcmc_step(S, C, dev(w.t), dev(v), dev(w.sigma), first, count, gamma,
+                            torch.tensor(partners, dtype=torch.int32), dev(eps), dev(u),
+                            proposals=prop, chi2_prop=cp, mode=mode).cpu().numpy()
+    prop = prop.cpu().numpy()
+    finite = np.all(np.isfinite(ref_prop), axis=1)
+    assert np.array_equal(prop[finite], ref_prop[finite])       # bit for bit
+    assert np.all(np.isnan(prop[7])) and acc[7] == 0
+    cp = cp.cpu().numpy().astype(np.float64)
+    ok = np.isfinite(ref_cp)
+    assert np.max(np.abs(cp[ok] - ref_cp[ok]) / np.maximum(ref_cp[ok], 1.0)) <= tol
+    # decisions away from the Metropolis boundary are identical
+    chi_cur = C.cpu().numpy().astype(np.float64)[first:] if mode == "mixed" else chi[first:]
+    margin = np.abs(np.log(u) + 0.5 * (ref_cp - chi[first:]))
+    slack = 4 * tol * np.maximum(ref_cp, 1.0) + 4 * tol * np.maximum(chi_cur, 1.0)
+    sure = ok & (margin > slack)
+    assert sure.sum() > count // 2
+    assert np.array_equal(acc[sure], ref_acc[sure])
+    new_states = S.cpu().numpy()
+    for c in np.nonzero(sure)[0]:
+        expect = ref_prop[c] if ref_acc[c] else states[first + c]
+        assert np.array_equal(new_states[first + c], expect)
+    assert np.array_equal(new_states[:first], states[:first])
+
+
+def test_driver_samples_the_linear_gaussian_posterior(kc):
+    """The DEMCMC driver on a circular planet with only K and gamma free:
+    the posterior is Gaussian with the least-squares mean and covariance."""
+    rng = np.random.default_rng(41)
+    P, w, M0 = 37.0, 0.4, 1.3
+    t = np.sort(rng.uniform(2450000, 2450200, 40))
+    sig = rng.uniform(1, 3, 40)
+    phase = w + 2 * np.pi * np.fmod(t, P) / P + M0
+    A = np.stack([np.cos(phase), np.ones_like(t)], axis=1)
+    v = A @ np.array([12.0, -3.0]) + rng.normal(0, sig)
+    Wm = np.diag(1 / sig ** 2)
+    cov = np.linalg.inv(A.T @ Wm @ A)
+    mean = cov @ A.T @ Wm @ v
+    n = 256
+    states = np.tile([P, 0.0, 0.0, w, M0, 0.0], (n, 1))
+    states[:, 1] = mean[0] + 3 * np.sqrt(cov[0, 0]) * rng.standard_normal(n)
+    states[:, 5] = mean[1] + 3 * np.sqrt(cov[1, 1]) * rng.standard_normal(n)
+    mc = kc.DEMCMC(dev(states), dev(t), dev(v), dev(sig), mode="mixed",
+                   eps_scale=[0.0, 1e-5, 0.0, 0.0, 0.0, 1e-5], seed=3)
+    samples = []
+    for gen in range(1200):
+        mc.step()
+        if gen >= 200 and gen % 2 == 0:
+            samples.append(mc.states[:, [1, 5]].clone())
+    s = torch.cat(samples).cpu().numpy()
+    assert 0.1 < mc.acceptance < 0.9
+    assert np.all(np.abs(s.mean(axis=0) - mean) < 0.1 * np.sqrt(np.diag(cov)))
+    assert np.allclose(np.cov(s.T), cov, rtol=0.15, atol=0.1 * np.sqrt(cov[0, 0] * cov[1, 1]))
+    # P, w, M0 never move: every chain holds the same value
+    st = mc.states.cpu().numpy()
+    assert np.all(st[:, 0] == P) and np.all(st[:, 3] == w) and np.all(st[:, 4] == M0)
+
+
+def test_graph_replay_equals_eager(kc):
+    """The same seed gives the same chain eagerly and with graph replay."""
+    from paper_0812_2976_gb300 import synth
+    import oracle
+    w = synth.uniform(1, n_sys=256)
+    v = oracle.predict(w.truth, w.t, w.n_pl)[0] + w.noise
+    runs = []
+    for use_graph in (False, True):
+        mc = kc.DEMCMC(dev(w.params), dev(w.t), dev(v), dev(w.sigma), mode="mixed",
+                       eps_scale=1e-6, hop_every=0, seed=11)
+        mc.run(12, use_graph=use_graph)
+        runs.append((mc.states.cpu().numpy(), mc.chi2.cpu().numpy(), mc.acceptance))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
+    assert np.median(runs[0][1]) < np.median(oracle.chi2(w.params, w.t, v, w.sigma, w.n_pl))

@@ -431,3 +431,91 @@ def test_nll_gradient_matches_central_differences(oracle_mod):
                      - oracle_mod.nll(p2[None], t, v, sig, n_pl, t0=t0)[0]) / (2 * h)
         scale = np.maximum(np.abs(g[s]), 1e-3 * np.linalg.norm(g[s]))
         assert np.max(np.abs(fd - g[s]) / scale) < 1e-5
+
+
+# ------------------------------------------------ DE-MC step
+
+def test_demcmc_zero_move_always_accepted(oracle_mod):
+    """gamma = 0, eps = 0: the proposal is the state itself, Delta chi2 = 0,
+    and ln u < 0 for u < 1 accepts it (states unchanged)."""
+    rng = np.random.default_rng(22)
+    states = _random_systems(rng, 8, 2)
+    t = np.sort(rng.uniform(2450000, 2452000, 30))
+    v = rng.normal(0, 30, 30)
+    sig = rng.uniform(1, 5, 30)
+    chi = oracle_mod.chi2(states, t, v, sig, 2)
+    partners = np.stack([np.arange(4, 8), np.arange(5, 9) % 8 + 0], axis=1)
+    partners[:, 1] = np.where(partners[:, 1] < 4, 4, partners[:, 1])
+    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, 2, 0, 4, 0.0, partners,
+                                                   np.zeros((4, 11)), rng.uniform(0.01, 0.99, 4))
+    assert np.array_equal(prop, states[:4]) and np.array_equal(cp, chi[:4])
+    assert np.all(acc == 1) and np.array_equal(st, states)
+
+
+def test_demcmc_metropolis_rule(oracle_mod):
+    """Accept iff u < exp(-(chi2* - chi2)/2), checked against chi2 computed
+    separately; rejected chains keep state and chi2, bad partners reject."""
+    rng = np.random.default_rng(23)
+    n, n_pl = 40, 1
+    states = _random_systems(rng, n, n_pl, e_max=0.5)
+    t = np.sort(rng.uniform(2450000, 2451000, 25))
+    v = oracle_mod.predict(states[0], t, n_pl)[0] + rng.normal(0, 2, 25)
+    sig = np.full(25, 2.0)
+    chi = oracle_mod.chi2(states, t, v, sig, n_pl)
+    partners = np.stack([rng.integers(20, 40, 20), rng.integers(20, 40, 20)], axis=1)
+    partners[3] = [55, 21]                                 # out of range
+    eps = rng.normal(0, 1e-3, (20, 6)) * np.abs(states[:20])
+    u = rng.uniform(0, 1, 20)
+    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, n_pl, 0, 20, 0.7,
+                                                   partners, eps, u)
+    ref_cp = oracle_mod.chi2(prop, t, v, sig, n_pl)
+    finite = np.isfinite(ref_cp)
+    assert np.array_equal(cp[finite], ref_cp[finite])
+    assert np.all(np.isnan(prop[3])) and acc[3] == 0
+    with np.errstate(over="ignore"):
+        expect = np.where(np.isfinite(cp), u < np.exp(-0.5 * (cp - chi[:20])), False)
+    assert np.array_equal(acc.astype(bool), expect)
+    assert np.array_equal(st[:20][~expect], states[:20][~expect])
+    assert np.array_equal(st[:20][expect], prop[expect])
+    assert np.array_equal(st[20:], states[20:])
+
+
+def test_demcmc_samples_the_linear_gaussian_posterior(oracle_mod):
+    """A circular planet with P, w, M0 fixed (identical in every chain, so
+    DE never moves them) makes v linear in (K, gamma): the posterior is
+    Gaussian with the least-squares mean and covariance.  Two-half DE-MC
+    with the oracle's steps must reproduce them."""
+    rng = np.random.default_rng(24)
+    P, w, M0 = 37.0, 0.4, 1.3
+    t = np.sort(rng.uniform(0, 200, 40))
+    sig = rng.uniform(1, 3, 40)
+    phase = w + 2 * np.pi * t / P + M0
+    A = np.stack([np.cos(phase), np.ones_like(t)], axis=1)      # v = K cos + gamma
+    truth = np.array([12.0, -3.0])
+    v = A @ truth + rng.normal(0, sig)
+    Wm = np.diag(1 / sig ** 2)
+    cov = np.linalg.inv(A.T @ Wm @ A)
+    mean = cov @ A.T @ Wm @ v
+    n = 64
+    states = np.tile([P, 0.0, 0.0, w, M0, 0.0], (n, 1))
+    states[:, 1] = mean[0] + 3 * np.sqrt(cov[0, 0]) * rng.standard_normal(n)
+    states[:, 5] = mean[1] + 3 * np.sqrt(cov[1, 1]) * rng.standard_normal(n)
+    chi = oracle_mod.chi2(states, t, v, sig, 1)
+    gamma = 2.38 / np.sqrt(2 * 2)
+    half = n // 2
+    samples = []
+    for gen in range(1500):
+        for first, other in ((0, half), (half, 0)):
+            partners = np.stack([other + rng.integers(0, half, half),
+                                 other + rng.integers(0, half, half)], axis=1)
+            eps = np.zeros((half, 6))
+            eps[:, 1] = 1e-4 * rng.standard_normal(half)
+            eps[:, 5] = 1e-4 * rng.standard_normal(half)
+            states, chi, _, _, _ = oracle_mod.demcmc_step(states, chi, t, v, sig, 1, first, half,
+                                                          gamma, partners, eps,
+                                                          rng.uniform(0, 1, half))
+        if gen >= 300:
+            samples.append(states[:, [1, 5]].copy())
+    s = np.concatenate(samples)
+    assert np.all(np.abs(s.mean(axis=0) - mean) < 0.1 * np.sqrt(np.diag(cov)))
+    assert np.allclose(np.cov(s.T), cov, rtol=0.15, atol=0.1 * np.sqrt(cov[0, 0] * cov[1, 1]))

@@ -47,6 +47,10 @@ MUTATIONS = [
     ("nll log term dropped", "0.5 * (wk * r * r + log(KCO_TWO_PI * var))", "0.5 * (wk * r * r)"),
     ("nll jitter gradient sign", "sj * wk * (1.0 - wk * r * r)", "sj * wk * (1.0 + wk * r * r)"),
     ("nll gradient factor", "double a = wk * r;", "double a = 2.0 * wk * r;"),
+    ("DE-MC acceptance sign", "log(u[c]) < -0.5 * (chi2_prop[c] - chi2[i])",
+     "log(u[c]) < 0.5 * (chi2_prop[c] - chi2[i])"),
+    ("DE-MC gamma dropped", "x = (states[i * n_par + p] + gamma * d) + eps[c * n_par + p];",
+     "x = (states[i * n_par + p] + d) + eps[c * n_par + p];"),
     ("prediction without gamma", "double V = par[5 * n_pl];\n            for (j = 0; j < n_pl; ++j) V +=",
      "double V = 0.0;\n            for (j = 0; j < n_pl; ++j) V +="),
 ]
