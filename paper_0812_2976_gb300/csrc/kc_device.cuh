@@ -31,51 +31,65 @@ constexpr int kItersF32 = 3;
 
 // ------------------------------------------------ conversions (integer pipe)
 
-// double -> float, round to nearest even, by bit manipulation.  Exact IEEE
-// result for normal float results; zero, subnormal, huge and non-finite
-// inputs take the conversion instruction (rare).
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+// All of them are branch-free: on GB300 a conversion with a rarely taken
+// double-precision fallback branch measured three times the latency of the
+// same code without it, and these conversions sit on the critical path of
+// every kernel's prologue.  Values outside the normal float range follow
+// flush-to-zero rules (results below 2^-126 become a signed zero, above the
+// float range a signed infinity; NaN stays NaN), like the .ftz arithmetic
+// of the kernels.
+
+// Float bits of the double with high word hi and low word lo, rounded to
+// nearest even; m and rest are the 23 kept and 29 dropped fraction bits.
+__device__ __forceinline__ unsigned d2f_bits(unsigned hi, unsigned lo, unsigned &m,
+                                             unsigned &rest, unsigned &up) {
   const unsigned ex = (hi >> 20) & 0x7ffu;
-  if (ex - 897u > 253u) return __double2float_rn(x);   // ex outside [897, 1150]
-  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;
-  unsigned f = (hi & 0x80000000u) | ((ex - 896u) << 23) | m;
-  f += (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
-  return __uint_as_float(f);
+  const unsigned sign = hi & 0x80000000u;
+  m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  rest = lo & 0x1fffffffu;
+  up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
+  unsigned f = ((sign | ((ex - 896u) << 23) | m) + up);
+  const unsigned special = (ex == 2047u && (((hi & 0xfffffu) | lo) != 0u)) ? 0x7fc00000u
+                                                                           : (sign | 0x7f800000u);
+  f = ex < 897u ? sign : f;
+  f = ex > 1150u ? special : f;
+  return f;
 }
 
-// float -> double, exact, by bit manipulation (normal inputs).
+// double -> float, round to nearest even, by bit manipulation.
+__device__ __forceinline__ float d2f(double x) {
+  unsigned m, rest, up;
+  return __uint_as_float(d2f_bits((unsigned)__double2hiint(x), (unsigned)__double2loint(x), m,
+                                  rest, up));
+}
+
+// float -> double, exact, by bit manipulation.
 __device__ __forceinline__ double f2d(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned ex = (b >> 23) & 0xffu;
-  if (ex - 1u > 253u) return (double)f;                // zero, subnormal, inf, nan
-  const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  return __hiloint2double((int)hi, (int)(b << 29));
+  const unsigned sign = b & 0x80000000u;
+  unsigned hi = sign | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  unsigned lo = b << 29;
+  hi = ex == 0u ? sign : hi;
+  lo = ex == 0u ? 0u : lo;
+  hi = ex == 255u ? (sign | 0x7ff00000u | ((b & 0x7fffffu) >> 3)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // x = hi + lo with hi = RN(x), lo = RN(x - hi): a double as a pair of floats
-// (48 significant bits), by bit manipulation.
+// (48 significant bits), by bit manipulation.  lo is zero when x lies
+// outside [2^-74, 2^127) (there only hi is kept).
 __device__ __forceinline__ void split_d(double x, float &hi, float &lo) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
   const unsigned ex = (h >> 20) & 0x7ffu;
-  if (ex - 949u > 201u) {             // outside [949, 1150]: tiny, huge, zero, nan
-    hi = __double2float_rn(x);
-    lo = __double2float_rn(x - (double)hi);
-    return;
-  }
-  const unsigned m = ((h & 0xfffffu) << 3) | (l >> 29);
-  const unsigned rest = l & 0x1fffffffu;
-  const unsigned up = (rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u));
-  const unsigned sign = h & 0x80000000u;
-  hi = __uint_as_float((sign | ((ex - 896u) << 23) | m) + up);
+  unsigned m, rest, up;
+  hi = __uint_as_float(d2f_bits(h, l, m, rest, up));
   // x - hi = (rest - up 2^29) 2^(ex - 1075), |.| <= 2^28 units
   const int r = (int)rest - (int)(up << 29);
-  const float scale = __uint_as_float((ex - 948u) << 23);   // 2^(ex - 1075)
-  const float lo_abs = __int2float_rn(r) * scale;
-  lo = sign ? -lo_abs : lo_abs;
+  const float scale = __uint_as_float(((ex - 948u) & 0xffu) << 23);   // 2^(ex - 1075)
+  float lo_abs = __int2float_rn(r) * scale;
+  lo_abs = (ex - 949u > 201u) ? 0.0f : lo_abs;
+  lo = (h & 0x80000000u) ? -lo_abs : lo_abs;
 }
 
 // ------------------------------------------------ FP32 building blocks
@@ -331,9 +345,18 @@ struct PlanetF {
   float n_hi, n_lo, c_hi, c_lo, e, A, B, C;
 };
 
+// Parameter checks on the bit patterns (integer pipe, no FP64 compares):
+// finite P > 0; K, w, M0 finite; 0 <= e < 1 (-0 counts as 0).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+
 __device__ __forceinline__ bool planet_valid(double P, double K, double e, double w, double M0) {
-  return isfinite(P) && P > 0.0 && isfinite(K) && isfinite(e) && e >= 0.0 && e < 1.0 &&
-         isfinite(w) && isfinite(M0);
+  const long long pb = __double_as_longlong(P), eb = __double_as_longlong(e);
+  const long long emag = eb & 0x7fffffffffffffffll;
+  const bool p_ok = pb > 0 && pb < 0x7ff0000000000000ll;            // +0 < P < +inf
+  const bool e_ok = (eb >= 0 || emag == 0) && emag < 0x3ff0000000000000ll;   // [0, 1)
+  return p_ok && e_ok && finite_bits(K) && finite_bits(w) && finite_bits(M0);
 }
 
 // 1/P as a double-double n + nl (|nl| < 2^-52 n): single-precision seed and
@@ -386,16 +409,158 @@ __device__ __forceinline__ PlanetD planet_setup_f64(const double *p, double dref
   return q;
 }
 
-__device__ __forceinline__ PlanetF planet_setup_mixed(const double *p, double dref) {
-  const double P = p[0], K = p[1], e = p[2], w = p[3], M0 = p[4];
-  PlanetF q;
+// ------------------------------------------------ float expansions (setup)
+
+// a b = p + err exactly (the FMA remainder).
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &err) {
+  p = __fmul_rn(a, b);
+  err = __fmaf_rn(a, b, -p);
+}
+
+// s + err == a + b exactly when |a| >= |b| (or a == 0).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &err) {
+  s = __fadd_rn(a, b);
+  err = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// hi + lo += x, the rounding error of the leading add kept exactly.
+__device__ __forceinline__ void expansion_add(float &hi, float &lo, float x) {
+  float s, err;
+  two_sum(hi, x, s, err);
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// x = x0 + x1 + x2 exactly (24 + 24 + 5 significant bits) by bit
+// manipulation, for x = 0 or 2^-74 <= |x| < 2^127 (elsewhere x1 = x2 = 0 and
+// x0 follows the flush-to-zero rules of d2f).
+__device__ __forceinline__ void split3_d(double x, float &x0, float &x1, float &x2) {
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned ex = (h >> 20) & 0x7ffu;
+  unsigned m, rest, up;
+  x0 = __uint_as_float(d2f_bits(h, l, m, rest, up));
+  // x - x0 = r 2^(ex - 1075) with |r| <= 2^28: r = RN24(r) + (a 5-bit rest)
+  const int r = (int)rest - (int)(up << 29);
+  const float r1 = __int2float_rn(r);
+  const int r2 = r - __float2int_rz(r1);                   // exact, |r2| <= 16
+  const float scale = __uint_as_float(((ex - 948u) & 0xffu) << 23);   // 2^(ex - 1075)
+  const bool in_range = ex - 949u <= 201u;
+  const float y1 = in_range ? r1 * scale : 0.0f;
+  const float y2 = in_range ? __int2float_rn(r2) * scale : 0.0f;
+  const bool neg = (h & 0x80000000u) != 0u;
+  x1 = neg ? -y1 : y1;
+  x2 = neg ? -y2 : y2;
+}
+
+struct Split3 {
+  float x0, x1, x2;
+};
+
+__device__ __forceinline__ Split3 split3(double x) {
+  Split3 r;
+  split3_d(x, r.x0, r.x1, r.x2);
+  return r;
+}
+
+// a - b as a float pair hi + lo (about 2^-48 relative) from exact splits of
+// the doubles a and b: no FP64 instruction.
+__device__ __forceinline__ void sub_ds(const Split3 &a, const Split3 &b, float &hi, float &lo) {
+  float h, l;
+  two_sum(a.x0, -b.x0, h, l);
+  expansion_add(h, l, a.x1);
+  expansion_add(h, l, -b.x1);
+  expansion_add(h, l, a.x2);
+  expansion_add(h, l, -b.x2);
+  fast_two_sum(h, l, hi, lo);
+}
+
+constexpr float kInvTwoPiHi = 0.15915493667125702f;       // RN(1/(2 pi))
+constexpr float kInvTwoPiLo = 6.4206382432985265e-09f;    // 1/(2 pi) - hi
+
+// The same quantities in double-double arithmetic, for periods or epochs
+// outside the range of the float-expansion code below (out of line).
+static __device__ __noinline__ void phase_setup_wide(double P, double M0, double t_ref, double t0,
+                                              float &n_hi, float &n_lo, float &c_hi,
+                                              float &c_lo) {
   double n, nl;
   recip_checked(P, n, nl);
   float nlo2;
-  split_d(n, q.n_hi, nlo2);
-  q.n_lo = nlo2 + d2f(nl);
-  const double c = phase_cycles(dref, n, nl, M0 * kInvTwoPi);
-  split_d(c, q.c_hi, q.c_lo);
+  split_d(n, n_hi, nlo2);
+  n_lo = nlo2 + d2f(nl);
+  split_d(phase_cycles(t_ref - t0, n, nl, M0 * kInvTwoPi), c_hi, c_lo);
+}
+
+// 1/P and the phase offset of the mixed path in float expansions (no FP64
+// instruction: the FP64 pipe runs at 1/64 of the FP32 rate).  With exact
+// three-float splits P = P0 + P1 + P2, t_ref = r0 + r1 + r2, t0 = e0 + e1 + e2:
+//   1/P = n_hi + n_lo: r = 1/P0 (MUFU), x = 1 - P r carried from the exact
+//     product P0 r (|x| < 2^-21), 1/P = r (1 + x + x^2); relative error
+//     about 2^-45, below 1e-9 cycles over 3e4 periods;
+//   frac((t_ref - t0)/P): D0 = RN(r0 - e0), k = the integer nearest to
+//     D0 n_hi, and the remainder rho = (t_ref - t0) - k P summed from the
+//     split terms, products by FMA remainders and sums by TwoSum, starting
+//     with the cancelling pair D0 - k P0 so that the running sum stays of
+//     the size of P; then rho (n_hi + n_lo) with |rho/P| < 3: error about
+//     1e-14 cycles.
+// Valid for 2^-20 <= P <= 2^40 d and |t_ref - t0| < 2^24 P; outside that
+// range the double-double code of the FP64 path is used (rare).
+__device__ __forceinline__ void phase_setup_ds(double P, double M0, double t_ref, double t0,
+                                               float &n_hi, float &n_lo, float &c_hi,
+                                               float &c_lo) {
+  const Split3 Ps = split3(P), tr = split3(t_ref), te = split3(t0);
+  float D0, D1;
+  two_sum(tr.x0, -te.x0, D0, D1);
+  if (!(Ps.x0 >= 0x1p-20f && Ps.x0 <= 0x1p40f && fabsf(D0) < 0x1p24f * Ps.x0)) {
+    phase_setup_wide(P, M0, t_ref, t0, n_hi, n_lo, c_hi, c_lo);
+    return;
+  }
+  const float r = rcp_fast(Ps.x0);
+  float pr, pre;
+  two_prod(Ps.x0, r, pr, pre);
+  const float x = __fmaf_rn(-Ps.x1, r, __fsub_rn(__fsub_rn(1.0f, pr), pre));  // 1 - pr exact
+  fast_two_sum(r, r * __fmaf_rn(x, x, x), n_hi, n_lo);
+  // rho = (t_ref - t0) - k P
+  const float k = rintf(D0 * n_hi);
+  float a0, a0e, a1, a1e, a2, a2e;
+  two_prod(k, Ps.x0, a0, a0e);
+  two_prod(k, Ps.x1, a1, a1e);
+  two_prod(k, Ps.x2, a2, a2e);
+  float hi, lo;
+  two_sum(D0, -a0, hi, lo);
+  expansion_add(hi, lo, D1);
+  expansion_add(hi, lo, -a0e);
+  expansion_add(hi, lo, tr.x1);
+  expansion_add(hi, lo, -te.x1);
+  expansion_add(hi, lo, -a1);
+  expansion_add(hi, lo, tr.x2);
+  expansion_add(hi, lo, -te.x2);
+  expansion_add(hi, lo, -a1e);
+  expansion_add(hi, lo, -a2);
+  expansion_add(hi, lo, -a2e);
+  float rh, rl;
+  fast_two_sum(hi, lo, rh, rl);
+  // cycles = rho (n_hi + n_lo) + M0/(2 pi), reduced to [-1/2, 1/2]
+  float u, ue;
+  two_prod(rh, n_hi, u, ue);
+  const float t_small = __fmaf_rn(rh, n_lo, __fmaf_rn(rl, n_hi, ue));
+  float mh0, ml0;
+  split_d(M0, mh0, ml0);
+  float mh, me;
+  two_prod(mh0, kInvTwoPiHi, mh, me);
+  const float ml = __fmaf_rn(mh0, kInvTwoPiLo, __fmaf_rn(ml0, kInvTwoPiHi, me));
+  float sc, se;
+  two_sum(u, mh, sc, se);
+  sc = __fsub_rn(sc, rintf(sc));                            // exact
+  fast_two_sum(sc, __fadd_rn(__fadd_rn(t_small, ml), se), c_hi, c_lo);
+}
+
+// Single-precision constants of one planet for the mixed path.
+// t_ref: the reference time the observation times are taken from; t0: the
+// epoch of M0.
+__device__ __forceinline__ PlanetF planet_setup_mixed(const double *p, double t_ref, double t0) {
+  const double P = p[0], K = p[1], e = p[2], w = p[3], M0 = p[4];
+  PlanetF q;
+  phase_setup_ds(P, M0, t_ref, t0, q.n_hi, q.n_lo, q.c_hi, q.c_lo);
   const float ef = d2f(e);
   q.e = ef;
   // sin/cos of w to single-precision rounding although w itself is double:

@@ -58,7 +58,7 @@ struct F64Layout {
 
 // gamma of system s, or NaN when any parameter of the system is invalid.
 __device__ inline double system_gamma(const double *p, int J) {
-  bool ok = isfinite(p[5 * J]);
+  bool ok = finite_bits(p[5 * J]);
   for (int j = 0; j < J; ++j)
     ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
   return ok ? p[5 * J] : __longlong_as_double(0x7ff8000000000000ll);
@@ -69,6 +69,12 @@ __device__ inline double system_gamma(const double *p, int J) {
 __device__ inline double system_jitter2(const double *p, int J) {
   const double sj = p[5 * J + 1];
   return isfinite(sj) ? sj * sj : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// The same as a float for the mixed path (no FP64 instruction).
+__device__ inline float system_jitter2_f(const double *p, int J) {
+  const float sj = d2f(p[5 * J + 1]);
+  return finite_bits(p[5 * J + 1]) ? sj * sj : __int_as_float(0x7fc00000);
 }
 
 __device__ __forceinline__ float lg2_fast(float x) {
@@ -129,7 +135,6 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   const int64_t sys0 = (int64_t)blockIdx.x * ST;
   const int npar = 5 * J + 1 + (NLL ? 1 : 0);
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
-  const double dref = t_ref - a.t0;
   const float jit2 = d2f(a.jitter2);
 
   if (PRE) {
@@ -145,20 +150,22 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       gam_s[i] = s < a.n_sys ? prep.gam[s] : 0.0f;
     }
   } else {
-    // per-(system, planet) constants, once, in FP64 (Eqs. 4/6 phase offset)
-    for (int i = setup_slot(tid, nwarps); i < ST * J; i += block) {
+    // per-(system, planet) constants, once (Eqs. 4/6 phase offset), packed
+    // into the first warps
+    for (int i = tid; i < ST * J; i += block) {
       const int sl = i / J, j = i - sl * J;
       const int64_t s = sys0 + sl;
       PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, dref);
+      if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, t_ref, a.t0);
       pl_s[i] = q;
     }
     for (int i = tid; i < ST; i += block) {
       const int64_t s = sys0 + i;
       gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
-      if (NLL) s2_s[i] = s < a.n_sys ? d2f(system_jitter2(a.params + s * npar, J)) : 0.0f;
+      if (NLL) s2_s[i] = s < a.n_sys ? system_jitter2_f(a.params + s * npar, J) : 0.0f;
     }
   }
+  const Split3 tr3 = split3(t_ref);
 
   const int sl = tid / G, c = tid - sl * G;
   const int64_t s = sys0 + sl;
@@ -176,7 +183,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
         w_s[k] = prep.w[k0 + k];
       } else {
         float th, tl, vh, vl;
-        split_d(a.t[k0 + k] - t_ref, th, tl);
+        sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
         split_d(a.v[k0 + k], vh, vl);
         obs_s[k] = make_float4(th, tl, vh, vl);
         const float sg = d2f(a.sigma[k0 + k]);
@@ -261,19 +268,19 @@ prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ g
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
-  const double dref = t_ref - a.t0;
   const float jit2 = d2f(a.jitter2);
   for (int64_t i = tid; i < a.n_sys * J; i += nth) {
     const int64_t s = i / J;
-    pl[i] = planet_setup_mixed(a.params + s * npar + 5 * (i - s * J), dref);
+    pl[i] = planet_setup_mixed(a.params + s * npar + 5 * (i - s * J), t_ref, a.t0);
   }
+  const Split3 tr3 = split3(t_ref);
   for (int64_t s = tid; s < a.n_sys; s += nth) {
     gam[s] = d2f(system_gamma(a.params + s * npar, J));
     if (counters) counters[s] = 0u;
   }
   for (int64_t k = tid; k < a.n_obs; k += nth) {
     float th, tl, vh, vl;
-    split_d(a.t[k] - t_ref, th, tl);
+    sub_ds(split3(a.t[k]), tr3, th, tl);
     split_d(a.v[k], vh, vl);
     obs[k] = make_float4(th, tl, vh, vl);
     const float sg = d2f(a.sigma[k]);

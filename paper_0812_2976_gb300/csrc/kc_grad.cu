@@ -42,9 +42,9 @@ struct GradPlanetD {
   double K, cw, sw, n2;
 };
 
-__device__ inline GradPlanetF grad_setup_mixed(const double *p, double dref) {
+__device__ inline GradPlanetF grad_setup_mixed(const double *p, double t_ref, double t0) {
   GradPlanetF g;
-  g.base = planet_setup_mixed(p, dref);
+  g.base = planet_setup_mixed(p, t_ref, t0);
   float w_hi, w_lo;
   split_d(p[3], w_hi, w_lo);
   float sw, cw;
@@ -71,7 +71,7 @@ __device__ inline GradPlanetD grad_setup_f64(const double *p, double dref) {
 __device__ inline double nan_d() { return __longlong_as_double(0x7ff8000000000000ll); }
 
 __device__ inline double system_gamma_g(const double *p, int J) {
-  bool ok = isfinite(p[5 * J]);
+  bool ok = finite_bits(p[5 * J]);
   for (int j = 0; j < J; ++j)
     ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
   return ok ? p[5 * J] : nan_d();
@@ -80,7 +80,7 @@ __device__ inline double system_gamma_g(const double *p, int J) {
 // Free jitter of a system whose parameters end with (gamma, sigma_j).
 __device__ inline double system_jitter_g(const double *p, int J) {
   const double sj = p[5 * J + 1];
-  return isfinite(sj) ? sj : nan_d();
+  return finite_bits(sj) ? sj : nan_d();
 }
 
 __device__ __forceinline__ float lg2_fast_g(float x) {
@@ -167,21 +167,20 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
   const int tid = threadIdx.x;
   const int64_t sys0 = (int64_t)blockIdx.x * ST;
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
-  const double dref = t_ref - a.t0;
-  const float dref_f = d2f(dref);
+  const Split3 tr3 = split3(t_ref), te3 = split3(a.t0);
+  const float dref_f = (tr3.x0 - te3.x0) + (tr3.x1 - te3.x1);     // t_ref - t0, float
   const float jit2 = d2f(a.jitter2);
-  const int nwarps = block >> 5;
 
-  for (int i = (tid & 31) * nwarps + (tid >> 5); i < ST * J; i += block) {
+  for (int i = tid; i < ST * J; i += block) {
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
     GradPlanetF q = {};
-    if (s < a.n_sys) q = grad_setup_mixed(a.params + s * NP + 5 * j, dref);
+    if (s < a.n_sys) q = grad_setup_mixed(a.params + s * NP + 5 * j, t_ref, a.t0);
     pl_s[i] = q;
   }
   for (int i = tid; i < ST; i += block) {
     const int64_t s = sys0 + i;
-    gam_s[i] = s < a.n_sys ? (float)system_gamma_g(a.params + s * NP, J) : 0.0f;
+    gam_s[i] = s < a.n_sys ? d2f(system_gamma_g(a.params + s * NP, J)) : 0.0f;
     if (NLL) sj_s[i] = s < a.n_sys ? d2f(system_jitter_g(a.params + s * NP, J)) : 0.0f;
   }
 
@@ -201,9 +200,8 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     const int nk = min(obs_tile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
-      const double tk = a.t[k0 + k];
       float th, tl, vh, vl;
-      split_d(tk - t_ref, th, tl);
+      sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
       split_d(a.v[k0 + k], vh, vl);
       obs_s[k] = make_float4(th, tl, vh, vl);
       const float sg = d2f(a.sigma[k0 + k]);

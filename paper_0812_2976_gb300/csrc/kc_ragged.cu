@@ -34,7 +34,7 @@ namespace {
 __device__ inline double nan_r() { return __longlong_as_double(0x7ff8000000000000ll); }
 
 __device__ inline double system_gamma_r(const double *p, int J) {
-  bool ok = isfinite(p[5 * J]);
+  bool ok = finite_bits(p[5 * J]);
   for (int j = 0; j < J; ++j)
     ok = ok && planet_valid(p[5 * j], p[5 * j + 1], p[5 * j + 2], p[5 * j + 3], p[5 * j + 4]);
   return ok ? p[5 * J] : nan_r();
@@ -55,14 +55,19 @@ __global__ void prep_obs_mixed(RaggedDev d, const double *__restrict__ t,
     const int64_t o0 = d.obs_off[s], o1 = d.obs_off[s + 1];
     const double tr = o1 > o0 ? t[o0] : d.t0;
     if (lane == 0) t_ref[s] = tr;
+    // no FP64 instruction: differences from exact three-float splits
+    const Split3 tr3 = split3(tr), te3 = split3(d.t0);
+    const float jit2 = d2f(jitter2);
     for (int64_t k = o0 + lane; k < o1; k += 32) {
+      const Split3 tk = split3(t[k]);
       float th, tl, vh, vl;
-      split_d(t[k] - tr, th, tl);
+      sub_ds(tk, tr3, th, tl);
       split_d(v[k], vh, vl);
       oa[k] = make_float4(th, tl, vh, vl);
-      const double var = fma(sigma[k], sigma[k], jitter2);
-      ob[k] = make_float2(var > 0.0 ? d2f(1.0 / var) : __int_as_float(0x7fc00000),
-                          d2f(t[k] - d.t0));
+      const float sg = d2f(sigma[k]);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      ob[k] = make_float2(var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000),
+                          (tk.x0 - te3.x0) + (tk.x1 - te3.x1));
     }
   }
 }
@@ -127,9 +132,9 @@ struct RPlanetD {
   double K, cw, sw, n2;
 };
 
-__device__ inline RPlanetF rsetup_mixed(const double *p, double dref, bool grad) {
+__device__ inline RPlanetF rsetup_mixed(const double *p, double t_ref, double t0, bool grad) {
   RPlanetF g;
-  g.base = planet_setup_mixed(p, dref);
+  g.base = planet_setup_mixed(p, t_ref, t0);
   g.K = g.cw = g.sw = g.beta = g.n2 = 0.0f;
   if (grad) {
     float w_hi, w_lo;
@@ -354,8 +359,7 @@ ragged_mixed_kernel(RaggedDev d, const float4 *__restrict__ oa, const float2 *__
     const int64_t o0 = d.obs_off[s];
     const int n = (int)(d.obs_off[s + 1] - o0);
     const double *p = params + d.par_off[s];
-    const double dref = d.t_ref[s] - d.t0;
-    if (lane < J) pl[lane] = rsetup_mixed(p + 5 * lane, dref, GRAD);
+    if (lane < J) pl[lane] = rsetup_mixed(p + 5 * lane, d.t_ref[s], d.t0, GRAD);
     const float gam = d2f(system_gamma_r(p, J));
     __syncwarp();
     float *gout = GRAD ? grad + d.par_off[s] : nullptr;
