@@ -136,6 +136,20 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   const int npar = 5 * J + 1 + (NLL ? 1 : 0);
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   const float jit2 = d2f(a.jitter2);
+  const Split3 tr3 = split3(t_ref);
+  const int nk0 = min(obs_tile, a.n_obs);
+
+  // tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jit^2) (NLL keeps
+  // sigma_k^2: its weight depends on each system's own jitter)
+  auto stage = [&](int slot, double t, double v, double sigma) {
+    float th, tl, vh, vl;
+    sub_ds(split3(t), tr3, th, tl);
+    split_d(v, vh, vl);
+    obs_s[slot] = make_float4(th, tl, vh, vl);
+    const float sg = d2f(sigma);
+    const float var = __fmaf_rn(sg, sg, jit2);
+    w_s[slot] = NLL ? sg * sg : (var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000));
+  };
 
   if (PRE) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -149,55 +163,75 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       const int64_t s = sys0 + i;
       gam_s[i] = s < a.n_sys ? prep.gam[s] : 0.0f;
     }
+    for (int k = tid; k < nk0; k += block) {
+      obs_s[k] = prep.obs[k];
+      w_s[k] = prep.w[k];
+    }
   } else {
-    // per-(system, planet) constants, once (Eqs. 4/6 phase offset), packed
-    // into the first warps
+    // Prologue, all latency: the loads of the first observation tile go out
+    // before the planet setup so that the two overlap.
+    const bool has0 = tid < nk0, has1 = tid + block < nk0;
+    double t0v = 0.0, v0v = 0.0, s0v = 0.0, t1v = 0.0, v1v = 0.0, s1v = 0.0;
+    if (has0) { t0v = a.t[tid]; v0v = a.v[tid]; s0v = a.sigma[tid]; }
+    if (has1) { t1v = a.t[tid + block]; v1v = a.v[tid + block]; s1v = a.sigma[tid + block]; }
+    // per-(system, planet) constants, once (Eqs. 4/6 phase offset); an
+    // invalid planet carries e = NaN, which poisons its system's chi2
     for (int i = tid; i < ST * J; i += block) {
       const int sl = i / J, j = i - sl * J;
       const int64_t s = sys0 + sl;
       PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (s < a.n_sys) q = planet_setup_mixed(a.params + s * npar + 5 * j, t_ref, a.t0);
+      if (s < a.n_sys) {
+        const double *p = a.params + s * npar + 5 * j;
+        q = planet_setup_mixed(p, t_ref, a.t0);
+        if (!planet_valid(p[0], p[1], p[2], p[3], p[4])) q.e = __int_as_float(0x7fc00000);
+      }
       pl_s[i] = q;
     }
     for (int i = tid; i < ST; i += block) {
       const int64_t s = sys0 + i;
-      gam_s[i] = s < a.n_sys ? d2f(system_gamma(a.params + s * npar, J)) : 0.0f;
+      float g = 0.0f;
+      if (s < a.n_sys) {
+        const double gd = a.params[s * npar + 5 * J];
+        g = finite_bits(gd) ? d2f(gd) : __int_as_float(0x7fc00000);
+      }
+      gam_s[i] = g;
       if (NLL) s2_s[i] = s < a.n_sys ? system_jitter2_f(a.params + s * npar, J) : 0.0f;
     }
+    if (has0) stage(tid, t0v, v0v, s0v);
+    if (has1) stage(tid + block, t1v, v1v, s1v);
+    for (int k = tid + 2 * block; k < nk0; k += block) stage(k, a.t[k], a.v[k], a.sigma[k]);
   }
-  const Split3 tr3 = split3(t_ref);
+  __syncthreads();
 
   const int sl = tid / G, c = tid - sl * G;
   const int64_t s = sys0 + sl;
   const bool want_resid = resid_out != nullptr;
   Kahan acc = {0.0f, 0.0f};
   float rmax = 0.0f;
+  const float gam = gam_s[sl];
+  const float s2 = NLL ? s2_s[sl] : 0.0f;
+  PlanetF q[J];
+  float poison = 0.0f * gam + (NLL ? 0.0f * s2 : 0.0f);   // NaN for an invalid system
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    q[j] = pl_s[sl * J + j];
+    poison += 0.0f * q[j].e;
+  }
 
   for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
     const int nk = min(obs_tile, a.n_obs - k0);
-    __syncthreads();
-    // stage: tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jit^2)
-    for (int k = tid; k < nk; k += block) {
-      if (PRE) {
-        obs_s[k] = prep.obs[k0 + k];
-        w_s[k] = prep.w[k0 + k];
-      } else {
-        float th, tl, vh, vl;
-        sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
-        split_d(a.v[k0 + k], vh, vl);
-        obs_s[k] = make_float4(th, tl, vh, vl);
-        const float sg = d2f(a.sigma[k0 + k]);
-        const float var = __fmaf_rn(sg, sg, jit2);
-        // NLL keeps sigma_k^2: the weight depends on the system's own jitter
-        w_s[k] = NLL ? sg * sg : (var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000));
+    if (k0 > 0) {
+      __syncthreads();
+      for (int k = tid; k < nk; k += block) {
+        if (PRE) {
+          obs_s[k] = prep.obs[k0 + k];
+          w_s[k] = prep.w[k0 + k];
+        } else {
+          stage(k, a.t[k0 + k], a.v[k0 + k], a.sigma[k0 + k]);
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
-    const float gam = gam_s[sl];
-    const float s2 = NLL ? s2_s[sl] : 0.0f;
-    PlanetF q[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) q[j] = pl_s[sl * J + j];
     for (int k = c; k < nk; k += G) {
       const float4 o = obs_s[k];
       Kahan V = {0.0f, 0.0f};
@@ -246,8 +280,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     }
   }
   if (c == 0 && s < a.n_sys) {
-    // 0 * gamma turns an invalid system into NaN even when n_obs == 0
-    const float poison = 0.0f * gam_s[sl] + (NLL ? 0.0f * s2_s[sl] : 0.0f);
+    // the poison turns an invalid system into NaN even when n_obs == 0
     out[s] = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2Pi) + poison
                  : kahan_value(acc) + poison;
     if (resid_out) resid_out[s] = rmax;
