@@ -32,7 +32,9 @@
  *  - Physically invalid parameters (P <= 0, e outside [0, 1), non-finite
  *    values) give NaN for that system; a non-positive or NaN variance gives
  *    NaN for every system, an infinite one a zero weight.  Nothing traps:
- *    every device loop has a fixed trip count.
+ *    every device loop has a fixed trip count.  Each system whose result
+ *    comes out NaN also adds one to a per-device counter read (and reset)
+ *    by kc_last_device_error.
  *  - n_sys == 0 is a no-op.  n_obs == 0 gives chi2 = 0 (NaN if invalid).
  *  - Calls are thread-safe; concurrent calls on different streams do not
  *    share device memory.
@@ -63,8 +65,13 @@ typedef enum kc_status {
  *  KC_MIXED - the phase frac((t-t0)/P) in pair-of-single (double-single)
  *             arithmetic, Kepler's equation, the velocities and the residuals
  *             in single precision, with compensated (Kahan) sums for the
- *             planet velocities and for chi2 (Sec. 4.4). */
-typedef enum kc_mode { KC_FP64 = 0, KC_MIXED = 1 } kc_mode;
+ *             planet velocities and for chi2 (Sec. 4.4).
+ *  KC_FP32  - every step in single precision, observation times and periods
+ *             included: Sec. 5's pure single-precision variant, whose worst
+ *             chi2 error the paper puts at one part in ten.  Accepted by
+ *             kc_chi2_eval_ex only (float output), for precision comparisons;
+ *             not an accurate path for absolute times t/P >> 1e3. */
+typedef enum kc_mode { KC_FP64 = 0, KC_MIXED = 1, KC_FP32 = 2 } kc_mode;
 
 #define KC_MAX_PLANETS 8        /* n_pl range: 1 .. KC_MAX_PLANETS           */
 #define KC_MAX_OBS (1 << 24)    /* n_obs range: 0 .. KC_MAX_OBS              */
@@ -318,6 +325,28 @@ const char *kc_status_string(kc_status status);
 
 /* Detail of the calling thread's last non-OK status ("" if none). */
 const char *kc_last_error(void);
+
+/* Number of systems whose result came out NaN (invalid parameters or
+ * observations, convention above) in every evaluation on the current device
+ * since the previous call, then resets that count to zero.  The paper has no
+ * counterpart (its kernels return chi2 only); the count lets a caller notice
+ * invalid models without scanning the outputs.  Synchronises the current
+ * device first, so an asynchronous fault of an earlier launch is reported
+ * here as KC_ERR_CUDA (with *n_invalid = 0).  Evaluations made by
+ * kc_demcmc_step on its proposals are counted too.  n_invalid must not be
+ * NULL (KC_ERR_ARG). */
+kc_status kc_last_device_error(int64_t *n_invalid);
+
+/* Measured throughput of one arithmetic pipe of the current GPU, in
+ * operations per SM per SM-clock cycle: pipe 0 = FP32 FMA, 1 = FP64 FMA.
+ * The roofline denominators of the two paths (the paper quotes none; the
+ * FP64 rate of this part is 1/64 of its FP32 rate).  Runs one CTA of 1024
+ * threads per SM with eight independent FMA chains per thread and divides
+ * the FMAs each CTA executed by its SM-clock cycles (clock64), so the result
+ * does not depend on the clock frequency.  Blocking: synchronises `stream`;
+ * allocates and frees its own scratch.  KC_ERR_ARG for another pipe or a
+ * NULL result pointer. */
+kc_status kc_measure_pipe_rate(int32_t pipe, double *ops_per_sm_clock, kc_stream stream);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int32_t kc_version(void);

@@ -17,15 +17,15 @@ from typing import Optional, Tuple
 import torch
 
 from . import _lib
-from ._lib import KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
+from ._lib import KC_FP32, KC_FP64, KC_MIXED, KC_MAX_PLANETS, KcError
 
 __all__ = [
-    "KC_FP64", "KC_MIXED", "KC_MAX_PLANETS", "KcError",
+    "KC_FP64", "KC_MIXED", "KC_FP32", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
     "kc_chi2_eval_mixed_noalloc", "kc_nll_eval", "kc_nll_grad", "nll",
     "kc_demcmc_step", "DEMCMC",
     "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
-    "RaggedPlan", "chi2", "n_planets", "library_path",
+    "RaggedPlan", "chi2", "n_planets", "library_path", "kc_last_device_error", "kc_measure_pipe_rate",
 ]
 
 library_path = _lib.LIB_PATH
@@ -36,6 +36,8 @@ def _mode(mode) -> int:
         return KC_FP64
     if mode in (KC_MIXED, "mixed"):
         return KC_MIXED
+    if mode in (KC_FP32, "fp32", "single"):
+        return KC_FP32      # kc_chi2_eval_ex only: the all-single-precision comparison
     raise ValueError(f"unknown mode {mode!r}: use 'fp64' or 'mixed'")
 
 
@@ -101,6 +103,25 @@ def kc_chi2_eval_ex(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.
         t.numel(), float(t0), float(jitter), m, out.data_ptr(), _ptr(resid),
         _stream(stream)), "kc_chi2_eval_ex")
     return (out, resid) if resid is not None else out
+
+
+def kc_measure_pipe_rate(pipe: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput per SM per clock of the FP32 ('fp32') or FP64
+    ('fp64') pipe (kc_measure_pipe_rate; blocking)."""
+    r = ctypes.c_double(0.0)
+    lib = _lib.load()
+    _lib.check(lib.kc_measure_pipe_rate({"fp32": 0, "fp64": 1}[pipe], ctypes.byref(r),
+                                        _stream(stream)), "kc_measure_pipe_rate")
+    return float(r.value)
+
+
+def kc_last_device_error() -> int:
+    """Systems whose result came out NaN since the previous call on the
+    current device (kc_last_device_error; synchronises the device)."""
+    n = ctypes.c_int64(0)
+    lib = _lib.load()
+    _lib.check(lib.kc_last_device_error(ctypes.byref(n)), "kc_last_device_error")
+    return int(n.value)
 
 
 def kc_chi2_eval(params, t, v_obs, sigma, out=None, stream=None) -> torch.Tensor:

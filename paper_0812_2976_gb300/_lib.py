@@ -13,7 +13,7 @@ import threading
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkc.so")
 
 KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_NOMEM, KC_ERR_UNSUPPORTED = range(5)
-KC_FP64, KC_MIXED = 0, 1
+KC_FP64, KC_MIXED, KC_FP32 = 0, 1, 2
 KC_MAX_PLANETS = 8
 
 _lock = threading.Lock()
@@ -66,6 +66,8 @@ SIGNATURES = {
     "kc_autotune": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _i32, _i32, _tile_p,
                            ctypes.POINTER(ctypes.c_float), _st]),
     "kc_status_string": (ctypes.c_char_p, [_i32]),
+    "kc_last_device_error": (_i32, [ctypes.POINTER(_i64)]),
+    "kc_measure_pipe_rate": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), _st]),
     "kc_last_error": (ctypes.c_char_p, []),
     "kc_version": (_i32, []),
 }

@@ -74,6 +74,32 @@ cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st) {
   return cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 256, pool, st);
 }
 
+namespace {
+// Systems whose result came out NaN (invalid parameters or observations),
+// summed over every launch on the device since the last read.
+__device__ unsigned long long g_invalid_systems = 0ull;
+std::mutex g_inv_mu;
+std::map<int, unsigned long long *> g_inv_addr;
+}  // namespace
+
+unsigned long long *invalid_counter() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_inv_mu);
+  auto it = g_inv_addr.find(dev);
+  if (it != g_inv_addr.end()) return it->second;
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_invalid_systems) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  g_inv_addr[dev] = static_cast<unsigned long long *>(p);
+  return static_cast<unsigned long long *>(p);
+}
+
 }  // namespace kc
 
 using kc::cuda_status;
@@ -193,6 +219,51 @@ const char *kc_status_string(kc_status s) {
 
 const char *kc_last_error(void) { return g_last_error.c_str(); }
 
+kc_status kc_measure_pipe_rate(int32_t pipe, double *ops_per_sm_clock, kc_stream stream) {
+  const char *fn = "kc_measure_pipe_rate";
+  if (!ops_per_sm_clock) return fail(KC_ERR_ARG, "%s: NULL pointer", fn);
+  if (pipe != 0 && pipe != 1) return fail(KC_ERR_ARG, "%s: pipe must be 0 (FP32) or 1 (FP64)", fn);
+  *ops_per_sm_clock = 0.0;
+  int dev = 0, n_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_status(e, fn);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool f64 = pipe == 1;
+  const int iters = f64 ? 256 : 16384;     // a few ms either way
+  void *sink = nullptr;
+  long long *cyc_d = nullptr;
+  e = cudaMallocAsync(&sink, (size_t)n_sm * 1024 * (f64 ? 8 : 4), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&cyc_d, sizeof(long long) * n_sm, s);
+  std::vector<long long> cyc(n_sm, 0);
+  if (e == cudaSuccess) e = kc::probe_fma_rate(f64, n_sm, iters / 4, sink, cyc_d, s);  // warm-up
+  if (e == cudaSuccess) e = kc::probe_fma_rate(f64, n_sm, iters, sink, cyc_d, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cyc.data(), cyc_d, sizeof(long long) * n_sm, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (sink) cudaFreeAsync(sink, s);
+  if (cyc_d) cudaFreeAsync(cyc_d, s);
+  if (e != cudaSuccess) return cuda_status(e, fn);
+  // the slowest CTA sets the rate an SM sustains
+  long long worst = 1;
+  for (long long c : cyc) worst = c > worst ? c : worst;
+  *ops_per_sm_clock = 1024.0 * 8.0 * iters / (double)worst;
+  return ok();
+}
+
+kc_status kc_last_device_error(int64_t *n_invalid) {
+  if (!n_invalid) return fail(KC_ERR_ARG, "kc_last_device_error: NULL pointer");
+  *n_invalid = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e, "kc_last_device_error: device");
+  unsigned long long n = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&n, kc::g_invalid_systems, sizeof(n));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(kc::g_invalid_systems, &zero, sizeof(zero));
+  if (e != cudaSuccess) return cuda_status(e, "kc_last_device_error: counter");
+  *n_invalid = (int64_t)n;
+  return ok();
+}
+
 int32_t kc_version(void) { return 100; }
 
 kc_status kc_chi2_eval_ex(const double *params, const double *t, const double *v_obs,
@@ -202,11 +273,12 @@ kc_status kc_chi2_eval_ex(const double *params, const double *t, const double *v
   kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, out,
                                "kc_chi2_eval_ex");
   if (st != KC_OK) return st;
-  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_chi2_eval_ex: bad mode");
+  if (mode != KC_FP64 && mode != KC_MIXED && mode != KC_FP32)
+    return fail(KC_ERR_ARG, "kc_chi2_eval_ex: bad mode");
   if (!std::isfinite(t0) || !std::isfinite(jitter))
     return fail(KC_ERR_ARG, "kc_chi2_eval_ex: t0 and jitter must be finite");
   if (n_sys == 0) return ok();
-  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter, kc::invalid_counter()};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == KC_FP64) {
     const Tile tile = kc::choose_tile(Kind::Chi2F64, n_sys, n_pl, n_obs);
@@ -214,6 +286,11 @@ kc_status kc_chi2_eval_ex(const double *params, const double *t, const double *v
                                            max_kepler_resid, s),
                        "kc_chi2_eval_ex (fp64)");
   }
+  if (mode == KC_FP32)
+    return cuda_status(kc::launch_chi2_single(a, kc::default_tile(Kind::Chi2Mixed, n_sys, n_pl,
+                                                                  n_obs),
+                                              static_cast<float *>(out), max_kepler_resid, s),
+                       "kc_chi2_eval_ex (fp32)");
   const Tile tile = kc::choose_tile(Kind::Chi2Mixed, n_sys, n_pl, n_obs);
   return cuda_status(kc::launch_chi2_mixed(a, tile, static_cast<float *>(out),
                                            max_kepler_resid, s),
@@ -245,7 +322,7 @@ kc_status kc_chi2_grad(const double *params, const double *t, const double *v_ob
   if (!std::isfinite(t0) || !std::isfinite(jitter))
     return fail(KC_ERR_ARG, "kc_chi2_grad: t0 and jitter must be finite");
   if (n_sys == 0) return ok();
-  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter, kc::invalid_counter()};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == KC_FP64) {
     const Tile tile = kc::choose_tile(Kind::GradF64, n_sys, n_pl, n_obs);
@@ -276,7 +353,7 @@ kc_status kc_nll_eval(const double *params, const double *t, const double *v_obs
   if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_nll_eval: bad mode");
   if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_nll_eval: t0 must be finite");
   if (n_sys == 0) return ok();
-  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0};
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0, kc::invalid_counter()};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == KC_FP64)
     return cuda_status(kc::launch_nll_f64(a, nll_tile(Kind::Chi2F64, n_sys, n_pl, n_obs),
@@ -296,7 +373,7 @@ kc_status kc_nll_grad(const double *params, const double *t, const double *v_obs
   if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "kc_nll_grad: bad mode");
   if (!std::isfinite(t0)) return fail(KC_ERR_ARG, "kc_nll_grad: t0 must be finite");
   if (n_sys == 0) return ok();
-  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0};
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, 0.0, kc::invalid_counter()};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (mode == KC_FP64)
     return cuda_status(kc::launch_grad_f64(a, nll_tile(Kind::GradF64, n_sys, n_pl, n_obs),
@@ -466,7 +543,7 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, 0.0, 0.0};
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, 0.0, 0.0, kc::invalid_counter()};
   auto launch = [&](const Tile &tile) -> cudaError_t {
     switch (kind) {
       case kc::Kind::Chi2F64: return kc::launch_chi2_f64(a, tile, (double *)chi, nullptr, s);

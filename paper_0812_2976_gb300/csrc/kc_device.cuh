@@ -596,6 +596,14 @@ __device__ __forceinline__ float mean_anomaly_mixed(float tau_hi, float tau_lo, 
   return (u + lo) * kTwoPiF;
 }
 
+// Pure single precision (the paper's all-float variant, for comparisons):
+// tau = t - t0 as one float, so the phase loses ~|tau/P| 2^-24 cycles.
+__device__ __forceinline__ float mean_anomaly_single(float tau, const PlanetF &q) {
+  float x = __fmaf_rn(tau, q.n_hi, q.c_hi);
+  x = __fsub_rn(x, rintf(x));
+  return x * kTwoPiF;
+}
+
 __device__ __forceinline__ double mean_anomaly_f64(double tau, const PlanetD &q) {
   const double p = __dmul_rn(tau, q.inv_P);
   const double pe = fma(tau, q.inv_P, -p);

@@ -115,7 +115,10 @@ struct MixedPrep {
 // NLL = true (with PRE = false): every system carries its own jitter after
 // gamma and the kernel returns the negative log-likelihood
 //   1/2 sum_k [r_k^2/(sigma_k^2 + sigma_j^2) + ln(2 pi (sigma_k^2 + sigma_j^2))].
-template <int J, bool PRE, bool NLL = false>
+// SINGLE = true (with PRE = false): the pure single-precision variant of
+// Sec. 5 (precision comparisons only): times, epoch and periods rounded to
+// float and the phase formed in float.
+template <int J, bool PRE, bool NLL = false, bool SINGLE = false>
 __global__ void __launch_bounds__(256, 2)
 chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__restrict__ out,
                   float *__restrict__ resid_out) {
@@ -143,7 +146,12 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   // sigma_k^2: its weight depends on each system's own jitter)
   auto stage = [&](int slot, double t, double v, double sigma) {
     float th, tl, vh, vl;
-    sub_ds(split3(t), tr3, th, tl);
+    if (SINGLE) {
+      th = __fsub_rn(d2f(t), d2f(a.t0));
+      tl = 0.0f;
+    } else {
+      sub_ds(split3(t), tr3, th, tl);
+    }
     split_d(v, vh, vl);
     obs_s[slot] = make_float4(th, tl, vh, vl);
     const float sg = d2f(sigma);
@@ -183,6 +191,12 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       if (s < a.n_sys) {
         const double *p = a.params + s * npar + 5 * j;
         q = planet_setup_mixed(p, t_ref, a.t0);
+        if (SINGLE) {     // 1/P and M0/(2 pi) in float, the phase taken from t - t0
+          q.n_hi = 1.0f / d2f(p[0]);
+          q.n_lo = 0.0f;
+          q.c_hi = d2f(p[4]) * (1.0f / kTwoPiF);
+          q.c_lo = 0.0f;
+        }
         if (!planet_valid(p[0], p[1], p[2], p[3], p[4])) q.e = __int_as_float(0x7fc00000);
       }
       pl_s[i] = q;
@@ -237,7 +251,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       Kahan V = {0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        const float M = mean_anomaly_mixed(o.x, o.y, q[j]);
+        const float M = SINGLE ? mean_anomaly_single(o.x, q[j]) : mean_anomaly_mixed(o.x, o.y, q[j]);
         float sE, cE;
         const float E = kepler_f32(M, q[j].e, sE, cE);
         if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
@@ -281,8 +295,10 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   }
   if (c == 0 && s < a.n_sys) {
     // the poison turns an invalid system into NaN even when n_obs == 0
-    out[s] = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2Pi) + poison
-                 : kahan_value(acc) + poison;
+    const float value = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2Pi) + poison
+                            : kahan_value(acc) + poison;
+    out[s] = value;
+    note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = rmax;
   }
 }
@@ -406,6 +422,7 @@ chi2_mixed_chunk_kernel(UniformArgs a, MixedPrep prep, ChunkScratch cs, int chun
   }
   if (lane == 0) {
     out[s] = kahan_value(m) + 0.0f * gam;
+    note_invalid(a.invalid, out[s]);
     if (resid_out) resid_out[s] = rm;
   }
 }
@@ -509,6 +526,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   if (c == 0 && s < a.n_sys) {
     const double poison = 0.0 * gam_s[sl] + (NLL ? 0.0 * s2_s[sl] : 0.0);
     out[s] = NLL ? 0.5 * (acc + a.n_obs * kLn2Pi) + poison : acc + poison;
+    note_invalid(a.invalid, out[s]);
     if (resid_out) resid_out[s] = (float)rmax;
   }
 }
@@ -739,6 +757,24 @@ cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
   if (err == cudaSuccess)                                                            \
     chi2_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
                                                         resid);
+  KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chi2_single(const UniformArgs &a, const Tile &tile, float *out, float *resid,
+                               cudaStream_t st) {
+  const size_t smem = smem_chi2_mixed(a.n_pl, tile);
+  const int grid = grid_for(a.n_sys, tile.block / tile.G);
+  const MixedPrep none{nullptr, nullptr, nullptr, nullptr};
+  cudaError_t err = cudaSuccess;
+#define KC_LAUNCH(JJ)                                                                         \
+  err = set_smem(chi2_mixed_kernel<JJ, false, false, true>, smem);                            \
+  if (err == cudaSuccess)                                                                     \
+    chi2_mixed_kernel<JJ, false, false, true><<<grid, tile.block, smem, st>>>(a, none, tile.G,  \
+                                                                              tile.obs_tile,  \
+                                                                              out, resid);
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;

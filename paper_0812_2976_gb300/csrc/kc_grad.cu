@@ -272,9 +272,10 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
   if (c == 0 && s < a.n_sys) {
     // NaN for an invalid system
     const float poison = 0.0f * gam_s[sl] + (NLL ? 0.0f * sj_s[sl] : 0.0f);
-    if (chi2_out)
-      chi2_out[s] = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2PiG) + poison
-                        : kahan_value(acc) + poison;
+    const float value = NLL ? 0.5f * (kahan_value(acc) + (float)a.n_obs * (float)kLn2PiG) + poison
+                            : kahan_value(acc) + poison;
+    if (chi2_out) chi2_out[s] = value;
+    note_invalid(a.invalid, value);
 #pragma unroll
     for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
   }
@@ -384,7 +385,9 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
   }
   if (c == 0 && s < a.n_sys) {
     const double poison = 0.0 * gam_s[sl] + (NLL ? 0.0 * sj_s[sl] : 0.0);
-    if (chi2_out) chi2_out[s] = NLL ? 0.5 * (acc + a.n_obs * kLn2PiG) + poison : acc + poison;
+    const double value = NLL ? 0.5 * (acc + a.n_obs * kLn2PiG) + poison : acc + poison;
+    if (chi2_out) chi2_out[s] = value;
+    note_invalid(a.invalid, value);
 #pragma unroll
     for (int i = 0; i < NP; ++i) grad_out[s * NP + i] = g[i] + poison;
   }

@@ -30,7 +30,20 @@ struct UniformArgs {
   int n_obs;
   double t0;
   double jitter2;
+  // device counter of systems whose result is NaN (invalid inputs); may be
+  // NULL (kc_last_device_error reads it)
+  unsigned long long *invalid;
 };
+
+// The library's per-device invalid-system counter (kc_api.cu); NULL if its
+// address cannot be obtained.
+unsigned long long *invalid_counter();
+
+// Counts a NaN result (one atomic per invalid system).
+template <typename T>
+__device__ __forceinline__ void note_invalid(unsigned long long *ctr, T value) {
+  if (ctr != nullptr && value != value) atomicAdd(ctr, 1ull);
+}
 
 // Stream-ordered scratch from the library's per-device memory pool
 // (kc_api.cu); freed with cudaFreeAsync on the same stream.
@@ -45,6 +58,16 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
                                        float *out, float *resid, cudaStream_t st);
 cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
                             float *resid, cudaStream_t st);
+// FMA-pipe throughput probe (kc_probe.cu): one CTA of 1024 threads per SM
+// (grid n_sm), eight FMA chains per thread, iters steps; writes each CTA's
+// SM-clock cycles to cycles[n_sm]; sink is [n_sm * 1024] of the type.
+cudaError_t probe_fma_rate(bool f64, int n_sm, int iters, void *sink, long long *cycles,
+                           cudaStream_t st);
+
+// Pure single-precision variant (KC_FP32, a precision comparison only):
+// the fused mixed kernel with times and periods rounded to float.
+cudaError_t launch_chi2_single(const UniformArgs &a, const Tile &tile, float *out, float *resid,
+                               cudaStream_t st);
 cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out,
                               float *resid, cudaStream_t st);
 // Gradient (kc_grad.cu); nll = true: the free-jitter log-likelihood variant

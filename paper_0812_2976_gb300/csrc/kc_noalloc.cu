@@ -79,7 +79,8 @@ extern "C" kc_status kc_chi2_eval_mixed_noalloc(const double *params, const doub
   if (e != cudaSuccess) return kc::cuda_status(e, "kc_chi2_eval_mixed_noalloc: scratch address");
   // Nothing in the array has to start at zero: the preparation kernel of this
   // call writes every byte the main kernel then reads.
-  const kc::UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter};
+  const kc::UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter,
+                          kc::invalid_counter()};
   kc::Tile tile = kc::choose_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);
   if (tile.G > tile.block || tile.split == 2)
     tile = kc::default_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);

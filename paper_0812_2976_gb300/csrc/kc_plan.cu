@@ -40,7 +40,8 @@ struct kc_plan {
   std::mutex mu;
 
   kc::RaggedDev dev() const {
-    return kc::RaggedDev{d_obs_off, d_par_off, d_n_pl, d_order, d_t_ref, n_sys, t0};
+    return kc::RaggedDev{d_obs_off, d_par_off, d_n_pl, d_order, d_t_ref, n_sys, t0,
+                         kc::invalid_counter()};
   }
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);

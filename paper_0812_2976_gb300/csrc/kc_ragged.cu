@@ -366,6 +366,7 @@ ragged_mixed_kernel(RaggedDev d, const float4 *__restrict__ oa, const float2 *__
 #define KC_BODY(JJ) body_mixed<JJ, GRAD>(pl, gam, oa, ob, o0, n, lane, chi2 + s, gout)
     KC_RAGGED_SWITCH(KC_BODY)
 #undef KC_BODY
+    if (lane == 0) note_invalid(d.invalid, chi2[s]);      // lane 0 wrote it
     __syncwarp();
   }
 }
@@ -396,6 +397,7 @@ ragged_f64_kernel(RaggedDev d, const ObsR64 *__restrict__ od, const double *__re
 #define KC_BODY(JJ) body_f64<JJ, GRAD>(pl, gam, od, o0, n, lane, chi2 + s, gout)
     KC_RAGGED_SWITCH(KC_BODY)
 #undef KC_BODY
+    if (lane == 0) note_invalid(d.invalid, chi2[s]);      // lane 0 wrote it
     __syncwarp();
   }
 }

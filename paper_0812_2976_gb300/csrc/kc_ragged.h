@@ -25,6 +25,7 @@ struct RaggedDev {
   const double *t_ref;
   int64_t n_sys;
   double t0;
+  unsigned long long *invalid;   // NaN-result counter (kc_last_device_error) or NULL
 };
 
 // Converts t, v, sigma (device, [obs_off[n_sys]]) to the kernel's form:

@@ -29,7 +29,8 @@ def test_header_declares_the_documented_entry_points():
     names = declared_functions()
     for want in ("kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
                  "kc_rv_predict", "kc_kepler_solve", "kc_status_string", "kc_last_error",
-                 "kc_version"):
+                 "kc_last_device_error", "kc_plan_create_ragged", "kc_plan_run",
+                 "kc_plan_destroy", "kc_version"):
         assert want in names
 
 
@@ -70,6 +71,7 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.kc_chi2_eval_ex(p, p, p, p, 4, 2, 8, float("nan"), 0.0, 1, p, None, None) == 1
     assert lib.kc_kepler_solve(p, p, -1, 0, p, None) == 1
     assert lib.kc_rv_predict(p, p, 2, 0, 4, 0.0, p, None) == 1
+    assert lib.kc_last_device_error(None) == 1
 
 
 def test_empty_batches_are_no_ops(lib):

@@ -78,6 +78,22 @@ def test_config1_paper_batch(kc, oracle_mod):
     assert float(resid.max()) <= RESID_TOL
 
 
+def test_pure_single_precision_ablation(kc, oracle_mod):
+    """Sec. 5: phases formed in single precision from absolute times give
+    chi2 errors of order one part in ten; the double-single phase of the
+    mixed path keeps them below 1e-5 on the same data (t0 = 0, t ~ 2.45e6 d)."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1, n_sys=1024)
+    v = observed(oracle_mod, w)
+    ref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    e_mixed = rel_err(kc.kc_chi2_eval_ex(P, T, V, S, mode="mixed").cpu().numpy(), ref)
+    e_single = rel_err(kc.kc_chi2_eval_ex(P, T, V, S, mode="fp32").cpu().numpy(), ref)
+    assert e_mixed.max() <= MIXED_TOL
+    assert e_single.max() >= 1e-2, e_single.max()
+    assert np.median(e_single) > 100 * np.median(e_mixed)
+
+
 # ------------------------------------------------------------ config 2
 
 def test_config2_grid_sweep_full_size_sampled(kc, oracle_mod):
@@ -197,9 +213,14 @@ def test_empty_and_invalid(kc, oracle_mod):
     v = rng.normal(0, 5, 16)
     sig = np.ones(16)
     P, T, V, S = dev(par, t, v, sig)
+    kc.kc_last_device_error()                         # reset the counter
     for mode in ("fp64", "mixed"):
         out = kc.kc_chi2_eval_ex(P, T, V, S, mode=mode).cpu().numpy()
         assert np.all(np.isnan(out[[3, 5, 7]]))
+        assert kc.kc_last_device_error() == 3         # one count per invalid system
+        _, g = kc.kc_chi2_grad(P, T, V, S, mode=mode)
+        assert np.all(np.isnan(g.cpu().numpy()[[3, 5, 7]]))
+        assert kc.kc_last_device_error() == 3
         ok = np.setdiff1d(np.arange(10), [3, 5, 7])
         assert np.all(np.isfinite(out[ok]))
         # no observations: chi2 = 0 for valid systems, NaN for invalid ones
@@ -209,6 +230,7 @@ def test_empty_and_invalid(kc, oracle_mod):
         S_bad = S.clone()
         S_bad[4] = 0.0
         assert np.all(np.isnan(kc.kc_chi2_eval_ex(P, T, V, S_bad, mode=mode).cpu().numpy()))
+        assert kc.kc_last_device_error() == 3 + 10        # the n_obs = 0 call and S_bad
     # empty batch
     empty = kc.kc_chi2_eval(P[:0], T, V, S)
     assert empty.numel() == 0
