@@ -102,6 +102,9 @@ def bind(lib):
     lib.kco_demcmc_step.argtypes = [d, d, i64, ctypes.c_int, d, d, d, i64, ctypes.c_double,
                                     ctypes.c_double, i64, i64, ctypes.c_double, i32p, d, d, d,
                                     d, i32p]
+    lib.kco_gauss_newton.argtypes = [d, d, d, i64, ctypes.c_int, i64, ctypes.c_double,
+                                     ctypes.c_double, d]
+    lib.kco_gauss_newton.restype = ctypes.c_int
     lib.kco_kepler_batch.argtypes = [d, d, i64, d, i32p]
     lib.kco_mean_anomaly_batch.argtypes = [d, ctypes.c_double, d, d, i64, d]
     lib.kco_true_anomaly_batch.argtypes = [d, d, i64, d]
@@ -193,6 +196,33 @@ def chi2(params, t, v, sigma, n_pl: int, t0: float = 0.0,
     if rc != 0:
         raise ValueError("oracle.chi2: bad sizes")
     return (out, g) if grad else out
+
+
+def gauss_newton(params, t, sigma, n_pl: int, t0: float = 0.0, jitter: float = 0.0,
+                 packed: bool = True):
+    """Gauss-Newton matrix H = sum_k w_k J_k J_k^T of every system (J_k =
+    dV_k/dtheta over the 5*n_pl + 1 parameters): [n_sys, n(n+1)/2] packed
+    upper triangle row by row, or [n_sys, n, n] with packed=False."""
+    params, t, sigma = _f64(params), _f64(t), _f64(sigma)
+    n_par = 5 * n_pl + 1
+    params = params.reshape(-1, n_par)
+    n_sys = params.shape[0]
+    H = np.empty((n_sys, n_par * (n_par + 1) // 2))
+    rc = _load().kco_gauss_newton(_p(params), _p(t), _p(sigma), n_sys, int(n_pl), t.size,
+                                  float(t0), float(jitter), _p(H))
+    if rc != 0:
+        raise ValueError("oracle.gauss_newton: bad sizes")
+    return H if packed else unpack_symmetric(H, n_par)
+
+
+def unpack_symmetric(H, n: int):
+    """[..., n(n+1)/2] packed upper triangle (row by row) -> [..., n, n]."""
+    H = np.asarray(H)
+    iu = np.triu_indices(n)
+    full = np.zeros(H.shape[:-1] + (n, n))
+    full[..., iu[0], iu[1]] = H
+    full[..., iu[1], iu[0]] = H
+    return full
 
 
 def nll(params, t, v, sigma, n_pl: int, t0: float = 0.0, grad: bool = False):

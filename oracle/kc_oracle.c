@@ -429,6 +429,64 @@ int kco_demcmc_step(double *states, double *chi2, int64_t n_chains, int n_pl,
     return 0;
 }
 
+/* ------------------------------------------- Gauss-Newton normal matrix */
+
+/* H = sum_k w_k J_k J_k^T of one system, J_k = dV_k/dtheta over its
+ * 5*n_pl + 1 parameters (the planets' (P, K, e, omega, M0), then gamma),
+ * w_k = 1/(sigma_k^2 + jitter^2): the matrix of the normal equations of a
+ * Gauss-Newton / Levenberg-Marquardt step (derivatives for least-squares
+ * refinement, Sec. 6).  The Hessian of chi2 is 2 H + 2 sum_k w_k r_k
+ * d2V_k/dtheta2, so at zero residuals it is 2 H.  Written as the packed
+ * upper triangle, row by row: H[0][0..n-1], H[1][1..n-1], ...
+ * (n (n + 1)/2 values).  NaN everywhere for invalid parameters or a
+ * non-positive variance; an infinite variance is a zero weight. */
+static void kco_gn_system(const double *par, int n_pl, const double *t,
+                          const double *sigma, int64_t n_obs, double t0,
+                          double jitter, double *H)
+{
+    int n_par = 5 * n_pl + 1, n_tri = n_par * (n_par + 1) / 2;
+    kco_sum acc[(5 * 8 + 1) * (5 * 8 + 2) / 2];
+    double J[5 * 8 + 1];
+    int j, p, q, i;
+    int64_t k;
+    int valid = isfinite(par[5 * n_pl]);
+    for (j = 0; j < n_pl; ++j) valid = valid && kco_planet_valid(par + 5 * j);
+    if (!valid) {
+        for (i = 0; i < n_tri; ++i) H[i] = NAN;
+        return;
+    }
+    for (i = 0; i < n_tri; ++i) { acc[i].s = 0.0; acc[i].c = 0.0; }
+    for (k = 0; k < n_obs; ++k) {
+        double var = sigma[k] * sigma[k] + jitter * jitter;
+        double wk = 1.0 / var;
+        if (!(var > 0.0)) {
+            for (i = 0; i < n_tri; ++i) H[i] = NAN;
+            return;
+        }
+        for (j = 0; j < n_pl; ++j) kco_planet_velocity_grad(par + 5 * j, t[k], t0, J + 5 * j);
+        J[5 * n_pl] = 1.0;                                        /* dV/dgamma */
+        i = 0;
+        for (p = 0; p < n_par; ++p)
+            for (q = p; q < n_par; ++q) kco_sum_add(&acc[i++], wk * J[p] * J[q]);
+    }
+    for (i = 0; i < n_tri; ++i) H[i] = kco_sum_value(&acc[i]);
+}
+
+/* Uniform batch: H [n_sys][n (n + 1)/2] with n = 5*n_pl + 1 (n_pl <= 8). */
+int kco_gauss_newton(const double *params, const double *t, const double *sigma,
+                     int64_t n_sys, int n_pl, int64_t n_obs, double t0,
+                     double jitter, double *H)
+{
+    int64_t s;
+    int n_par = 5 * n_pl + 1, n_tri = n_par * (n_par + 1) / 2;
+    if (n_pl < 1 || n_pl > 8 || n_obs < 0 || n_sys < 0) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (s = 0; s < n_sys; ++s)
+        kco_gn_system(params + s * n_par, n_pl, t, sigma, n_obs, t0, jitter,
+                      H + s * n_tri);
+    return 0;
+}
+
 /* Elementwise Kepler solve (E for each (M, e) pair). */
 void kco_kepler_batch(const double *M, const double *e, int64_t n, double *E,
                       int32_t *n_iter)

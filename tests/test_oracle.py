@@ -519,3 +519,81 @@ def test_demcmc_samples_the_linear_gaussian_posterior(oracle_mod):
     s = np.concatenate(samples)
     assert np.all(np.abs(s.mean(axis=0) - mean) < 0.1 * np.sqrt(np.diag(cov)))
     assert np.allclose(np.cov(s.T), cov, rtol=0.15, atol=0.1 * np.sqrt(cov[0, 0] * cov[1, 1]))
+
+
+# ------------------------------------------------ Gauss-Newton matrix
+
+def test_gauss_newton_is_half_the_hessian_at_zero_residual(oracle_mod):
+    """With noise-free data from the same parameters every residual is zero,
+    so the Hessian of chi2 is exactly 2 sum_k w_k J_k J_k^T: its central
+    differences of the (separately pinned) analytic gradient must give 2H."""
+    rng = np.random.default_rng(31)
+    n_pl, n_obs, t0 = 2, 50, 2450000.0
+    par = _random_systems(rng, 3, n_pl, e_max=0.7)
+    t = np.sort(rng.uniform(2450000, 2451500, n_obs))
+    sig = rng.uniform(1, 5, n_obs)
+    H = oracle_mod.gauss_newton(par, t, sig, n_pl, t0=t0, packed=False)
+    for s in range(par.shape[0]):
+        v = oracle_mod.predict(par[s], t, n_pl, t0)[0]          # r_k = 0
+        n = par.shape[1]
+        hess = np.empty((n, n))
+        for q in range(n):
+            h = 1e-5 * max(abs(par[s, q]), 1e-2)
+            if q % 5 == 0 and q < 5 * n_pl:
+                P = par[s, q]
+                h = 1e-3 * P * P / (2 * np.pi * np.max(np.abs(t - t0)))
+            p1, p2 = par[s].copy(), par[s].copy()
+            p1[q] += h
+            p2[q] -= h
+            g1 = oracle_mod.chi2(p1[None], t, v, sig, n_pl, t0=t0, grad=True)[1][0]
+            g2 = oracle_mod.chi2(p2[None], t, v, sig, n_pl, t0=t0, grad=True)[1][0]
+            hess[:, q] = (g1 - g2) / (2 * h)
+        d = np.sqrt(np.abs(np.diag(2 * H[s])))
+        scale = np.maximum(np.outer(d, d), 1e-12)
+        assert np.max(np.abs(hess - 2 * H[s]) / scale) < 1e-5
+
+
+def test_gauss_newton_circular_closed_form(oracle_mod):
+    """e = 0: v = K cos(w + M) + gamma with M = 2 pi (t - t0)/P + M0, so the
+    (P, K, w, M0, gamma) block of H has a closed form."""
+    rng = np.random.default_rng(32)
+    P, K, w, M0, gam, t0 = 23.0, 17.0, 0.7, 2.1, 1.5, 2450100.0
+    t = np.sort(rng.uniform(2450000, 2451000, 45))
+    sig = rng.uniform(1, 4, 45)
+    H = oracle_mod.gauss_newton([P, K, 0.0, w, M0, gam], t, sig, 1, t0=t0, packed=False)[0]
+    ph = w + TWO_PI * (t - t0) / P + M0
+    J = np.stack([K * np.sin(ph) * TWO_PI * (t - t0) / P ** 2,   # dv/dP
+                  np.cos(ph),                                   # dv/dK
+                  -K * np.sin(ph),                              # dv/dw
+                  -K * np.sin(ph),                              # dv/dM0
+                  np.ones_like(t)], axis=1)                     # dv/dgamma
+    ref = J.T @ (J / sig[:, None] ** 2)
+    idx = [0, 1, 3, 4, 5]
+    sub = H[np.ix_(idx, idx)]
+    d = np.sqrt(np.diag(ref))
+    assert np.max(np.abs(sub - ref) / np.outer(d, d)) < 1e-12
+
+
+def test_gauss_newton_structure(oracle_mod):
+    """Symmetric positive semi-definite; a zero-weight (infinite sigma)
+    observation changes nothing; doubling every sigma divides H by 4; the
+    jitter adds in quadrature; invalid parameters give NaN."""
+    rng = np.random.default_rng(33)
+    par = _random_systems(rng, 4, 3)
+    t = np.sort(rng.uniform(2450000, 2452000, 30))
+    sig = rng.uniform(1, 5, 30)
+    H = oracle_mod.gauss_newton(par, t, sig, 3, packed=False)
+    for s in range(4):
+        ev = np.linalg.eigvalsh(H[s])
+        assert ev.min() > -1e-9 * ev.max()
+    t2, s2 = np.append(t, 2452500.0), np.append(sig, np.inf)
+    assert np.array_equal(oracle_mod.gauss_newton(par, t2, s2, 3), oracle_mod.gauss_newton(par, t, sig, 3))
+    Hp = oracle_mod.gauss_newton(par, t, sig, 3)
+    assert np.allclose(oracle_mod.gauss_newton(par, t, 2 * sig, 3), Hp / 4, rtol=1e-13, atol=0)
+    sig_j = np.sqrt(sig ** 2 - 0.5)
+    assert np.allclose(oracle_mod.gauss_newton(par, t, sig_j, 3, jitter=np.sqrt(0.5)), Hp,
+                       rtol=1e-12, atol=0)
+    bad = par.copy()
+    bad[1, 2] = 1.2
+    Hb = oracle_mod.gauss_newton(bad, t, sig, 3)
+    assert np.all(np.isnan(Hb[1])) and np.all(np.isfinite(Hb[[0, 2, 3]]))

@@ -51,6 +51,12 @@ MUTATIONS = [
      "log(u[c]) < 0.5 * (chi2_prop[c] - chi2[i])"),
     ("DE-MC gamma dropped", "x = (states[i * n_par + p] + gamma * d) + eps[c * n_par + p];",
      "x = (states[i * n_par + p] + d) + eps[c * n_par + p];"),
+    ("Gauss-Newton weight dropped", "kco_sum_add(&acc[i++], wk * J[p] * J[q]);",
+     "kco_sum_add(&acc[i++], J[p] * J[q]);"),
+    ("Gauss-Newton index", "kco_sum_add(&acc[i++], wk * J[p] * J[q]);",
+     "kco_sum_add(&acc[i++], wk * J[p] * J[p]);"),
+    ("Gauss-Newton gamma column", "J[5 * n_pl] = 1.0;                                        /* dV/dgamma */",
+     "J[5 * n_pl] = 0.0;"),
     ("prediction without gamma", "double V = par[5 * n_pl];\n            for (j = 0; j < n_pl; ++j) V +=",
      "double V = 0.0;\n            for (j = 0; j < n_pl; ++j) V +="),
 ]
