@@ -117,8 +117,9 @@ def grid_sweep_throughput(kc, synth, dev, stream, args):
 
 def gradient_throughput(kc, synth, dev, stream, args):
     """Config 3 (65536 systems, n_pl 3, n_obs 512, t0 = 2450000): chi2 and
-    its gradient in one adjoint launch, and the free-jitter log-likelihood
-    with its gradient, mixed precision."""
+    its gradient in one adjoint launch, the same plus the Gauss-Newton matrix
+    (16 x 16 per system), and the free-jitter log-likelihood with its
+    gradient, mixed precision; the FP64 adjoint."""
     import torch
     w = synth.uniform(3)
     P = torch.tensor(w.params, device=dev)
@@ -133,6 +134,9 @@ def gradient_throughput(kc, synth, dev, stream, args):
     out = {"n_sys": w.n_sys, "unit": "planet-obs evals/s"}
     for name, fn in (("chi2_grad", lambda: kc.kc_chi2_grad(P, T, V, S, t0=w.t0, mode="mixed",
                                                            stream=stream)),
+                     ("gauss_newton", lambda: kc.kc_chi2_gauss_newton(P, T, V, S, t0=w.t0,
+                                                                      mode="mixed",
+                                                                      stream=stream)),
                      ("nll_grad", lambda: kc.kc_nll_grad(PJ, T, V, S, t0=w.t0, mode="mixed",
                                                          stream=stream)),
                      ("chi2_grad_fp64", lambda: kc.kc_chi2_grad(P, T, V, S, t0=w.t0,

@@ -119,6 +119,26 @@ kc_status kc_chi2_grad(const double *params, const double *t,
                        double jitter, kc_mode mode, void *chi2_out,
                        void *grad_out, kc_stream stream);
 
+/* Gauss-Newton normal matrix (derivatives for least-squares refinement,
+ * which Sec. 6 lists as future work): for every system
+ *   H = sum_k w_k J_k J_k^T,  J_k = dV_k/dtheta over its n = 5*n_pl + 1
+ *   parameters, w_k = 1/(sigma_k^2 + jitter^2),
+ * the matrix of a Levenberg-Marquardt step (the chi2 Hessian is 2H plus a
+ * term proportional to the residuals), together with chi2 and its gradient
+ * from the same pass (chi2_out and grad_out may be NULL; grad_out as in
+ * kc_chi2_grad).  jtj_out: [n_sys][n (n + 1)/2], the upper triangle packed
+ * row by row (H[0][0..n-1], H[1][1..n-1], ...); float for KC_MIXED, double
+ * for KC_FP64.  KC_MIXED forms the per-batch update H += U^T U (U: 32
+ * observations x n, rows sqrt(w_k) J_k) on the tensor cores with TF32
+ * inputs split in two (error about 1e-6 of sqrt(H_pp H_qq)).  Invalid
+ * systems give NaN in all their outputs.  Errors as kc_chi2_grad. */
+kc_status kc_chi2_gauss_newton(const double *params, const double *t,
+                               const double *v_obs, const double *sigma,
+                               int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                               double t0, double jitter, kc_mode mode,
+                               void *chi2_out, void *grad_out, void *jtj_out,
+                               kc_stream stream);
+
 /* Free jitter: each system carries its own jitter sigma_j after gamma
  * (params [n_sys][5*n_pl + 2]) and the statistic is the Gaussian negative
  * log-likelihood whose exponent is Eq. 5's chi2 with that sigma_j,

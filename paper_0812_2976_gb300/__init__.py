@@ -23,7 +23,7 @@ __all__ = [
     "KC_FP64", "KC_MIXED", "KC_FP32", "KC_MAX_PLANETS", "KcError",
     "kc_chi2_eval", "kc_chi2_eval_mixed", "kc_chi2_eval_ex", "kc_chi2_grad",
     "kc_chi2_eval_mixed_noalloc", "kc_nll_eval", "kc_nll_grad", "nll",
-    "kc_demcmc_step", "DEMCMC",
+    "kc_demcmc_step", "DEMCMC", "kc_chi2_gauss_newton",
     "kc_rv_predict", "kc_rv_predict_ragged", "kc_kepler_solve", "kc_autotune", "kc_set_tile", "kc_get_tile",
     "RaggedPlan", "chi2", "n_planets", "library_path", "kc_last_device_error", "kc_measure_pipe_rate",
 ]
@@ -196,6 +196,32 @@ def kc_chi2_grad(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
         n_planets(params), t.numel(), float(t0), float(jitter), m, chi2_out.data_ptr(),
         grad_out.data_ptr(), _stream(stream)), "kc_chi2_grad")
     return chi2_out, grad_out
+
+
+def kc_chi2_gauss_newton(params, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
+                         mode="mixed", chi2_out=None, grad_out=None, jtj_out=None,
+                         stream=None):
+    """(chi2 [n_sys], gradient [n_sys, n], Gauss-Newton matrix [n_sys, n(n+1)/2]
+    packed upper triangle row by row), n = 5*n_pl + 1 (kc_chi2_gauss_newton)."""
+    params = _dev_f64("params", params, 2)
+    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    m = _mode(mode)
+    if m not in (KC_FP64, KC_MIXED):
+        raise ValueError("kc_chi2_gauss_newton takes 'fp64' or 'mixed'")
+    dtype = torch.float64 if m == KC_FP64 else torch.float32
+    n_sys, n = params.shape[0], params.shape[1]
+    if chi2_out is None:
+        chi2_out = torch.empty(n_sys, dtype=dtype, device=params.device)
+    if grad_out is None:
+        grad_out = torch.empty((n_sys, n), dtype=dtype, device=params.device)
+    if jtj_out is None:
+        jtj_out = torch.empty((n_sys, n * (n + 1) // 2), dtype=dtype, device=params.device)
+    lib = _lib.load()
+    _lib.check(lib.kc_chi2_gauss_newton(
+        params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), n_sys,
+        n_planets(params), t.numel(), float(t0), float(jitter), m, chi2_out.data_ptr(),
+        grad_out.data_ptr(), jtj_out.data_ptr(), _stream(stream)), "kc_chi2_gauss_newton")
+    return chi2_out, grad_out, jtj_out
 
 
 def n_planets_nll(params: torch.Tensor) -> int:

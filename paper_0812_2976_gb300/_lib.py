@@ -46,6 +46,8 @@ SIGNATURES = {
                                           _d, _st]),
     "kc_chi2_grad": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _i32, _d,
                             _d, _st]),
+    "kc_chi2_gauss_newton": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _f64, _i32, _d, _d,
+                                     _d, _st]),
     "kc_nll_eval": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _i32, _d, _st]),
     "kc_nll_grad": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _i32, _d, _d, _st]),
     "kc_demcmc_step": (_i32, [_d, _d, _i64, _i32, _d, _d, _d, _i32, _f64, _f64, _i32, _i64,

@@ -345,6 +345,27 @@ static Tile nll_tile(Kind kind, int64_t n_sys, int32_t n_pl, int32_t n_obs) {
   return tile;
 }
 
+kc_status kc_chi2_gauss_newton(const double *params, const double *t, const double *v_obs,
+                               const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs,
+                               double t0, double jitter, kc_mode mode, void *chi2_out,
+                               void *grad_out, void *jtj_out, kc_stream stream) {
+  const char *fn = "kc_chi2_gauss_newton";
+  kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, jtj_out, fn);
+  if (st != KC_OK) return st;
+  if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "%s: bad mode", fn);
+  if (!std::isfinite(t0) || !std::isfinite(jitter))
+    return fail(KC_ERR_ARG, "%s: t0 and jitter must be finite", fn);
+  const uintptr_t al = mode == KC_FP64 ? 7 : 3;
+  if (((uintptr_t)chi2_out | (uintptr_t)grad_out | (uintptr_t)jtj_out) & al)
+    return fail(KC_ERR_ARG, "%s: output not aligned for its type", fn);
+  if (n_sys == 0) return ok();
+  UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter,
+                kc::invalid_counter()};
+  return cuda_status(kc::launch_gauss_newton(a, mode == KC_FP64, chi2_out, grad_out, jtj_out,
+                                             reinterpret_cast<cudaStream_t>(stream)),
+                     fn);
+}
+
 kc_status kc_nll_eval(const double *params, const double *t, const double *v_obs,
                       const double *sigma, int64_t n_sys, int32_t n_pl, int32_t n_obs, double t0,
                       kc_mode mode, void *out, kc_stream stream) {

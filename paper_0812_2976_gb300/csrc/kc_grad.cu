@@ -393,6 +393,406 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
   }
 }
 
+// ------------------------------------------------------------ Gauss-Newton
+//
+// H = sum_k w_k J_k J_k^T per system (J_k = dV_k/dtheta), with chi2 and its
+// gradient from the same pass: the matrix and the right-hand side of a
+// Levenberg-Marquardt step (Sec. 6 lists derivatives for least-squares
+// refinement as future work).  One warp per system; each lane evaluates one
+// observation of a batch of 32 and writes u_k = sqrt(w_k) J_k as a row of a
+// 32 x n matrix U in shared memory; the warp then adds U^T U to its
+// accumulators.  Mixed path: that update is a rank-32 dense contraction per
+// batch on the tensor cores (mma.sync m16n8k8, TF32 inputs in the three-
+// product split hi*hi + hi*lo + lo*hi, FP32 accumulation), only the tiles
+// on or above the diagonal.  FP64 path: FMAs on the FP64 pipe, the packed
+// upper-triangle entries spread over the lanes.
+
+constexpr int kGnWarps = 4;      // mixed: systems (warps) per CTA
+constexpr int kGnWarpsD = 2;     // FP64
+constexpr int kGnObsTile = 256;
+
+__host__ __device__ constexpr int gn_np(int J) { return 5 * J + 1; }
+__host__ __device__ constexpr int gn_mt(int J) { return (gn_np(J) + 15) / 16; }
+__host__ __device__ constexpr int gn_nt(int J) { return (gn_np(J) + 7) / 8; }
+// Row stride of U (floats): covers the tiled width and is 8 mod 32, so the
+// fragment loads of a warp (8 rows x 4 columns of a tile) hit 32 banks.
+__host__ __device__ constexpr int gn_row(int J) {
+  return ((gn_mt(J) * 16 > gn_nt(J) * 8 ? gn_mt(J) * 16 : gn_nt(J) * 8) + 23) / 32 * 32 + 8;
+}
+
+struct GnMixedLayout {
+  size_t pl, gam, obs, w, u, total;
+  __host__ __device__ GnMixedLayout(int J, int obs_tile) {
+    pl = 0;
+    gam = pl + sizeof(GradPlanetF) * kGnWarps * J;
+    obs = align_up(gam + sizeof(float) * kGnWarps, 16);
+    w = obs + sizeof(float4) * obs_tile;
+    u = align_up(w + sizeof(float2) * obs_tile, 16);
+    total = align_up(u + sizeof(float) * kGnWarps * 32 * gn_row(J), 16);
+  }
+};
+
+struct GnF64Layout {
+  size_t pl, gam, obs, pq, u, total;
+  __host__ __device__ GnF64Layout(int J, int obs_tile) {
+    const int np = gn_np(J), ntri = np * (np + 1) / 2;
+    pl = 0;
+    gam = pl + sizeof(GradPlanetD) * kGnWarpsD * J;
+    obs = align_up(gam + sizeof(double) * kGnWarpsD, 16);
+    pq = obs + sizeof(ObsGD) * obs_tile;
+    u = align_up(pq + sizeof(short2) * ntri, 16);
+    total = align_up(u + sizeof(double) * kGnWarpsD * 32 * (np | 1), 16);
+  }
+};
+
+// Index of H[p][q], q >= p, in the packed upper triangle (row by row).
+__device__ __forceinline__ int tri_index(int np, int p, int q) {
+  return p * np - (p * (p - 1)) / 2 + (q - p);
+}
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// x = hi + lo with both TF32 (lo carries the next 11 bits of x).
+__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
+}
+
+// D = A B + D for one 16 x 8 tile, A 16 x 8 (row), B 8 x 8 (col), TF32.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4],
+                                         const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int J>
+__global__ void __launch_bounds__(kGnWarps * 32)
+gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__ grad_out,
+                float *__restrict__ jtj_out) {
+  constexpr int NP = gn_np(J), MT = gn_mt(J), NT = gn_nt(J), ROW = gn_row(J);
+  constexpr int NTRI = NP * (NP + 1) / 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GnMixedLayout L(J, kGnObsTile);
+  GradPlanetF *pl_s = reinterpret_cast<GradPlanetF *>(smem + L.pl);
+  float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
+  float2 *wt_s = reinterpret_cast<float2 *>(smem + L.w);
+  float *u_all = reinterpret_cast<float *>(smem + L.u);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int block = kGnWarps * 32;
+  const int64_t sys0 = (int64_t)blockIdx.x * kGnWarps;
+  const int64_t s = sys0 + warp;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const Split3 tr3 = split3(t_ref), te3 = split3(a.t0);
+  const float dref_f = (tr3.x0 - te3.x0) + (tr3.x1 - te3.x1);     // t_ref - t0
+  const float jit2 = d2f(a.jitter2);
+
+  for (int i = tid; i < kGnWarps * J; i += block) {
+    const int64_t si = sys0 + i / J;
+    GradPlanetF q = {};
+    if (si < a.n_sys) q = grad_setup_mixed(a.params + si * NP + 5 * (i % J), t_ref, a.t0);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < kGnWarps; i += block)
+    gam_s[i] = sys0 + i < a.n_sys ? d2f(system_gamma_g(a.params + (sys0 + i) * NP, J)) : 0.0f;
+  for (int i = tid; i < kGnWarps * 32 * ROW; i += block) u_all[i] = 0.0f;   // incl. padding
+
+  float *u = u_all + warp * 32 * ROW;
+  const int gid = lane >> 2, tig = lane & 3;
+  Kahan acc = {0.0f, 0.0f};
+  Kahan gP[J];
+  float g[NP];
+  float C[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) gP[j] = Kahan{0.0f, 0.0f};
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) C[mt][nt][i] = 0.0f;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += kGnObsTile) {
+    const int nk = min(kGnObsTile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += block) {
+      float th, tl, vh, vl;
+      sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
+      split_d(a.v[k0 + k], vh, vl);
+      obs_s[k] = make_float4(th, tl, vh, vl);
+      const float sg = d2f(a.sigma[k0 + k]);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      wt_s[k] = make_float2(var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000), th + dref_f);
+    }
+    __syncthreads();
+    const float gam = gam_s[warp];
+    const GradPlanetF *q = pl_s + warp * J;
+    for (int kb = 0; kb < nk; kb += 32) {
+      const int k = kb + lane;
+      float urow[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) urow[i] = 0.0f;
+      if (k < nk) {
+        const float4 o = obs_s[k];
+        const float2 wt = wt_s[k];
+        float sEj[J], cEj[J];
+        Kahan V = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const PlanetF p = q[j].base;
+          const float M = mean_anomaly_mixed(o.x, o.y, p);
+          kepler_f32(M, p.e, sEj[j], cEj[j]);
+          kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+        }
+        const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+        const float wk = wt.x, wr = wk * r, a2 = 2.0f * wr;
+        kahan_add(acc, wr * r);
+        const float sw = sqrtf(wk);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const GradPlanetF qj = q[j];
+          Partials<float> d;
+          const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+          d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
+          kahan_add(gP[j], a2 * d.dP);
+          g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
+          g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
+          g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
+          g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+          urow[5 * j + 0] = sw * d.dP;
+          urow[5 * j + 1] = sw * d.dK;
+          urow[5 * j + 2] = sw * d.de;
+          urow[5 * j + 3] = sw * d.dw;
+          urow[5 * j + 4] = sw * d.dM;
+        }
+        g[5 * J] += a2;
+        urow[5 * J] = sw;
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) u[lane * ROW + i] = urow[i];
+      __syncwarp();
+      // H += U^T U: k-steps of 8 rows; A = U^T (16 x 8 per m-tile), B = U (8 x 8 per n-tile)
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const float *r0 = u + (ks * 8 + tig) * ROW;
+        const float *r1 = r0 + 4 * ROW;
+        unsigned ah[MT][4], al[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          tf32_split(r0[16 * mt + gid], ah[mt][0], al[mt][0]);
+          tf32_split(r0[16 * mt + gid + 8], ah[mt][1], al[mt][1]);
+          tf32_split(r1[16 * mt + gid], ah[mt][2], al[mt][2]);
+          tf32_split(r1[16 * mt + gid + 8], ah[mt][3], al[mt][3]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          unsigned bh[2], bl[2];
+          tf32_split(r0[8 * nt + gid], bh[0], bl[0]);
+          tf32_split(r1[8 * nt + gid], bh[1], bl[1]);
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            if (8 * nt + 7 >= 16 * mt) {        // a tile on or above the diagonal
+              mma_tf32(C[mt][nt], al[mt], bh);
+              mma_tf32(C[mt][nt], ah[mt], bl);
+              mma_tf32(C[mt][nt], ah[mt], bh);
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+
+  for (int m = 16; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      Kahan op = {shfl_xor(gP[j].big, m), shfl_xor(gP[j].small, m)};
+      kahan_merge(gP[j], op);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) g[5 * j] = kahan_value(gP[j]);
+  if (s >= a.n_sys) return;
+  const float poison = 0.0f * gam_s[warp];             // NaN for an invalid system
+  if (lane == 0) {
+    const float value = kahan_value(acc) + poison;
+    if (chi2_out) chi2_out[s] = value;
+    note_invalid(a.invalid, value);
+  }
+  if (grad_out) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+      if (lane == (i & 31)) grad_out[s * NP + i] = g[i] + poison;
+  }
+  float *H = jtj_out + s * NTRI;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      if (8 * nt + 7 < 16 * mt) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int row = 16 * mt + gid + (i >= 2 ? 8 : 0);
+        const int col = 8 * nt + 2 * tig + (i & 1);
+        if (row < NP && col < NP && col >= row) H[tri_index(NP, row, col)] = C[mt][nt][i] + poison;
+      }
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(kGnWarpsD * 32)
+gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__ grad_out,
+              double *__restrict__ jtj_out) {
+  constexpr int NP = gn_np(J), ROWD = NP | 1;
+  constexpr int NTRI = NP * (NP + 1) / 2, E = (NTRI + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const GnF64Layout L(J, kGnObsTile);
+  GradPlanetD *pl_s = reinterpret_cast<GradPlanetD *>(smem + L.pl);
+  double *gam_s = reinterpret_cast<double *>(smem + L.gam);
+  ObsGD *obs_s = reinterpret_cast<ObsGD *>(smem + L.obs);
+  short2 *pq_s = reinterpret_cast<short2 *>(smem + L.pq);
+  double *u_all = reinterpret_cast<double *>(smem + L.u);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int block = kGnWarpsD * 32;
+  const int64_t sys0 = (int64_t)blockIdx.x * kGnWarpsD;
+  const int64_t s = sys0 + warp;
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const double dref = t_ref - a.t0;
+
+  for (int i = tid; i < kGnWarpsD * J; i += block) {
+    const int64_t si = sys0 + i / J;
+    GradPlanetD q = {};
+    if (si < a.n_sys) q = grad_setup_f64(a.params + si * NP + 5 * (i % J), dref);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < kGnWarpsD; i += block)
+    gam_s[i] = sys0 + i < a.n_sys ? system_gamma_g(a.params + (sys0 + i) * NP, J) : 0.0;
+  for (int p = tid; p < NP; p += block) {               // packed (p, q) table
+    const int base = p * NP - (p * (p - 1)) / 2;
+    for (int q = p; q < NP; ++q) pq_s[base + q - p] = make_short2((short)p, (short)q);
+  }
+
+  double *u = u_all + warp * 32 * ROWD;
+  double acc = 0.0, g[NP], h[E];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) h[i] = 0.0;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += kGnObsTile) {
+    const int nk = min(kGnObsTile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += block) {
+      ObsGD o;
+      const double tk = a.t[k0 + k];
+      o.tau = tk - t_ref;
+      o.v = a.v[k0 + k];
+      o.w = inv_variance_g(a.sigma[k0 + k], a.jitter2);
+      o.dt = tk - a.t0;
+      obs_s[k] = o;
+    }
+    __syncthreads();
+    const double gam = gam_s[warp];
+    const GradPlanetD *q = pl_s + warp * J;
+    for (int kb = 0; kb < nk; kb += 32) {
+      const int k = kb + lane;
+      double urow[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) urow[i] = 0.0;
+      if (k < nk) {
+        const ObsGD o = obs_s[k];
+        double sEj[J], cEj[J];
+        double V = gam;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const PlanetD p = q[j].base;
+          const double M = mean_anomaly_f64(o.tau, p);
+          kepler_f64(M, p.e, sEj[j], cEj[j]);
+          V += velocity_f64(p, sEj[j], cEj[j]);
+        }
+        const double r = V - o.v;
+        const double a2 = 2.0 * o.w * r;
+        acc = fma(o.w * r, r, acc);
+        const double sw = sqrt(o.w);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const GradPlanetD qj = q[j];
+          Partials<double> d;
+          const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
+          d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
+          g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
+          g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);
+          g[5 * j + 2] = fma(a2, d.de, g[5 * j + 2]);
+          g[5 * j + 3] = fma(a2, d.dw, g[5 * j + 3]);
+          g[5 * j + 4] = fma(a2, d.dM, g[5 * j + 4]);
+          urow[5 * j + 0] = sw * d.dP;
+          urow[5 * j + 1] = sw * d.dK;
+          urow[5 * j + 2] = sw * d.de;
+          urow[5 * j + 3] = sw * d.dw;
+          urow[5 * j + 4] = sw * d.dM;
+        }
+        g[5 * J] += a2;
+        urow[5 * J] = sw;
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) u[lane * ROWD + i] = urow[i];
+      __syncwarp();
+      const int rows = min(32, nk - kb);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int e = lane + 32 * i;
+        if (e < NTRI) {
+          const short2 pq = pq_s[e];
+          double sum = 0.0;
+          for (int rr = 0; rr < rows; ++rr) sum = fma(u[rr * ROWD + pq.x], u[rr * ROWD + pq.y], sum);
+          h[i] += sum;
+        }
+      }
+      __syncwarp();
+    }
+  }
+
+  for (int m = 16; m >= 1; m >>= 1) {
+    acc += shfl_xor(acc, m);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
+  }
+  if (s >= a.n_sys) return;
+  const double poison = 0.0 * gam_s[warp];
+  if (lane == 0) {
+    const double value = acc + poison;
+    if (chi2_out) chi2_out[s] = value;
+    note_invalid(a.invalid, value);
+  }
+  if (grad_out) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+      if (lane == (i & 31)) grad_out[s * NP + i] = g[i] + poison;
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    const int e = lane + 32 * i;
+    if (e < NTRI) jtj_out[s * NTRI + e] = h[i] + poison;
+  }
+}
+
 template <typename Kern>
 cudaError_t set_smem(Kern k, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
@@ -466,6 +866,38 @@ cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
 #undef KC_LAUNCH_NLL
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_newton(const UniformArgs &a, bool f64, void *chi2, void *grad,
+                                void *jtj, cudaStream_t st) {
+  cudaError_t err = cudaSuccess;
+  if (f64) {
+    const int grid = (int)((a.n_sys + kGnWarpsD - 1) / kGnWarpsD);
+#define KC_LAUNCH(JJ)                                                                        \
+  {                                                                                          \
+    const size_t smem = GnF64Layout(JJ, kGnObsTile).total;                                   \
+    err = set_smem(gn_f64_kernel<JJ>, smem);                                                 \
+    if (err == cudaSuccess)                                                                  \
+      gn_f64_kernel<JJ><<<grid, kGnWarpsD * 32, smem, st>>>(a, (double *)chi2, (double *)grad, \
+                                                            (double *)jtj);                  \
+  }
+    KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  } else {
+    const int grid = (int)((a.n_sys + kGnWarps - 1) / kGnWarps);
+#define KC_LAUNCH(JJ)                                                                        \
+  {                                                                                          \
+    const size_t smem = GnMixedLayout(JJ, kGnObsTile).total;                                 \
+    err = set_smem(gn_mixed_kernel<JJ>, smem);                                               \
+    if (err == cudaSuccess)                                                                  \
+      gn_mixed_kernel<JJ><<<grid, kGnWarps * 32, smem, st>>>(a, (float *)chi2, (float *)grad, \
+                                                             (float *)jtj);                  \
+  }
+    KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
+#undef KC_LAUNCH
+  }
   if (err != cudaSuccess) return err;
   return cudaGetLastError();
 }

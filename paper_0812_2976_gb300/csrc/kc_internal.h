@@ -58,6 +58,12 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
                                        float *out, float *resid, cudaStream_t st);
 cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
                             float *resid, cudaStream_t st);
+// Gauss-Newton matrix with chi2 and its gradient (kc_grad.cu): chi2 / grad
+// may be NULL; jtj is [n_sys][n (n + 1)/2], n = 5 n_pl + 1; float (mixed) or
+// double (f64).
+cudaError_t launch_gauss_newton(const UniformArgs &a, bool f64, void *chi2, void *grad,
+                                void *jtj, cudaStream_t st);
+
 // FMA-pipe throughput probe (kc_probe.cu): one CTA of 1024 threads per SM
 // (grid n_sm), eight FMA chains per thread, iters steps; writes each CTA's
 // SM-clock cycles to cycles[n_sm]; sink is [n_sm * 1024] of the type.

@@ -1,0 +1,126 @@
+"""Gauss-Newton normal matrix H = sum_k w_k J_k J_k^T with chi2 and its
+gradient from one pass (kc_chi2_gauss_newton) against the FP64 oracle.
+
+H entries are compared on the correlation scale: |dH_pq| / sqrt(H_pp H_qq)
+(an entry that cancels to ~0 cannot carry relative accuracy).  Tolerances:
+the mixed path forms J_k in FP32 (relative error ~1e-6, the period column
+~1e-5 through (t - t0)/P^2) and the update on the tensor cores with the
+two-term TF32 split (~5e-7 per product), so 1e-4 leaves an order of
+magnitude; FP64: 1e-10."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+H_MIXED_TOL = 1e-4
+H_F64_TOL = 1e-10
+CHI2_MIXED_TOL, CHI2_F64_TOL = 1e-5, 1e-12
+GRAD_MIXED_TOL, GRAD_F64_TOL = 1e-3, 1e-9
+
+
+@pytest.fixture(scope="module")
+def kc():
+    import paper_0812_2976_gb300 as kc
+    from paper_0812_2976_gb300 import build
+    build.build()
+    kc._lib.load()
+    return kc
+
+
+def dev(*arrs):
+    return [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+            for a in arrs]
+
+
+def h_err(got, ref, n):
+    import oracle
+    G = oracle.unpack_symmetric(np.asarray(got, np.float64), n)
+    R = oracle.unpack_symmetric(ref, n)
+    d = np.sqrt(np.abs(np.diagonal(R, axis1=1, axis2=2)))
+    scale = np.maximum(d[:, :, None] * d[:, None, :], 1e-30)
+    return np.abs(G - R) / scale
+
+
+def rel(got, ref):
+    return np.abs(np.asarray(got, np.float64) - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+def grad_err(got, ref):
+    scale = np.maximum(np.abs(ref), 1e-3 * np.linalg.norm(ref, axis=1, keepdims=True))
+    return np.abs(np.asarray(got, np.float64) - ref) / scale
+
+
+@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+def test_gradient_workload_sampled(kc, oracle_mod, mode):
+    """Config-3 shapes (n_pl 3, n_obs 512, t0 = 2450000) on 2048 systems."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(3, n_sys=2048)
+    v = oracle_mod.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
+    chi_ref, g_ref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
+    H_ref = oracle_mod.gauss_newton(w.params, w.t, w.sigma, w.n_pl, t0=w.t0)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=w.t0, mode=mode)
+    tol = (CHI2_MIXED_TOL, GRAD_MIXED_TOL, H_MIXED_TOL) if mode == "mixed" else \
+        (CHI2_F64_TOL, GRAD_F64_TOL, H_F64_TOL)
+    assert rel(chi.cpu().numpy(), chi_ref).max() <= tol[0]
+    assert grad_err(g.cpu().numpy(), g_ref).max() <= tol[1]
+    e = h_err(H.cpu().numpy(), H_ref, 5 * w.n_pl + 1)
+    assert e.max() <= tol[2], e.max()
+
+
+@pytest.mark.parametrize("n_pl,n_obs", [(1, 33), (2, 300), (4, 77), (5, 129), (7, 64), (8, 257)])
+def test_planet_counts_ragged_tails_invalid(kc, oracle_mod, n_pl, n_obs):
+    rng = np.random.default_rng(40 + n_pl)
+    n_sys = 37
+    cols = []
+    for _ in range(n_pl):
+        cols += [np.exp(rng.uniform(0, np.log(3000), n_sys)), rng.uniform(1, 80, n_sys),
+                 rng.uniform(0, 0.85, n_sys), rng.uniform(0, 2 * np.pi, n_sys),
+                 rng.uniform(0, 2 * np.pi, n_sys)]
+    par = np.stack(cols + [rng.uniform(-10, 10, n_sys)], axis=1)
+    par[4, 2] = 1.5                                   # e > 1: invalid
+    t = np.sort(rng.uniform(2450000, 2453000, n_obs))
+    v = rng.normal(0, 30, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    t0 = 2450500.0
+    chi_ref, g_ref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=t0, grad=True)
+    H_ref = oracle_mod.gauss_newton(par, t, sig, n_pl, t0=t0)
+    P, T, V, S = dev(par, t, v, sig)
+    ok = np.setdiff1d(np.arange(n_sys), [4])
+    kc.kc_last_device_error()
+    for mode, tol in (("mixed", (CHI2_MIXED_TOL, GRAD_MIXED_TOL, H_MIXED_TOL)),
+                      ("fp64", (CHI2_F64_TOL, GRAD_F64_TOL, H_F64_TOL))):
+        chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=t0, mode=mode)
+        chi, g, H = chi.cpu().numpy(), g.cpu().numpy(), H.cpu().numpy()
+        assert np.isnan(chi[4]) and np.all(np.isnan(g[4])) and np.all(np.isnan(H[4]))
+        assert rel(chi[ok], chi_ref[ok]).max() <= tol[0]
+        assert grad_err(g[ok], g_ref[ok]).max() <= tol[1]
+        assert h_err(H[ok], H_ref[ok], 5 * n_pl + 1).max() <= tol[2]
+        assert kc.kc_last_device_error() == 1
+
+
+def test_levenberg_marquardt_step_reduces_chi2(kc, oracle_mod):
+    """One damped Gauss-Newton step built from the GPU outputs lowers chi2
+    of perturbed models of noise-free data (the matrix is the one a fitter
+    needs, not only numerically close to the oracle's)."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(0, n_sys=64)
+    t0 = float(w.t[0])
+    v = oracle_mod.predict(w.truth, w.t, w.n_pl, t0)[0]
+    rng = np.random.default_rng(5)
+    params = w.truth * (1 + 1e-4 * rng.standard_normal((64, w.truth.size)))
+    P, T, V, S = dev(params, w.t, v, w.sigma)
+    chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=t0, mode="mixed")
+    import oracle
+    n = 5 * w.n_pl + 1
+    Hf = oracle.unpack_symmetric(H.cpu().numpy().astype(np.float64), n)
+    g = g.cpu().numpy().astype(np.float64)
+    base = oracle_mod.chi2(params, w.t, v, w.sigma, w.n_pl, t0=t0)
+    better = 0
+    for s in range(params.shape[0]):
+        A = Hf[s] + 1e-3 * np.diag(np.diag(Hf[s]))
+        step = np.linalg.solve(A, -0.5 * g[s])
+        new = oracle_mod.chi2((params[s] + step)[None], w.t, v, w.sigma, w.n_pl, t0=t0)[0]
+        better += new < 0.5 * base[s]
+    assert better >= 0.9 * params.shape[0]
