@@ -505,8 +505,12 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
     gam_s[i] = sys0 + i < a.n_sys ? d2f(system_gamma_g(a.params + (sys0 + i) * NP, J)) : 0.0f;
   for (int i = tid; i < kGnWarps * 32 * ROW; i += block) u_all[i] = 0.0f;   // incl. padding
 
+  // Element (row r, column c) of U sits at r * ROW + (c ^ ((r >> 2) & 7)):
+  // with ROW = 8 mod 32 both the row writes (one row per lane) and the
+  // fragment loads touch 32 different banks.
   float *u = u_all + warp * 32 * ROW;
   const int gid = lane >> 2, tig = lane & 3;
+  const int sw_row = (lane >> 2) & 7;
   Kahan acc = {0.0f, 0.0f};
   Kahan gP[J];
   float g[NP];
@@ -580,26 +584,27 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         urow[5 * J] = sw;
       }
 #pragma unroll
-      for (int i = 0; i < NP; ++i) u[lane * ROW + i] = urow[i];
+      for (int i = 0; i < NP; ++i) u[lane * ROW + (i ^ sw_row)] = urow[i];
       __syncwarp();
       // H += U^T U: k-steps of 8 rows; A = U^T (16 x 8 per m-tile), B = U (8 x 8 per n-tile)
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
         const float *r0 = u + (ks * 8 + tig) * ROW;
         const float *r1 = r0 + 4 * ROW;
+        const int g0 = gid ^ ((2 * ks) & 7), g1 = gid ^ ((2 * ks + 1) & 7);   // row swizzles
         unsigned ah[MT][4], al[MT][4];
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
-          tf32_split(r0[16 * mt + gid], ah[mt][0], al[mt][0]);
-          tf32_split(r0[16 * mt + gid + 8], ah[mt][1], al[mt][1]);
-          tf32_split(r1[16 * mt + gid], ah[mt][2], al[mt][2]);
-          tf32_split(r1[16 * mt + gid + 8], ah[mt][3], al[mt][3]);
+          tf32_split(r0[16 * mt + g0], ah[mt][0], al[mt][0]);
+          tf32_split(r0[16 * mt + g0 + 8], ah[mt][1], al[mt][1]);
+          tf32_split(r1[16 * mt + g1], ah[mt][2], al[mt][2]);
+          tf32_split(r1[16 * mt + g1 + 8], ah[mt][3], al[mt][3]);
         }
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
           unsigned bh[2], bl[2];
-          tf32_split(r0[8 * nt + gid], bh[0], bl[0]);
-          tf32_split(r1[8 * nt + gid], bh[1], bl[1]);
+          tf32_split(r0[8 * nt + g0], bh[0], bl[0]);
+          tf32_split(r1[8 * nt + g1], bh[1], bl[1]);
 #pragma unroll
           for (int mt = 0; mt < MT; ++mt) {
             if (8 * nt + 7 >= 16 * mt) {        // a tile on or above the diagonal
