@@ -304,8 +304,8 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
 }
 
 // Split variant, first pass: every per-(system, planet) setup, gamma and
-// observation conversion of the batch, spread over the whole grid (so the
-// FP64 setup runs at full pipe occupancy instead of at each CTA's start).
+// observation conversion of the batch, spread over the whole grid (once per
+// batch instead of once per CTA).
 __global__ void __launch_bounds__(64)
 prep_mixed_kernel(UniformArgs a, PlanetF *__restrict__ pl, float *__restrict__ gam,
                   float4 *__restrict__ obs, float *__restrict__ w,
@@ -667,9 +667,9 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
     base += align_up(sizeof(float) * a.n_sys * chunks, 256);
     cs.count = reinterpret_cast<unsigned *>(base);
   }
-  // The setup is a chain of dependent FP64 operations on a pipe of ~2 lanes
-  // per SM per clock, so the items are spread thinly over every SM (64-thread
-  // CTAs, one item per thread) rather than packed into a few full CTAs.
+  // Each setup item is a long dependent chain (float expansions, ~2k cycles),
+  // so the items are spread thinly over every SM (64-thread CTAs, one item
+  // per thread) rather than packed into a few full CTAs.
   const int64_t items = std::max<int64_t>(a.n_sys * a.n_pl, std::max<int64_t>(a.n_obs, 1));
   const int prep_grid = (int)std::min<int64_t>((items + 63) / 64, 152 * 16);
   prep_mixed_kernel<<<prep_grid, 64, 0, st>>>(a, pl, gam, obs, w, cs.count);

@@ -72,6 +72,15 @@ def test_bad_arguments_rejected_on_host(lib):
     assert lib.kc_kepler_solve(p, p, -1, 0, p, None) == 1
     assert lib.kc_rv_predict(p, p, 2, 0, 4, 0.0, p, None) == 1
     assert lib.kc_last_device_error(None) == 1
+    # Gauss-Newton: bad mode, n_pl, non-finite t0, misaligned output, NULL matrix
+    assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 2, None, None, p, None) == 1
+    assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 9, 8, 0.0, 0.0, 1, None, None, p, None) == 1
+    assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, float("inf"), 0.0, 1, None, None, p,
+                                    None) == 1
+    assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 0, ctypes.c_void_p(68), None,
+                                    p, None) == 1
+    assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 1, None, None, None, None) == 1
+    assert lib.kc_measure_pipe_rate(0, None, None) == 1
 
 
 def test_empty_batches_are_no_ops(lib):
