@@ -57,6 +57,14 @@ def mixed_flops_per_eval(n_pl: int) -> float:
 F64_FLOPS_PER_EVAL = 14 + 41 + 30 + 10 + 16 + 2
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the mixed chi2 kernel in its current form, from an ncu capture of this
+# benchmark's own default workload (autotuned tile 32,128,0): the batch reads
+# its 688 KB of parameters and 6 KB of observations once.  Keyed by (config,
+# n_sys override); other workloads report null.
+DRAM_BYTES_PER_LAUNCH = {(1, None): 755456}
+
+
 def sm_mhz_for_peaks():
     pk, _ = peaks()
     return pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
@@ -512,9 +520,10 @@ def run_kc(args):
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
     peak_tflops = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz * 1e6 / 1e12
     flops = mixed_flops_per_eval(w.n_pl) * evals
-    achieved = flops / (t_sum / args.steps) / 1e12 / world
+    achieved = flops / (t_sum / args.steps) / 1e12          # one GPU's launch
+    traffic = DRAM_BYTES_PER_LAUNCH.get((args.config, args.n_sys)) if world == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": f"chi2_mixed_kernel<{w.n_pl}>",
                 "peak_basis": f"FP32 FMA pipe: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP "
                               f"x {sm_mhz:.0f} MHz ({pk_kind} max SM clock)",
