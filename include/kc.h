@@ -298,9 +298,9 @@ void kc_plan_destroy(kc_plan *plan);
 /* ------------------------------------------------------------ tiling */
 
 /* Launch shape of the uniform-batch kernels: each system is handled by
- * threads_per_system consecutive threads (a power of two, 1..block; at most
- * 32 for the gradient kernel), `block` threads per CTA (32..256, a multiple
- * of 32 and of threads_per_system).  split (mixed chi2 only) selects a
+ * threads_per_system consecutive threads (1..block and a divisor of block;
+ * a power of two except for the mixed chi2 kernel; at most 32 for the
+ * gradient kernel), `block` threads per CTA (32..256, a multiple of 32).  split (mixed chi2 only) selects a
  * two-pass variant for small batches: a preparation pass first writes every
  * per-(system, planet) constant and the converted observations to
  * stream-ordered scratch from a library memory pool, then the main kernel

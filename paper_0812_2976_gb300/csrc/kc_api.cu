@@ -501,7 +501,10 @@ bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
   if (t.split != 0 && (kernel != KC_KERNEL_CHI2 || mode != KC_MIXED)) return false;
   if (t.split == 2)     // one warp per chunk: G = 32 x chunks, chunks <= 32
     return G >= 32 && G <= 1024 && !(G & (G - 1));
-  if (G < 1 || G > B || (G & (G - 1)) || (B % G)) return false;
+  if (G < 1 || G > B || (B % G)) return false;
+  // any G for the mixed chi2 kernel (a G that is not a power of two merges
+  // its systems' partial sums through shared memory); powers of two elsewhere
+  if ((G & (G - 1)) && (kernel != KC_KERNEL_CHI2 || mode != KC_MIXED)) return false;
   if (kernel == KC_KERNEL_GRAD && G > 32) return false;
   return true;
 }
@@ -580,10 +583,20 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
   const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
-  for (int split = 0; split <= 2; ++split)
-  for (int B : {32, 64, 128, 256}) {
-    for (int G = 1; G <= (split == 2 ? 1024 : B); G <<= 1) {
-      const kc_tile cand{G, B, split};
+  // powers of two, plus G = 12, 24, 48 with 96- and 192-thread blocks: with
+  // 96 registers a thread, 24 threads per system fit 4096 systems of 256
+  // observations into one wave of 152 SMs where 32 would need 1.3 waves
+  std::vector<kc_tile> cands;
+  for (int split = 0; split <= 2; ++split) {
+    for (int B : {32, 64, 128, 256})
+      for (int G = 1; G <= (split == 2 ? 1024 : B); G <<= 1) cands.push_back(kc_tile{G, B, split});
+    if (split < 2)
+      for (int B : {96, 192})
+        for (int G : {12, 24, 48}) cands.push_back(kc_tile{G, B, split});
+  }
+  for (const kc_tile &cand : cands) {
+    {
+      const int G = cand.threads_per_system, B = cand.block, split = cand.split;
       if (!tile_ok(kernel, mode, cand)) continue;
       if (n_obs > 0 && G > n_obs) continue;
       if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs

@@ -34,7 +34,7 @@ struct MixedLayout {
     gam = pl + sizeof(PlanetF) * ST * J;
     s2 = gam + sizeof(float) * ST;
     red = align_up(s2 + sizeof(float) * ST, 16);
-    obs = align_up(red + sizeof(float) * 3 * nwarps, 16);
+    obs = align_up(red + sizeof(float) * 3 * 32 * nwarps, 16);   // 3 per thread
     w = obs + sizeof(float4) * obs_tile;
     total = align_up(w + sizeof(float) * obs_tile, 16);
   }
@@ -270,13 +270,29 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   }
 
   // combine the G partial sums of each system
-  const int gw = G < 32 ? G : 32;
+  if (G & (G - 1)) {
+    // G not a power of two (a system's threads may straddle two warps): the
+    // first thread of each system merges the others' sums in thread order
+    __syncthreads();
+    red_s[3 * tid] = acc.big;
+    red_s[3 * tid + 1] = acc.small;
+    red_s[3 * tid + 2] = rmax;
+    __syncthreads();
+    if (c == 0) {
+      for (int i = tid + 1; i < tid + G; ++i) {
+        Kahan o = {red_s[3 * i], red_s[3 * i + 1]};
+        kahan_merge(acc, o);
+        rmax = fmaxf(rmax, red_s[3 * i + 2]);
+      }
+    }
+  }
+  const int gw = (G & (G - 1)) ? 1 : (G < 32 ? G : 32);
   for (int m = gw >> 1; m >= 1; m >>= 1) {
     Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
     kahan_merge(acc, o);
     rmax = fmaxf(rmax, shfl_xor(rmax, m));
   }
-  if (G > 32) {
+  if (G > 32 && !(G & (G - 1))) {
     const int warp = tid >> 5, lane = tid & 31;
     __syncthreads();
     if (lane == 0) {
