@@ -595,34 +595,31 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
         for (int G : {12, 24, 48}) cands.push_back(kc_tile{G, B, split});
   }
   for (const kc_tile &cand : cands) {
-    {
-      const int G = cand.threads_per_system, B = cand.block, split = cand.split;
-      if (!tile_ok(kernel, mode, cand)) continue;
-      if (n_obs > 0 && G > n_obs) continue;
-      if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
-      Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
-      err = launch(tile);                       // warm-up (and smem attribute)
-      if (err != cudaSuccess) break;
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 5 && err == cudaSuccess; ++rep) {
-        cudaEventRecord(e0, s);
-        err = launch(tile);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        tmin = ms < tmin ? ms : tmin;
-      }
-      if (err != cudaSuccess) break;
-      if (verbose)
-        fprintf(stderr, "kc_autotune: kind %d n_sys %lld G %3d block %3d split %d: %9.2f us\n",
-                (int)kind, (long long)n_sys, G, B, split, 1e3 * tmin);
-      if (tmin < best_t) {
-        best_t = tmin;
-        best_tile = tile;
-      }
+    const int G = cand.threads_per_system, B = cand.block, split = cand.split;
+    if (!tile_ok(kernel, mode, cand)) continue;
+    if (n_obs > 0 && G > n_obs) continue;
+    if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
+    Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
+    err = launch(tile);                       // warm-up (and smem attribute)
+    if (err != cudaSuccess) break;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 5 && err == cudaSuccess; ++rep) {
+      cudaEventRecord(e0, s);
+      err = launch(tile);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = ms < tmin ? ms : tmin;
     }
     if (err != cudaSuccess) break;
+    if (verbose)
+      fprintf(stderr, "kc_autotune: kind %d n_sys %lld G %3d block %3d split %d: %9.2f us\n",
+              (int)kind, (long long)n_sys, G, B, split, 1e3 * tmin);
+    if (tmin < best_t) {
+      best_t = tmin;
+      best_tile = tile;
+    }
   }
   cudaFreeAsync(chi, s);
   if (grad) cudaFreeAsync(grad, s);
