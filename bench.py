@@ -50,6 +50,30 @@ def mixed_flops_per_eval(n_pl: int) -> float:
     return 17 + 2 + 3 * 22 + 27 + 10 + 8 + 4 + 10.0 / n_pl
 
 
+# The adjoint adds, per planet and observation: the velocity partials 26
+# (cos f, sin f, cos/sin(w + f), dK, dw, dM, de), 1/D 2, dP 3, the
+# compensated dP sum 5 and the four other accumulations 8; per observation
+# the weighted residual, chi2 sum and gamma term 12 (instead of 10).
+def grad_flops_per_eval(n_pl: int) -> float:
+    return 17 + 2 + 3 * 22 + 27 + 10 + 8 + 4 + 44 + 12.0 / n_pl
+
+
+# The Gauss-Newton pass adds the row u = sqrt(w) J of U (5 products per
+# planet, 1 per observation) on the FP32 pipe; its U^T U update runs on the
+# tensor cores (reported separately).
+def gn_flops_per_eval(n_pl: int) -> float:
+    return grad_flops_per_eval(n_pl) + 5 + 1.0 / n_pl
+
+
+def gn_tensor_flops_per_obs(n_pl: int) -> float:
+    """Tensor FLOPs per observation of the U^T U update as issued: 16 x 8 x 8
+    tiles on or above the diagonal, three TF32 products each, 2 FLOP/MAC."""
+    n = 5 * n_pl + 1
+    mt, nt = (n + 15) // 16, (n + 7) // 8
+    tiles = sum(1 for m in range(mt) for q in range(nt) if 8 * q + 7 >= 16 * m)
+    return tiles * 3 * 16 * 8 * 2          # per observation (K = 1 of each 8-deep step)
+
+
 # FP64 path, FP64 FLOPs per planet-observation evaluation (FMA = 2), from its
 # algorithm: mean anomaly 14, sin/cos (Cody-Waite + Taylor) 41, Danby step
 # with a Newton reciprocal 30, last-step update 10, velocity with a Newton
@@ -158,6 +182,15 @@ def gradient_throughput(kc, synth, dev, stream, args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         out[name] = evals * reps / (a.elapsed_time(b) / 1e3)
+    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    out["roofline_alu"] = {
+        "peak": peak, "unit": "TFLOP/s",
+        "chi2_grad_frac": out["chi2_grad"] * grad_flops_per_eval(w.n_pl) / 1e12 / peak,
+        "nll_grad_frac": out["nll_grad"] * grad_flops_per_eval(w.n_pl) / 1e12 / peak,
+        "gauss_newton_frac": out["gauss_newton"] * gn_flops_per_eval(w.n_pl) / 1e12 / peak,
+        "flops_per_eval": {"grad": grad_flops_per_eval(w.n_pl), "gauss_newton": gn_flops_per_eval(w.n_pl)},
+        "gauss_newton_tensor_tflops": out["gauss_newton"] / w.n_pl
+                                      * gn_tensor_flops_per_obs(w.n_pl) / 1e12}
     return out
 
 
@@ -672,6 +705,18 @@ def run_kc_ragged(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    # ALU roofline of the persistent kernel: every system at its own n_pl
+    n_obs_s = np.diff(np.asarray(w.obs_off)).astype(np.float64)
+    npl_s = np.asarray(w.n_pl).astype(np.float64)
+    per_planet = (grad_flops_per_eval(1) - 12.0) if want_grad else (mixed_flops_per_eval(1) - 10.0)
+    per_obs = 12.0 if want_grad else 10.0
+    flops_step = float(np.sum(n_obs_s * (npl_s * per_planet + per_obs)))
+    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    achieved = flops_step / (t_sum / args.steps) / 1e12
+    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": f"ragged_mixed_kernel<{'GRAD' if want_grad else 'FWD'}>",
+                        "flops_per_step": flops_step}
     line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         import oracle
