@@ -94,6 +94,26 @@ def test_pure_single_precision_ablation(kc, oracle_mod):
     assert np.median(e_single) > 100 * np.median(e_mixed)
 
 
+def test_config1_in_the_benchmarked_launch(kc, oracle_mod):
+    """The full paper-shaped batch in the launch bench.py times: the tile the
+    autotuner picks (pinned in the table by kc_autotune), with the bench's
+    observed-data construction; every system against the oracle."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1)
+    v = observed(oracle_mod, w)
+    ref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    try:
+        tile, _ = kc.kc_autotune(P, T, V, S, kernel="chi2", mode="mixed")
+        assert kc.kc_get_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs) == tuple(tile)
+        out = torch.empty(w.n_sys, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            kc.kc_chi2_eval_mixed(P, T, V, S, out=out)
+            assert rel_err(out.cpu().numpy(), ref).max() <= MIXED_TOL
+    finally:
+        kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, None)
+
+
 # ------------------------------------------------------------ config 2
 
 def test_config2_grid_sweep_full_size_sampled(kc, oracle_mod):
