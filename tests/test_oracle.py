@@ -597,3 +597,23 @@ def test_gauss_newton_structure(oracle_mod):
     bad[1, 2] = 1.2
     Hb = oracle_mod.gauss_newton(bad, t, sig, 3)
     assert np.all(np.isnan(Hb[1])) and np.all(np.isfinite(Hb[[0, 2, 3]]))
+
+
+def test_velocity_equals_the_eccentric_anomaly_form(oracle_mod):
+    """The kernels evaluate Eq. 3 in its eccentric-anomaly form
+    [K cos w (cos E - e) - K sqrt(1 - e^2) sin w sin E]/(1 - e cos E)
+    + K e cos w; the oracle uses the true anomaly f explicitly.  The two are
+    algebraically identical (cos f = (cos E - e)/D, sin f = sqrt(1-e^2)
+    sin E / D), so they must agree to rounding."""
+    rng = np.random.default_rng(41)
+    for _ in range(20):
+        P, K = np.exp(rng.uniform(0, np.log(3000))), rng.uniform(1, 100)
+        e, w, M0 = rng.uniform(0, 0.97), rng.uniform(0, TWO_PI), rng.uniform(0, TWO_PI)
+        t = np.sort(rng.uniform(0, 5000, 25))
+        v = oracle_mod.planet_velocity([P, K, e, w, M0], t)
+        M = oracle_mod.mean_anomaly(t, 0.0, P, M0)
+        E = oracle_mod.kepler_E(M, e)
+        D = 1 - e * np.cos(E)
+        v_E = (K * np.cos(w) * (np.cos(E) - e)
+               - K * np.sqrt((1 - e) * (1 + e)) * np.sin(w) * np.sin(E)) / D + K * e * np.cos(w)
+        assert np.max(np.abs(v_E - v)) <= 1e-13 * K / (1 - e)
