@@ -342,3 +342,48 @@ def test_split_variant_matches_oracle(kc, oracle_mod, tile):
             assert float(resid.max()) <= RESID_TOL
     finally:
         kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, None)
+
+
+def test_short_periods_far_from_the_epoch(kc, oracle_mod):
+    """|t_ref - t0| / P above 2^24 (periods of 0.02-0.14 d, t0 = 0, times near
+    2.45e6 d) sends the mixed path's phase setup to its double-double branch;
+    periods of 0.2-1 d stay on the float-expansion branch next to it."""
+    rng = np.random.default_rng(51)
+    n_sys, n_pl, n_obs = 300, 2, 150
+    par = synth_rows(rng, n_sys, n_pl)
+    par[:, 0] = np.where(np.arange(n_sys) % 2 == 0, rng.uniform(0.02, 0.14, n_sys),
+                         rng.uniform(0.2, 1.0, n_sys))
+    t = np.sort(rng.uniform(2450000, 2450300, n_obs))
+    v = oracle_mod.predict(par[0], t, n_pl)[0] + rng.normal(0, 2, n_obs)
+    sig = rng.uniform(1, 3, n_obs)
+    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, grad=True)
+    P, T, V, S = dev(par, t, v, sig)
+    c32, r = kc.kc_chi2_eval_ex(P, T, V, S, mode="mixed", max_kepler_resid=True)
+    assert rel_err(c32.cpu().numpy(), ref).max() <= MIXED_TOL
+    assert float(r.max()) <= RESID_TOL
+    assert rel_err(kc.kc_chi2_eval(P, T, V, S).cpu().numpy(), ref).max() <= FP64_TOL
+    _, g32 = kc.kc_chi2_grad(P, T, V, S, mode="mixed")
+    assert grad_err(g32.cpu().numpy(), gref).max() <= GRAD_MIXED_TOL
+
+
+def test_circular_and_eccentric_extremes(kc, oracle_mod):
+    """e = 0 exactly (circular orbits) and e = 0.95 (the highest eccentricity
+    of the workloads) in both paths."""
+    rng = np.random.default_rng(52)
+    n_sys, n_pl, n_obs = 256, 3, 200
+    par = synth_rows(rng, n_sys, n_pl)
+    par[:128, 2::5][:, :n_pl] = 0.0
+    par[128:, 2::5][:, :n_pl] = 0.95
+    t = np.sort(rng.uniform(2450000, 2453000, n_obs))
+    v = rng.normal(0, 20, n_obs)
+    sig = rng.uniform(1, 4, n_obs)
+    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, grad=True)
+    P, T, V, S = dev(par, t, v, sig)
+    c32, r = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="mixed", max_kepler_resid=True)
+    assert rel_err(c32.cpu().numpy(), ref).max() <= MIXED_TOL
+    assert float(r.max()) <= RESID_TOL
+    c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="fp64").cpu().numpy()
+    assert rel_err(c64, ref).max() <= FP64_TOL
+    for mode, tol in (("mixed", GRAD_MIXED_TOL), ("fp64", GRAD_F64_TOL)):
+        _, g = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, mode=mode)
+        assert grad_err(g.cpu().numpy(), gref).max() <= tol
