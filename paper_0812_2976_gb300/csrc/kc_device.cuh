@@ -120,16 +120,16 @@ __device__ __forceinline__ float rcp_fast(float x) {
   return y;
 }
 
-// 1/x in double for normal, finite x: the MUFU double-precision seed and
-// two Newton steps (error ~1 ulp).  IEEE division costs more FP64-pipe
-// instructions, which are the bound of the FP64 path.
+// 1/x in double for x in the normal float range: the single-precision
+// MUFU reciprocal (relative error < 2^-22, converted on the integer pipe)
+// and one Newton step in double, r (2 - x r), whose error is the square of
+// the seed's: below 2^-44 relative, always on the low side.  Two FP64
+// operations instead of the four of an IEEE-exact reciprocal; the FP64 path
+// uses it where that error is far below its 1e-12 target (the Danby step's
+// correction, which is itself tiny, and 1/(1 - e cos E) of the velocity).
 __device__ __forceinline__ double rcp_f64(double x) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double r = f2d(rcp_fast(d2f(x)));
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 // sin and cos to about one ulp for |x| <= 8, on the FMA pipe.
