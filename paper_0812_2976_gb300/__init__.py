@@ -511,33 +511,47 @@ class DEMCMC:
         dev = self.states.device
         self._prop = torch.empty((self.half, self.npar), dtype=torch.float64, device=dev)
         self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
-        self._acc = torch.empty(self.half, dtype=torch.int32, device=dev)
+        self._acc = torch.empty(n, dtype=torch.int32, device=dev)
+        # partner index offsets: the first half draws from the second, and back
+        self._off = torch.cat([torch.full((self.half, 2), self.half, dtype=torch.int64),
+                               torch.zeros((self.half, 2), dtype=torch.int64)]).to(dev)
         self.generation = 0
         self._n_acc = torch.zeros((), dtype=torch.int64, device=dev)   # no host syncs
         self.proposed = 0
 
-    def _partners(self, other: int):
+    def _draws(self):
+        """Every random number of one generation (both halves) in one go:
+        the second half's states, which scale its jitter, do not change while
+        the first half moves, and partner indices only name chains."""
+        h, dev = self.half, self.states.device
+        eps = torch.randn((2 * h, self.npar), generator=self.gen, dtype=torch.float64,
+                          device=dev)
+        eps.mul_(self.eps_scale).mul_(self.states.abs())
+        u = torch.rand(2 * h, generator=self.gen, dtype=torch.float64, device=dev)
+        u.clamp_min_(1e-300)
+        r1 = torch.randint(0, h, (2 * h,), generator=self.gen, device=dev)
+        r2 = torch.randint(0, h - 1, (2 * h,), generator=self.gen, device=dev)
+        r2 += (r2 >= r1).to(r2.dtype)                # uniform over the others: r2 != r1
+        return eps, u, (torch.stack([r1, r2], dim=1) + self._off).to(torch.int32)
+
+    def _generation(self, gamma: float) -> None:
+        eps, u, partners = self._draws()
         h = self.half
-        r1 = torch.randint(0, h, (h,), generator=self.gen, device=self.states.device)
-        r2 = torch.randint(0, h - 1, (h,), generator=self.gen, device=self.states.device)
-        r2 = r2 + (r2 >= r1).to(r2.dtype)                 # r2 != r1
-        return (torch.stack([r1, r2], dim=1) + other).to(torch.int32)
+        for first in (0, h):
+            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, gamma,
+                           partners[first:first + h], eps[first:first + h], u[first:first + h],
+                           self._prop, self._cp, self._acc[first:first + h], self.t0,
+                           self.jitter, self.mode)
+        self._n_acc += self._acc.sum()
+
+    def _gamma(self) -> float:
+        hop = self.hop_every and (self.generation + 1) % self.hop_every == 0
+        return 1.0 if hop else self.gamma
 
     def step(self) -> None:
         """One generation (both halves)."""
-        gamma = 1.0 if self.hop_every and (self.generation + 1) % self.hop_every == 0 \
-            else self.gamma
-        for first, other in ((0, self.half), (self.half, 0)):
-            cur = self.states[first:first + self.half]
-            eps = torch.randn((self.half, self.npar), generator=self.gen, dtype=torch.float64,
-                              device=self.states.device) * (self.eps_scale * cur.abs())
-            u = torch.rand(self.half, generator=self.gen, dtype=torch.float64,
-                           device=self.states.device).clamp_min_(1e-300)
-            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, self.half,
-                           gamma, self._partners(other), eps, u, self._prop, self._cp,
-                           self._acc, self.t0, self.jitter, self.mode)
-            self._n_acc += self._acc.sum()
-            self.proposed += self.half
+        self._generation(self._gamma())
+        self.proposed += 2 * self.half
         self.generation += 1
 
     def run(self, generations: int, use_graph: bool = True) -> None:
@@ -556,34 +570,19 @@ class DEMCMC:
             side.wait_stream(torch.cuda.current_stream())
             g = torch.cuda.CUDAGraph()
             g.register_generator_state(self.gen)          # replays advance self.gen
-            saved = (self.generation, self.proposed)
-            self.generation = 0                           # capture a regular generation
             with torch.cuda.stream(side):
                 with torch.cuda.graph(g, stream=side):
-                    self._graph_gen()
-            self.generation, self.proposed = saved
+                    self._generation(self.gamma)
+            torch.cuda.current_stream().wait_stream(side)
             self._graph = g
             generations -= 1
         for _ in range(generations):
-            hop = self.hop_every and (self.generation + 1) % self.hop_every == 0
-            if hop:
+            if self._gamma() != self.gamma:
                 self.step()
             else:
                 self._graph.replay()
                 self.generation += 1
                 self.proposed += 2 * self.half
-
-    def _graph_gen(self) -> None:
-        for first, other in ((0, self.half), (self.half, 0)):
-            cur = self.states[first:first + self.half]
-            eps = torch.randn((self.half, self.npar), generator=self.gen, dtype=torch.float64,
-                              device=self.states.device) * (self.eps_scale * cur.abs())
-            u = torch.rand(self.half, generator=self.gen, dtype=torch.float64,
-                           device=self.states.device).clamp_min_(1e-300)
-            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, self.half,
-                           self.gamma, self._partners(other), eps, u, self._prop, self._cp,
-                           self._acc, self.t0, self.jitter, self.mode)
-            self._n_acc += self._acc.sum()
 
     @property
     def acceptance(self) -> float:
