@@ -300,12 +300,52 @@ __device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &
   return E + d;
 }
 
+// Table-driven sin/cos in double (the table method of Tang, 1989-1991):
+// x = k (2 pi/N) + b with k the nearest integer to x N/(2 pi) (chosen in
+// single precision from x as a float, kf), b reduced in double with 2 pi/N
+// split into two doubles, |b| <= pi/N + 1e-5; sin b and cos b by Taylor
+// series to b^5 and b^6 (truncation below 1e-17 at N = 256); then
+// sin x = S_k cos b + C_k sin b, cos x = C_k cos b - S_k sin b with
+// (S_k, C_k) = (sin, cos)(2 pi k/N) from a table in shared memory
+// (sincos_table_build).  13 FP64 operations against 21 for sincos_f64.
+constexpr int kSinTabN = 256;
+constexpr double kTabStepHi = 0.02454369260617026;      // RN(2 pi/256)
+constexpr double kTabStepLo = 9.567553118338697e-19;    // 2 pi/256 - hi
+constexpr float kTabInvStepF = 40.74366543152521f;      // 256/(2 pi)
+
+__device__ __forceinline__ void sincos_table_build(double2 *tab, int tid, int nthreads) {
+  for (int i = tid; i < kSinTabN; i += nthreads) {
+    double s, c;
+    sincos_f64(fma((double)i, kTabStepHi, (double)i * kTabStepLo), s, c);
+    tab[i] = make_double2(s, c);
+  }
+}
+
+// x must equal the float xf (the FP64 path evaluates sin/cos at its
+// single-precision Kepler solution).
+__device__ __forceinline__ void sincos_tab(double x, float xf, const double2 *tab, double &s,
+                                           double &c) {
+  const float kf = rintf(xf * kTabInvStepF);
+  const double kd = f2d(kf);
+  double b = fma(-kd, kTabStepHi, x);
+  b = fma(-kd, kTabStepLo, b);
+  const double b2 = b * b;
+  const double sb = fma(b * b2, fma(b2, 1.0 / 120.0, -1.0 / 6.0), b);
+  const double cb = fma(b2, fma(b2, fma(b2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double2 sc = tab[(int)kf & (kSinTabN - 1)];
+  s = fma(sc.x, cb, sc.y * sb);
+  c = fma(sc.y, cb, -(sc.x * sb));
+}
+
 // Kepler's equation in double precision.  The single-precision solve (all
 // three steps on MUFU sin/cos; error below 2e-5 for e <= 0.95) seeds one
 // double-precision Danby step, whose quartic convergence lands on the
 // double root; sin/cos of the result follow by angle addition to second
 // order in that last step.
-__device__ __forceinline__ double kepler_f64(double M, double e, double &sE, double &cE) {
+// With a table (tab != nullptr, sincos_table_build), sin/cos at the
+// single-precision solution come from sincos_tab.
+__device__ __forceinline__ double kepler_f64(double M, double e, double &sE, double &cE,
+                                             const double2 *tab = nullptr) {
   const float Mf = d2f(M), ef = d2f(e);
   float Ef = kepler_start(Mf, ef);
 #pragma unroll
@@ -313,7 +353,10 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
     Ef += danby_delta_f32(Ef, Mf, ef, sin_fast(Ef), cos_fast(Ef));
   const double E = f2d(Ef);
   double s, c;
-  sincos_f64(E, s, c);
+  if (tab)
+    sincos_tab(E, Ef, tab, s, c);
+  else
+    sincos_f64(E, s, c);
   const double d = danby_delta_f64(E, M, e, s, c);
   const double hd2 = 0.5 * d * d;
   sE = fma(d, c, fma(-hd2, s, s));

@@ -45,9 +45,10 @@ struct ObsD {
 };
 
 struct F64Layout {
-  size_t pl, gam, s2, red, obs, total;
+  size_t tab, pl, gam, s2, red, obs, total;
   __host__ __device__ F64Layout(int ST, int J, int nwarps, int obs_tile) {
-    pl = 0;
+    tab = 0;                                          // sin/cos table, 4 KB
+    pl = tab + sizeof(double2) * kSinTabN;
     gam = pl + sizeof(PlanetD) * ST * J;
     s2 = gam + sizeof(double) * ST;
     red = align_up(s2 + sizeof(double) * ST, 16);
@@ -453,6 +454,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   const int block = blockDim.x;
   const int ST = block / G;
   const F64Layout L(ST, J, block / 32, obs_tile);
+  double2 *tab_s = reinterpret_cast<double2 *>(smem + L.tab);
   PlanetD *pl_s = reinterpret_cast<PlanetD *>(smem + L.pl);
   double *gam_s = reinterpret_cast<double *>(smem + L.gam);
   double *s2_s = reinterpret_cast<double *>(smem + L.s2);
@@ -464,6 +466,8 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   const int npar = 5 * J + 1 + (NLL ? 1 : 0);
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   const double dref = t_ref - a.t0;
+  const bool want_resid = resid_out != nullptr;
+  sincos_table_build(tab_s, tid, block);      // read after the tile loop's first barrier
 
   for (int i = setup_slot(tid, block >> 5); i < ST * J; i += block) {
     const int sl = i / J, j = i - sl * J;
@@ -504,8 +508,8 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
         const PlanetD p = q[j];
         const double M = mean_anomaly_f64(o.tau, p);
         double sE, cE;
-        const double E = kepler_f64(M, p.e, sE, cE);
-        rmax = fmax(rmax, fabs((E - M) - p.e * sE));
+        const double E = kepler_f64(M, p.e, sE, cE, tab_s);
+        if (want_resid) rmax = fmax(rmax, fabs((E - M) - p.e * sE));
         V += velocity_f64(p, sE, cE);
       }
       const double r = V - o.v;
