@@ -134,9 +134,10 @@ struct ObsGD {
 };
 
 struct F64GradLayout {
-  size_t pl, gam, sj, obs, total;
+  size_t tab, pl, gam, sj, obs, total;
   __host__ __device__ F64GradLayout(int ST, int J, int obs_tile) {
-    pl = 0;
+    tab = 0;                                          // sin/cos table, 4 KB
+    pl = tab + sizeof(double2) * kSinTabN;
     gam = pl + sizeof(GradPlanetD) * ST * J;
     sj = gam + sizeof(double) * ST;
     obs = align_up(sj + sizeof(double) * ST, 16);
@@ -292,6 +293,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
   const int block = blockDim.x;
   const int ST = block / G;
   const F64GradLayout L(ST, J, obs_tile);
+  double2 *tab_s = reinterpret_cast<double2 *>(smem + L.tab);
   GradPlanetD *pl_s = reinterpret_cast<GradPlanetD *>(smem + L.pl);
   double *gam_s = reinterpret_cast<double *>(smem + L.gam);
   double *sj_s = reinterpret_cast<double *>(smem + L.sj);
@@ -301,6 +303,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
   const int64_t sys0 = (int64_t)blockIdx.x * ST;
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   const double dref = t_ref - a.t0;
+  sincos_table_build(tab_s, tid, block);      // read after the tile loop's first barrier
 
   for (int i = (tid & 31) * (block >> 5) + (tid >> 5); i < ST * J; i += block) {
     const int sl = i / J, j = i - sl * J;
@@ -345,7 +348,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
       for (int j = 0; j < J; ++j) {
         const PlanetD p = q[j].base;
         const double M = mean_anomaly_f64(o.tau, p);
-        kepler_f64(M, p.e, sEj[j], cEj[j]);
+        kepler_f64(M, p.e, sEj[j], cEj[j], tab_s);
         V += velocity_f64(p, sEj[j], cEj[j]);
       }
       const double r = V - o.v;
