@@ -341,11 +341,12 @@ constexpr int kMaxWarps = 8;   // block <= 256
 // order of work), set up its planets (one lane per planet, FP64), evaluate
 // it with 32 lanes over its observations, reduce, write; until the queue is
 // empty.  The queue counter must be zero at launch.
-// At most 128 registers: two CTAs of 256 threads per SM.  The gradient body
+// Gradient: at most 128 registers, two CTAs of 256 threads per SM; the body
 // then keeps part of its accumulators in local memory, and still runs 1.26x
 // faster than at one CTA per SM (252 registers) on the ragged workload.
+// Forward: at most 80 registers, three CTAs per SM (1.08x over two).
 template <bool GRAD>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, GRAD ? 2 : 3)
 ragged_mixed_kernel(RaggedDev d, const float4 *__restrict__ oa, const float2 *__restrict__ ob,
                     const double *__restrict__ params, float *__restrict__ chi2,
                     float *__restrict__ grad, unsigned long long *__restrict__ queue) {
