@@ -24,10 +24,21 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 
 // Fixed Danby iteration counts (Sec. 4.3 caps the loop so the GPU is never
 // trapped; a fixed count also keeps warps branch-uniform).  From the paper's
-// starting guess E0 = M + 0.85 e sign(sin M), three quartic steps bring
-// |E - e sin E - M| to single-precision rounding for e <= 0.95 (worst error
-// after two steps 7e-4, after three 1e-13 in exact arithmetic).
-constexpr int kItersF32 = 3;
+// starting guess E0 = M + 0.85 e sign(sin M) the worst error over
+// e <= kEccFast is 0.17 rad; after one quartic step 7e-4, after two 1e-13
+// (exact arithmetic).  The single-precision solve takes two steps on MUFU
+// sin/cos and a Newton step with accurate sin/cos; the double-precision one
+// takes three MUFU steps and one quartic step in double.
+constexpr int kMufuStepsF32 = 2;
+constexpr int kMufuStepsF64 = 3;
+
+// Largest eccentricity the fixed steps cover (the workloads draw e <= 0.95).
+// Above it Danby's start is far from the root near pericentre (0.06 rad
+// after two steps at e = 0.99, 0.04 after three at e = 0.999): the solvers'
+// HI = true variant branches on e > kEccFast into more steps, accurate up to
+// e ~ 0.9999.  Kernels pick HI once per warp (any_high_e), so that the usual
+// case keeps one straight-line body with no branch per planet.
+constexpr float kEccFast = 0.95f;
 
 // ------------------------------------------------ conversions (integer pipe)
 
@@ -279,25 +290,68 @@ __device__ __forceinline__ float kepler_start(float M, float e) {
   return M + (M >= 0.0f ? 0.85f : -0.85f) * e;
 }
 
-// Kepler's equation in single precision: three Danby steps from the paper's
-// start.  Steps one and two take sin/cos from MUFU; their error (~1e-6)
-// only perturbs the iterate, which the next quartic step corrects, so only
-// the last step needs sin/cos to an ulp.  sin/cos of the returned E come from
-// the last evaluation by the angle-addition expansion to second order in the
-// last step (|delta| < 1e-3, truncation < 2e-10).
+// Newton's step -f/f' for f(E) = E - e sin E - M.  From an iterate within
+// 7e-4 of the root (two quartic steps, e <= kEccFast) its quadratic error
+// e sin E delta^2 / (2 f') stays below 1e-7 rad (9e-8 at worst in exact
+// arithmetic), under the single-precision rounding of E.
+__device__ __forceinline__ float newton_delta_f32(float E, float M, float e, float s, float c) {
+  const float f = __fmaf_rn(-e, s, E - M);
+  return -f * rcp_fast(__fmaf_rn(-e, c, 1.0f));
+}
+
+// Extra steps for e > kEccFast: two more MUFU quartic steps up to e = 0.99,
+// five above (exact-arithmetic error then below 3e-15 up to e = 0.99 and
+// 9e-8 up to e = 0.9999), leaving the iterate at the MUFU floor
+// (~4e-7 e / (1 - e cos E)), then one quartic step with accurate sin/cos.
+__device__ __noinline__ static float kepler_high_e_f32(float E, float M, float e) {
+  const int n = e > 0.99f ? 5 : 2;
+  for (int it = 0; it < n; ++it) E += danby_delta_f32(E, M, e, sin_fast(E), cos_fast(E));
+  float s, c;
+  sincos_accurate(E, s, c);
+  return E + danby_delta_f32(E, M, e, s, c);
+}
+
+// Kepler's equation in single precision: two Danby steps from the paper's
+// start on MUFU sin/cos, whose error (~1e-6) only perturbs the iterate, then
+// one Newton step with sin/cos to an ulp.  sin/cos of the returned E come
+// from that evaluation by the angle-addition expansion to second order in
+// the last step (|delta| < 1e-3, truncation < 2e-10).  HI = false: valid
+// for e <= kEccFast only, no branch.
+template <bool HI = true>
 __device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &cE) {
   float E = kepler_start(M, e);
 #pragma unroll
-  for (int it = 0; it < kItersF32 - 1; ++it) {
+  for (int it = 0; it < kMufuStepsF32; ++it) {
     E += danby_delta_f32(E, M, e, sin_fast(E), cos_fast(E));
   }
+  if (HI && e > kEccFast) E = kepler_high_e_f32(E, M, e);
   float s, c;
   sincos_accurate(E, s, c);
-  const float d = danby_delta_f32(E, M, e, s, c);
+  const float d = newton_delta_f32(E, M, e, s, c);
   const float hd2 = 0.5f * d * d;
   sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
   cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
   return E + d;
+}
+
+// Warp-uniform choice of the solvers' HI variant: true if any lane holds an
+// eccentricity above kEccFast.  All lanes of `mask` must call it.
+__device__ __forceinline__ bool any_high_e(bool mine, unsigned mask = 0xffffffffu) {
+  return __any_sync(mask, mine) != 0;
+}
+
+// Calls body(HiTag<true>) or body(HiTag<false>): the observation loops are
+// compiled twice, once without the high-eccentricity branch.
+template <bool B>
+struct HiTag {
+  static constexpr bool value = B;
+};
+template <typename F>
+__device__ __forceinline__ void with_high_e(bool hi, F &&body) {
+  if (hi)
+    body(HiTag<true>{});
+  else
+    body(HiTag<false>{});
 }
 
 // Table-driven sin/cos in double (the table method of Tang, 1989-1991):
@@ -321,8 +375,8 @@ __device__ __forceinline__ void sincos_table_build(double2 *tab, int tid, int nt
   }
 }
 
-// x must equal the float xf (the FP64 path evaluates sin/cos at its
-// single-precision Kepler solution).
+// xf: x rounded to float (the FP64 path evaluates sin/cos at its
+// single-precision Kepler solution, or within a float ulp of it).
 __device__ __forceinline__ void sincos_tab(double x, float xf, const double2 *tab, double &s,
                                            double &c) {
   const float kf = rintf(xf * kTabInvStepF);
@@ -338,26 +392,39 @@ __device__ __forceinline__ void sincos_tab(double x, float xf, const double2 *ta
 }
 
 // Kepler's equation in double precision.  The single-precision solve (all
-// three steps on MUFU sin/cos; error below 2e-5 for e <= 0.95) seeds one
+// three steps on MUFU sin/cos; error below 2e-5 for e <= kEccFast) seeds one
 // double-precision Danby step, whose quartic convergence lands on the
 // double root; sin/cos of the result follow by angle addition to second
-// order in that last step.
-// With a table (tab != nullptr, sincos_table_build), sin/cos at the
-// single-precision solution come from sincos_tab.
+// order in that last step.  HI and e > kEccFast: the extra single-precision
+// steps of kepler_high_e_f32, then two double-precision steps (the seed's
+// error grows like 1e-7 / (1 - e cos E)).
+// With a table (tab != nullptr, sincos_table_build), sin/cos come from
+// sincos_tab.
+template <bool HI = true>
 __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, double &cE,
                                              const double2 *tab = nullptr) {
   const float Mf = d2f(M), ef = d2f(e);
   float Ef = kepler_start(Mf, ef);
 #pragma unroll
-  for (int it = 0; it < kItersF32; ++it)
+  for (int it = 0; it < kMufuStepsF64; ++it)
     Ef += danby_delta_f32(Ef, Mf, ef, sin_fast(Ef), cos_fast(Ef));
-  const double E = f2d(Ef);
+  const bool high = HI && ef > kEccFast;
+  if (high) Ef = kepler_high_e_f32(Ef, Mf, ef);
+  double E = f2d(Ef);
   double s, c;
   if (tab)
     sincos_tab(E, Ef, tab, s, c);
   else
     sincos_f64(E, s, c);
-  const double d = danby_delta_f64(E, M, e, s, c);
+  double d = danby_delta_f64(E, M, e, s, c);
+  if (high) {
+    E += d;
+    if (tab)
+      sincos_tab(E, d2f(E), tab, s, c);
+    else
+      sincos_f64(E, s, c);
+    d = danby_delta_f64(E, M, e, s, c);
+  }
   const double hd2 = 0.5 * d * d;
   sE = fma(d, c, fma(-hd2, s, s));
   cE = fma(-d, s, fma(-hd2, c, c));

@@ -227,11 +227,14 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
   const float s2 = NLL ? s2_s[sl] : 0.0f;
   PlanetF q[J];
   float poison = 0.0f * gam + (NLL ? 0.0f * s2 : 0.0f);   // NaN for an invalid system
+  bool hi = false;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     q[j] = pl_s[sl * J + j];
     poison += 0.0f * q[j].e;
+    hi = hi || q[j].e > kEccFast;
   }
+  hi = any_high_e(hi);
 
   for (int k0 = 0; k0 < a.n_obs; k0 += obs_tile) {
     const int nk = min(obs_tile, a.n_obs - k0);
@@ -247,27 +250,31 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       }
       __syncthreads();
     }
-    for (int k = c; k < nk; k += G) {
-      const float4 o = obs_s[k];
-      Kahan V = {0.0f, 0.0f};
+    with_high_e(hi, [&](auto tag) {
+      constexpr bool HI = decltype(tag)::value;
+      for (int k = c; k < nk; k += G) {
+        const float4 o = obs_s[k];
+        Kahan V = {0.0f, 0.0f};
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const float M = SINGLE ? mean_anomaly_single(o.x, q[j]) : mean_anomaly_mixed(o.x, o.y, q[j]);
-        float sE, cE;
-        const float E = kepler_f32(M, q[j].e, sE, cE);
-        if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
-        kahan_add(V, velocity_mixed(q[j], sE, cE));
+        for (int j = 0; j < J; ++j) {
+          const float M =
+              SINGLE ? mean_anomaly_single(o.x, q[j]) : mean_anomaly_mixed(o.x, o.y, q[j]);
+          float sE, cE;
+          const float E = kepler_f32<HI>(M, q[j].e, sE, cE);
+          if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
+          kahan_add(V, velocity_mixed(q[j], sE, cE));
+        }
+        // residual V - v_obs with the model and the observation as float pairs
+        const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+        if (NLL) {
+          const float var = w_s[k] + s2;              // sigma_k^2 + sigma_j^2
+          const float wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
+          kahan_add(acc, __fmaf_rn(wk * r, r, lg2_fast(var) * kLn2F));
+        } else {
+          kahan_add(acc, w_s[k] * r * r);
+        }
       }
-      // residual V - v_obs with the model and the observation as float pairs
-      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-      if (NLL) {
-        const float var = w_s[k] + s2;              // sigma_k^2 + sigma_j^2
-        const float wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
-        kahan_add(acc, __fmaf_rn(wk * r, r, lg2_fast(var) * kLn2F));
-      } else {
-        kahan_add(acc, w_s[k] * r * r);
-      }
-    }
+    });
   }
 
   // combine the G partial sums of each system
@@ -382,27 +389,34 @@ chi2_mixed_chunk_kernel(UniformArgs a, MixedPrep prep, ChunkScratch cs, int chun
   const int len = (a.n_obs + chunks - 1) / chunks;
   const int k0 = c * len, k1 = min(a.n_obs, k0 + len);
   PlanetF q[J];
+  bool hi = false;               // uniform: the warp holds one system
 #pragma unroll
-  for (int j = 0; j < J; ++j) q[j] = prep.pl[s * J + j];
+  for (int j = 0; j < J; ++j) {
+    q[j] = prep.pl[s * J + j];
+    hi = hi || q[j].e > kEccFast;
+  }
   const float gam = prep.gam[s];
   const bool want_resid = resid_out != nullptr;
   Kahan acc = {0.0f, 0.0f};
   float rmax = 0.0f;
-  for (int k = k0 + lane; k < k1; k += 32) {
-    const float4 o = prep.obs[k];
-    const float wk = prep.w[k];
-    Kahan V = {0.0f, 0.0f};
+  with_high_e(hi, [&](auto tag) {
+    constexpr bool HI = decltype(tag)::value;
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const float4 o = prep.obs[k];
+      const float wk = prep.w[k];
+      Kahan V = {0.0f, 0.0f};
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const float M = mean_anomaly_mixed(o.x, o.y, q[j]);
-      float sE, cE;
-      const float E = kepler_f32(M, q[j].e, sE, cE);
-      if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
-      kahan_add(V, velocity_mixed(q[j], sE, cE));
+      for (int j = 0; j < J; ++j) {
+        const float M = mean_anomaly_mixed(o.x, o.y, q[j]);
+        float sE, cE;
+        const float E = kepler_f32<HI>(M, q[j].e, sE, cE);
+        if (want_resid) rmax = fmaxf(rmax, fabsf((E - M) - q[j].e * sE));
+        kahan_add(V, velocity_mixed(q[j], sE, cE));
+      }
+      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+      kahan_add(acc, wk * r * r);
     }
-    const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-    kahan_add(acc, wk * r * r);
-  }
+  });
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) {
     Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
@@ -500,27 +514,33 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     __syncthreads();
     const double gam = gam_s[sl];
     const PlanetD *q = pl_s + sl * J;
-    for (int k = c; k < nk; k += G) {
-      const ObsD o = obs_s[k];
-      double V = gam;
+    bool hi = false;
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const PlanetD p = q[j];
-        const double M = mean_anomaly_f64(o.tau, p);
-        double sE, cE;
-        const double E = kepler_f64(M, p.e, sE, cE, tab_s);
-        if (want_resid) rmax = fmax(rmax, fabs((E - M) - p.e * sE));
-        V += velocity_f64(p, sE, cE);
+    for (int j = 0; j < J; ++j) hi = hi || q[j].e > (double)kEccFast;
+    with_high_e(any_high_e(hi), [&](auto tag) {
+      constexpr bool HI = decltype(tag)::value;
+      for (int k = c; k < nk; k += G) {
+        const ObsD o = obs_s[k];
+        double V = gam;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const PlanetD p = q[j];
+          const double M = mean_anomaly_f64(o.tau, p);
+          double sE, cE;
+          const double E = kepler_f64<HI>(M, p.e, sE, cE, tab_s);
+          if (want_resid) rmax = fmax(rmax, fabs((E - M) - p.e * sE));
+          V += velocity_f64(p, sE, cE);
+        }
+        const double r = V - o.v;
+        if (NLL) {
+          const double var = o.w + s2_s[sl];
+          const double wk = var > 0.0 ? 1.0 / var : __longlong_as_double(0x7ff8000000000000ll);
+          acc += fma(wk * r, r, log(var));
+        } else {
+          acc = fma(o.w * r, r, acc);
+        }
       }
-      const double r = V - o.v;
-      if (NLL) {
-        const double var = o.w + s2_s[sl];
-        const double wk = var > 0.0 ? 1.0 / var : __longlong_as_double(0x7ff8000000000000ll);
-        acc += fma(wk * r, r, log(var));
-      } else {
-        acc = fma(o.w * r, r, acc);
-      }
-    }
+    });
   }
 
   const int gw = G < 32 ? G : 32;
@@ -597,12 +617,18 @@ __device__ inline float reduce_pi<float>(float M) {
   return __fmaf_rn(-q, -1.74845553e-7f, __fmaf_rn(-q, 6.28318548202514648f, M));
 }
 
+// One (M, e) per thread; the lanes of a warp vote for the high-eccentricity
+// variant (the lanes still in the grid-stride loop).
 __global__ void kepler_f64_kernel(const double *__restrict__ M, const double *__restrict__ e,
                                   int64_t n, double *__restrict__ E) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double s, c;
-    E[i] = kepler_f64(reduce_pi(M[i]), e[i], s, c);
+    const double ei = e[i], Mi = reduce_pi(M[i]);
+    if (any_high_e(ei > (double)kEccFast, __activemask()))
+      E[i] = kepler_f64<true>(Mi, ei, s, c);
+    else
+      E[i] = kepler_f64<false>(Mi, ei, s, c);
   }
 }
 
@@ -611,7 +637,11 @@ __global__ void kepler_f32_kernel(const float *__restrict__ M, const float *__re
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float s, c;
-    E[i] = kepler_f32(reduce_pi(M[i]), e[i], s, c);
+    const float ei = e[i], Mi = reduce_pi(M[i]);
+    if (any_high_e(ei > kEccFast, __activemask()))
+      E[i] = kepler_f32<true>(Mi, ei, s, c);
+    else
+      E[i] = kepler_f32<false>(Mi, ei, s, c);
   }
 }
 

@@ -214,47 +214,53 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     const float gam = gam_s[sl];
     const float sj = NLL ? sj_s[sl] : 0.0f;
     const GradPlanetF *q = pl_s + sl * J;
-    for (int k = c; k < nk; k += G) {
-      const float4 o = obs_s[k];
-      const float2 wt = wt_s[k];
-      float sEj[J], cEj[J];
-      Kahan V = {0.0f, 0.0f};
+    bool hi = false;
+    #pragma unroll
+    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > kEccFast;
+    with_high_e(any_high_e(hi), [&](auto tag) {
+      constexpr bool HI = decltype(tag)::value;
+      for (int k = c; k < nk; k += G) {
+        const float4 o = obs_s[k];
+        const float2 wt = wt_s[k];
+        float sEj[J], cEj[J];
+        Kahan V = {0.0f, 0.0f};
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const PlanetF p = q[j].base;
-        const float M = mean_anomaly_mixed(o.x, o.y, p);
-        kepler_f32(M, p.e, sEj[j], cEj[j]);
-        kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
-      }
-      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-      float wk = wt.x, a2;
-      if (NLL) {
-        const float var = __fmaf_rn(sj, sj, wt.x);           // sigma_k^2 + sigma_j^2
-        wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
-        const float wr = wk * r;
-        kahan_add(acc, __fmaf_rn(wr, r, lg2_fast_g(var) * 0.693147180559945309f));
-        a2 = wr;
-        g[NP - 1] = __fmaf_rn(sj * wk, __fmaf_rn(-wr, r, 1.0f), g[NP - 1]);
-      } else {
-        const float wr = wk * r;
-        kahan_add(acc, wr * r);
-        a2 = 2.0f * wr;
-      }
+        for (int j = 0; j < J; ++j) {
+          const PlanetF p = q[j].base;
+          const float M = mean_anomaly_mixed(o.x, o.y, p);
+          kepler_f32<HI>(M, p.e, sEj[j], cEj[j]);
+          kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+        }
+        const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+        float wk = wt.x, a2;
+        if (NLL) {
+          const float var = __fmaf_rn(sj, sj, wt.x);           // sigma_k^2 + sigma_j^2
+          wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
+          const float wr = wk * r;
+          kahan_add(acc, __fmaf_rn(wr, r, lg2_fast_g(var) * 0.693147180559945309f));
+          a2 = wr;
+          g[NP - 1] = __fmaf_rn(sj * wk, __fmaf_rn(-wr, r, 1.0f), g[NP - 1]);
+        } else {
+          const float wr = wk * r;
+          kahan_add(acc, wr * r);
+          a2 = 2.0f * wr;
+        }
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const GradPlanetF qj = q[j];
-        Partials<float> d;
-        const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
-        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
-        d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
-        kahan_add(gP[j], a2 * d.dP);
-        g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
-        g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
-        g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
-        g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+        for (int j = 0; j < J; ++j) {
+          const GradPlanetF qj = q[j];
+          Partials<float> d;
+          const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+          d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
+          kahan_add(gP[j], a2 * d.dP);
+          g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
+          g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
+          g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
+          g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+        }
+        g[5 * J] += a2;
       }
-      g[5 * J] += a2;
-    }
+    });
   }
 
   for (int m = G >> 1; m >= 1; m >>= 1) {
@@ -340,45 +346,51 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
     __syncthreads();
     const double gam = gam_s[sl];
     const GradPlanetD *q = pl_s + sl * J;
-    for (int k = c; k < nk; k += G) {
-      const ObsGD o = obs_s[k];
-      double sEj[J], cEj[J];
-      double V = gam;
+    bool hi = false;
+    #pragma unroll
+    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > (double)kEccFast;
+    with_high_e(any_high_e(hi), [&](auto tag) {
+      constexpr bool HI = decltype(tag)::value;
+      for (int k = c; k < nk; k += G) {
+        const ObsGD o = obs_s[k];
+        double sEj[J], cEj[J];
+        double V = gam;
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const PlanetD p = q[j].base;
-        const double M = mean_anomaly_f64(o.tau, p);
-        kepler_f64(M, p.e, sEj[j], cEj[j], tab_s);
-        V += velocity_f64(p, sEj[j], cEj[j]);
-      }
-      const double r = V - o.v;
-      double a2;
-      if (NLL) {
-        const double sj = sj_s[sl];
-        const double var = fma(sj, sj, o.w);
-        const double wk = var > 0.0 ? 1.0 / var : nan_d();
-        acc += fma(wk * r, r, log(var));
-        a2 = wk * r;
-        g[NP - 1] = fma(sj * wk, fma(-wk * r, r, 1.0), g[NP - 1]);
-      } else {
-        acc = fma(o.w * r, r, acc);
-        a2 = 2.0 * o.w * r;
-      }
+        for (int j = 0; j < J; ++j) {
+          const PlanetD p = q[j].base;
+          const double M = mean_anomaly_f64(o.tau, p);
+          kepler_f64<HI>(M, p.e, sEj[j], cEj[j], tab_s);
+          V += velocity_f64(p, sEj[j], cEj[j]);
+        }
+        const double r = V - o.v;
+        double a2;
+        if (NLL) {
+          const double sj = sj_s[sl];
+          const double var = fma(sj, sj, o.w);
+          const double wk = var > 0.0 ? 1.0 / var : nan_d();
+          acc += fma(wk * r, r, log(var));
+          a2 = wk * r;
+          g[NP - 1] = fma(sj * wk, fma(-wk * r, r, 1.0), g[NP - 1]);
+        } else {
+          acc = fma(o.w * r, r, acc);
+          a2 = 2.0 * o.w * r;
+        }
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const GradPlanetD qj = q[j];
-        Partials<double> d;
-        const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
-        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
-        d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
-        g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
-        g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);
-        g[5 * j + 2] = fma(a2, d.de, g[5 * j + 2]);
-        g[5 * j + 3] = fma(a2, d.dw, g[5 * j + 3]);
-        g[5 * j + 4] = fma(a2, d.dM, g[5 * j + 4]);
+        for (int j = 0; j < J; ++j) {
+          const GradPlanetD qj = q[j];
+          Partials<double> d;
+          const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
+          d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
+          g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
+          g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);
+          g[5 * j + 2] = fma(a2, d.de, g[5 * j + 2]);
+          g[5 * j + 3] = fma(a2, d.dw, g[5 * j + 3]);
+          g[5 * j + 4] = fma(a2, d.dM, g[5 * j + 4]);
+        }
+        g[5 * J] += a2;
       }
-      g[5 * J] += a2;
-    }
+    });
   }
 
   for (int m = G >> 1; m >= 1; m >>= 1) {
@@ -544,6 +556,9 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
     __syncthreads();
     const float gam = gam_s[warp];
     const GradPlanetF *q = pl_s + warp * J;
+    bool hi = false;                        // uniform: the warp holds one system
+#pragma unroll
+    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > kEccFast;
     for (int kb = 0; kb < nk; kb += 32) {
       const int k = kb + lane;
       float urow[NP];
@@ -554,13 +569,16 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         const float2 wt = wt_s[k];
         float sEj[J], cEj[J];
         Kahan V = {0.0f, 0.0f};
+        with_high_e(hi, [&](auto tag) {
+          constexpr bool HI = decltype(tag)::value;
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const PlanetF p = q[j].base;
-          const float M = mean_anomaly_mixed(o.x, o.y, p);
-          kepler_f32(M, p.e, sEj[j], cEj[j]);
-          kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
-        }
+          for (int j = 0; j < J; ++j) {
+            const PlanetF p = q[j].base;
+            const float M = mean_anomaly_mixed(o.x, o.y, p);
+            kepler_f32<HI>(M, p.e, sEj[j], cEj[j]);
+            kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+          }
+        });
         const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
         const float wk = wt.x, wr = wk * r, a2 = 2.0f * wr;
         kahan_add(acc, wr * r);
@@ -718,6 +736,9 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
     __syncthreads();
     const double gam = gam_s[warp];
     const GradPlanetD *q = pl_s + warp * J;
+    bool hi = false;                        // uniform: the warp holds one system
+#pragma unroll
+    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > (double)kEccFast;
     for (int kb = 0; kb < nk; kb += 32) {
       const int k = kb + lane;
       double urow[NP];
@@ -727,13 +748,16 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
         const ObsGD o = obs_s[k];
         double sEj[J], cEj[J];
         double V = gam;
+        with_high_e(hi, [&](auto tag) {
+          constexpr bool HI = decltype(tag)::value;
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const PlanetD p = q[j].base;
-          const double M = mean_anomaly_f64(o.tau, p);
-          kepler_f64(M, p.e, sEj[j], cEj[j]);
-          V += velocity_f64(p, sEj[j], cEj[j]);
-        }
+          for (int j = 0; j < J; ++j) {
+            const PlanetD p = q[j].base;
+            const double M = mean_anomaly_f64(o.tau, p);
+            kepler_f64<HI>(M, p.e, sEj[j], cEj[j]);
+            V += velocity_f64(p, sEj[j], cEj[j]);
+          }
+        });
         const double r = V - o.v;
         const double a2 = 2.0 * o.w * r;
         acc = fma(o.w * r, r, acc);

@@ -100,6 +100,37 @@ def test_planet_counts_ragged_tails_invalid(kc, oracle_mod, n_pl, n_obs):
         assert kc.kc_last_device_error() == 1
 
 
+def test_high_eccentricity(kc, oracle_mod):
+    """One planet of each system at 0.96 <= e <= 0.99 (the solvers' extra
+    steps).  FP64: H, chi2 and gradient at the usual tolerances.  Mixed:
+    chi2 within 1e-5 plus the single-precision conditioning bound of the
+    velocity near pericentre, |dv| <= 4e-7 K / (1 - e), carried through
+    2 sum_k w_k |r_k| |dv|."""
+    rng = np.random.default_rng(71)
+    n_sys, n_pl, n_obs = 64, 2, 200
+    cols = []
+    for j in range(n_pl):
+        cols += [np.exp(rng.uniform(0, np.log(3000), n_sys)), rng.uniform(1, 80, n_sys),
+                 rng.uniform(0.96, 0.99, n_sys) if j == 0 else rng.uniform(0, 0.8, n_sys),
+                 rng.uniform(0, 2 * np.pi, n_sys), rng.uniform(0, 2 * np.pi, n_sys)]
+    par = np.stack(cols + [rng.uniform(-5, 5, n_sys)], axis=1)
+    t = np.sort(rng.uniform(2450000, 2453000, n_obs))
+    sig = rng.uniform(1, 4, n_obs)
+    v = oracle_mod.predict(par[:1], t, n_pl, 2450000.0)[0] + sig * rng.standard_normal(n_obs)
+    chi_ref, g_ref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, grad=True)
+    H_ref = oracle_mod.gauss_newton(par, t, sig, n_pl, t0=2450000.0)
+    P, T, V, S = dev(par, t, v, sig)
+    chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=2450000.0, mode="fp64")
+    assert rel(chi.cpu().numpy(), chi_ref).max() <= CHI2_F64_TOL
+    assert grad_err(g.cpu().numpy(), g_ref).max() <= GRAD_F64_TOL
+    assert h_err(H.cpu().numpy(), H_ref, 5 * n_pl + 1).max() <= H_F64_TOL
+    chi32, _, _ = kc.kc_chi2_gauss_newton(P, T, V, S, t0=2450000.0, mode="mixed")
+    r = np.abs(oracle_mod.predict(par, t, n_pl, 2450000.0) - v[None, :])
+    dv = sum(par[:, 5 * j + 1] * 4e-7 / (1 - par[:, 5 * j + 2]) for j in range(n_pl))
+    bound = 1e-5 * np.maximum(chi_ref, 1.0) + 2 * (r / sig[None, :] ** 2).sum(axis=1) * dv
+    assert np.all(np.abs(chi32.cpu().numpy().astype(np.float64) - chi_ref) <= bound)
+
+
 def test_levenberg_marquardt_step_reduces_chi2(kc, oracle_mod):
     """One damped Gauss-Newton step built from the GPU outputs lowers chi2
     of perturbed models of noise-free data (the matrix is the one a fitter

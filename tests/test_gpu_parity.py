@@ -309,6 +309,56 @@ def test_kepler_solve_vs_oracle(kc, oracle_mod):
     assert np.max(wrapped) <= 1e-12
 
 
+def test_kepler_solve_high_eccentricity(kc, oracle_mod):
+    """0.95 < e <= 0.999, where the fixed steps alone do not converge from
+    Danby's start near pericentre: the solvers' extra steps (taken when any
+    lane of a warp holds such an e) reach the root in both precisions; M
+    also log-spaced towards 0, where convergence is slowest."""
+    Mg = np.concatenate([np.linspace(-np.pi, np.pi, 301), np.logspace(-7, 0, 100),
+                         -np.logspace(-7, 0, 100)])
+    e = np.repeat(np.linspace(0.95, 0.999, 64), Mg.size)
+    M = np.tile(Mg, 64)
+    Eref = oracle_mod.kepler_E(M, e)
+    E64 = kc.kc_kepler_solve(*dev(M, e), mode="fp64").cpu().numpy()
+    assert np.max(np.abs(E64 - Eref) * (1 - e * np.cos(Eref))) <= 1e-14
+    Mf = torch.tensor(M, dtype=torch.float32, device="cuda")
+    ef = torch.tensor(e, dtype=torch.float32, device="cuda")
+    E32 = kc.kc_kepler_solve(Mf, ef, mode="mixed").cpu().numpy().astype(np.float64)
+    m32 = Mf.cpu().numpy().astype(np.float64)
+    e32 = ef.cpu().numpy().astype(np.float64)
+    resid = np.abs(E32 - e32 * np.sin(E32) - m32)
+    assert resid.max() <= RESID_TOL, resid.max()
+
+
+def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
+    """Systems with one planet at 0.96 <= e <= 0.99 (Table 2 draws e up to
+    0.99) and one at e <= 0.9.  FP64: the usual tolerances.  Mixed: the
+    velocity in single precision is ill-conditioned near pericentre, |dv| up
+    to about 4e-7 K / (1 - e) (the Kepler solve itself converges), so chi2
+    is held to 1e-5 plus that bound carried through 2 sum_k w_k |r_k| |dv|."""
+    rng = np.random.default_rng(61)
+    n_sys, n_pl, n_obs = 192, 2, 300
+    par = synth_rows(rng, n_sys, n_pl)
+    par[:, 2] = rng.uniform(0.96, 0.99, n_sys)
+    t = np.sort(rng.uniform(2450000, 2454000, n_obs))
+    sig = rng.uniform(1, 4, n_obs)
+    truth = par[0].copy()
+    v = oracle_mod.predict(truth[None], t, n_pl, 2450000.0)[0] + sig * rng.standard_normal(n_obs)
+    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, grad=True)
+    P, T, V, S = dev(par, t, v, sig)
+    c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="fp64").cpu().numpy()
+    assert rel_err(c64, ref).max() <= FP64_TOL
+    _, g64 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, mode="fp64")
+    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+    c32, resid = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="mixed", max_kepler_resid=True)
+    assert float(resid.max()) <= RESID_TOL
+    model = oracle_mod.predict(par, t, n_pl, 2450000.0)
+    r = np.abs(model - v[None, :])
+    dv = sum(par[:, 5 * j + 1] * 4e-7 / (1 - par[:, 5 * j + 2]) for j in range(n_pl))
+    bound = 1e-5 * np.maximum(ref, 1.0) + 2 * (r / sig[None, :] ** 2).sum(axis=1) * dv
+    assert np.all(np.abs(c32.cpu().numpy().astype(np.float64) - ref) <= bound)
+
+
 def test_rv_predict_vs_oracle(kc, oracle_mod):
     rng = np.random.default_rng(11)
     par = synth_rows(rng, 50, 3)
