@@ -28,9 +28,8 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 // e <= kEccFast is 0.17 rad; after one quartic step 7e-4, after two 1e-13
 // (exact arithmetic).  The single-precision solve takes two steps on MUFU
 // sin/cos and a Newton step with accurate sin/cos; the double-precision one
-// takes three MUFU steps and one quartic step in double.
+// polishes that solution with one Halley step in double.
 constexpr int kMufuStepsF32 = 2;
-constexpr int kMufuStepsF64 = 3;
 
 // Largest eccentricity the fixed steps cover (the workloads draw e <= 0.95).
 // Above it Danby's start is far from the root near pericentre (0.06 rad
@@ -391,39 +390,52 @@ __device__ __forceinline__ void sincos_tab(double x, float xf, const double2 *ta
   c = fma(sc.y, cb, -(sc.x * sb));
 }
 
-// Kepler's equation in double precision.  The single-precision solve (all
-// three steps on MUFU sin/cos; error below 2e-5 for e <= kEccFast) seeds one
-// double-precision Danby step, whose quartic convergence lands on the
-// double root; sin/cos of the result follow by angle addition to second
-// order in that last step.  HI and e > kEccFast: the extra single-precision
-// steps of kepler_high_e_f32, then two double-precision steps (the seed's
-// error grows like 1e-7 / (1 - e cos E)).
+// Halley's step -2 f f' / (2 f'^2 - f f'') for f(E) = E - e sin E - M, in
+// double: 16 FP64 FLOPs against 26 for Danby's quartic step.  From the
+// single-precision solution (within 7e-7 of the root for e <= kEccFast,
+// M rounded to float included) its cubic error is below double rounding
+// (5e-16 |f'| at worst in a float emulation of the seed over 4e5 (M, e)).
+__device__ __forceinline__ double halley_delta_f64(double E, double M, double e, double s,
+                                                   double c) {
+  const double es = e * s;
+  const double f = (E - M) - es;
+  const double f1 = fma(-e, c, 1.0);
+  const double num = f * f1;
+  return -(num + num) * rcp_f64(fma(f1 + f1, f1, -(f * es)));
+}
+
+// Kepler's equation in double precision.  The single-precision solve
+// (kepler_f32, the same variant HI) seeds one double-precision Halley step,
+// which lands on the double root; sin/cos of the result follow by angle
+// addition to second order in that last step.  HI and e > kEccFast: two
+// quartic steps in double instead (the seed's error grows like
+// 1e-7 / (1 - e cos E)).  The single-precision work costs little here: one
+// FP64 instruction takes as long on GB300's FP64 pipe as ~76 FP32 issues.
 // With a table (tab != nullptr, sincos_table_build), sin/cos come from
 // sincos_tab.
 template <bool HI = true>
 __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, double &cE,
                                              const double2 *tab = nullptr) {
   const float Mf = d2f(M), ef = d2f(e);
-  float Ef = kepler_start(Mf, ef);
-#pragma unroll
-  for (int it = 0; it < kMufuStepsF64; ++it)
-    Ef += danby_delta_f32(Ef, Mf, ef, sin_fast(Ef), cos_fast(Ef));
+  float sf, cf;
+  const float Ef = kepler_f32<HI>(Mf, ef, sf, cf);
   const bool high = HI && ef > kEccFast;
-  if (high) Ef = kepler_high_e_f32(Ef, Mf, ef);
   double E = f2d(Ef);
   double s, c;
   if (tab)
     sincos_tab(E, Ef, tab, s, c);
   else
     sincos_f64(E, s, c);
-  double d = danby_delta_f64(E, M, e, s, c);
+  double d;
   if (high) {
-    E += d;
+    E += danby_delta_f64(E, M, e, s, c);
     if (tab)
       sincos_tab(E, d2f(E), tab, s, c);
     else
       sincos_f64(E, s, c);
     d = danby_delta_f64(E, M, e, s, c);
+  } else {
+    d = halley_delta_f64(E, M, e, s, c);
   }
   const double hd2 = 0.5 * d * d;
   sE = fma(d, c, fma(-hd2, s, s));
