@@ -101,6 +101,18 @@ def sm_mhz_for_peaks():
     return pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
 
 
+def hold_gpu(stream, host_us):
+    """Queue a bounded spin of the GPU clock (torch.cuda._sleep, a fixed
+    cycle count) ahead of a timed loop, long enough for the host to enqueue
+    the whole loop meanwhile: the GPU then reaches every start event with
+    the step's work already queued, so the CUDA events bracket GPU work, not
+    host-side launch latency (or a host stalled by the clock sampler)."""
+    import torch
+    cycles = int(max(2000.0, host_us) * sm_mhz_for_peaks())
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(cycles)
+
+
 def kepler_throughput(kc, dev, stream, n=1 << 24):
     """Solutions of Kepler's equation per second (the paper's Table 2 also
     reports this), FP32 and FP64, on n random (M, e) pairs, e <= 0.95."""
@@ -114,6 +126,7 @@ def kepler_throughput(kc, dev, stream, n=1 << 24):
         for _ in range(3):
             kc.kc_kepler_solve(Mx, ex, mode=mode, out=E, stream=stream)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hold_gpu(stream, 10 * 200.0)
         a.record(stream)
         for _ in range(10):
             kc.kc_kepler_solve(Mx, ex, mode=mode, out=E, stream=stream)
@@ -140,6 +153,7 @@ def grid_sweep_throughput(kc, synth, dev, stream, args):
         kc.kc_chi2_eval_mixed(P, T, V, S, out=out, stream=stream)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = 5
+    hold_gpu(stream, steps * 200.0)
     a.record(stream)
     for _ in range(steps):
         kc.kc_chi2_eval_mixed(P, T, V, S, out=out, stream=stream)
@@ -183,6 +197,7 @@ def gradient_throughput(kc, synth, dev, stream, args):
         fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 2 if name.endswith("fp64") else 5
+        hold_gpu(stream, reps * 200.0)
         a.record(stream)
         for _ in range(reps):
             fn()
@@ -209,6 +224,7 @@ def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):
     mc.run(3)                                        # includes the graph capture
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_gpu(torch.cuda.current_stream(dev), generations * 300.0)
     a.record()
     mc.run(generations)
     b.record()
@@ -470,6 +486,7 @@ def run_kc(args):
     torch.cuda.synchronize(dev)
     if sampler:
         sampler.start()
+    hold_gpu(stream, args.steps * 300.0)
     for i in range(args.steps):
         flush.fill_(i & 0xFF)                      # cold L2 for every step
         ev[i][0].record(stream)
@@ -507,6 +524,7 @@ def run_kc(args):
     torch.cuda.synchronize(dev)
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(args.steps)]
+    hold_gpu(stream, args.steps * 400.0)
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         e_ev[i][0].record(stream)
@@ -529,6 +547,7 @@ def run_kc(args):
             kc.kc_chi2_eval(P, T, V, S, out=out64, stream=stream)
         f_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 for _ in range(min(args.steps, 20))]
+        hold_gpu(stream, len(f_ev) * 300.0)
         for a, b in f_ev:
             flush.fill_(1)
             a.record(stream)
@@ -603,6 +622,11 @@ class L2Flush:
         import torch
         self.a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.b = torch.ones(nbytes // 4, dtype=torch.float32, device=dev)
+        # first use loads the fill and reduction kernels (a host stall of up
+        # to a second): done here, outside every timed loop
+        for v in range(2):
+            self.fill_(v)
+        torch.cuda.synchronize(dev)
 
     def fill_(self, v):
         self.a.fill_(v)
@@ -614,6 +638,7 @@ def time_steps(fn, steps, stream, flush):
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
+    hold_gpu(stream, steps * 400.0)
     for i, (a, b) in enumerate(ev):
         flush.fill_(i & 0xFF)
         a.record(stream)
