@@ -359,6 +359,35 @@ def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
     assert np.all(np.abs(c32.cpu().numpy().astype(np.float64) - ref) <= bound)
 
 
+@pytest.mark.parametrize("tile", [(4, 128, 0), (8, 64, 1), (32, 128, 0), (64, 128, 2)])
+def test_high_eccentricity_mixed_warps(kc, oracle_mod, tile):
+    """Every third system has a planet at e = 0.985, the others e <= 0.9:
+    with 4 or 8 threads per system a warp holds several systems, and the
+    warp's vote sends all of them through the solver's extra steps; results
+    must not depend on the neighbours (every system against the oracle)."""
+    rng = np.random.default_rng(62)
+    n_sys, n_pl, n_obs = 300, 3, 160
+    par = synth_rows(rng, n_sys, n_pl)
+    par[::3, 5 + 2] = 0.985
+    t = np.sort(rng.uniform(2450000, 2453000, n_obs))
+    sig = rng.uniform(1, 4, n_obs)
+    v = oracle_mod.predict(par[1:2], t, n_pl, 0.0)[0] + sig * rng.standard_normal(n_obs)
+    ref = oracle_mod.chi2(par, t, v, sig, n_pl)
+    P, T, V, S = dev(par, t, v, sig)
+    kc.kc_set_tile("chi2", "mixed", n_sys, n_pl, n_obs, tile)
+    try:
+        c32, resid = kc.kc_chi2_eval_mixed(P, T, V, S, max_kepler_resid=True)
+    finally:
+        kc.kc_set_tile("chi2", "mixed", n_sys, n_pl, n_obs, None)
+    assert float(resid.max()) <= RESID_TOL
+    r = np.abs(oracle_mod.predict(par, t, n_pl, 0.0) - v[None, :])
+    dv = sum(par[:, 5 * j + 1] * 4e-7 / (1 - par[:, 5 * j + 2]) for j in range(n_pl))
+    bound = 1e-5 * np.maximum(ref, 1.0) + 2 * (r / sig[None, :] ** 2).sum(axis=1) * dv
+    assert np.all(np.abs(c32.cpu().numpy().astype(np.float64) - ref) <= bound)
+    c64 = kc.kc_chi2_eval(P, T, V, S).cpu().numpy()
+    assert rel_err(c64, ref).max() <= FP64_TOL
+
+
 def test_rv_predict_vs_oracle(kc, oracle_mod):
     rng = np.random.default_rng(11)
     par = synth_rows(rng, 50, 3)
