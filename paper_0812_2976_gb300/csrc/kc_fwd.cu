@@ -632,10 +632,39 @@ __global__ void kepler_f64_kernel(const double *__restrict__ M, const double *__
   }
 }
 
+// Four (M, e) per thread and iteration when the three arrays are 16-byte
+// aligned: float4 streaming loads and stores (the data are touched once) and
+// four independent solves in flight per thread, which keeps more loads
+// outstanding than one element per thread does.  The rest (or everything,
+// unaligned) one element per thread.
+template <bool HI>
+__device__ __forceinline__ float4 kepler_f32_x4(float4 m, float4 ee) {
+  float s, c;
+  float4 r;
+  r.x = kepler_f32<HI>(reduce_pi(m.x), ee.x, s, c);
+  r.y = kepler_f32<HI>(reduce_pi(m.y), ee.y, s, c);
+  r.z = kepler_f32<HI>(reduce_pi(m.z), ee.z, s, c);
+  r.w = kepler_f32<HI>(reduce_pi(m.w), ee.w, s, c);
+  return r;
+}
+
 __global__ void kepler_f32_kernel(const float *__restrict__ M, const float *__restrict__ e,
                                   int64_t n, float *__restrict__ E) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(M) | reinterpret_cast<uintptr_t>(e) |
+                         reinterpret_cast<uintptr_t>(E)) & 15u) == 0;
+  const int64_t n4 = aligned ? n / 4 : 0;
+  const float4 *M4 = reinterpret_cast<const float4 *>(M);
+  const float4 *e4 = reinterpret_cast<const float4 *>(e);
+  float4 *E4 = reinterpret_cast<float4 *>(E);
+  for (int64_t i = tid; i < n4; i += stride) {
+    const float4 m = __ldcs(M4 + i), ee = __ldcs(e4 + i);
+    const bool hi = ee.x > kEccFast || ee.y > kEccFast || ee.z > kEccFast || ee.w > kEccFast;
+    __stcs(E4 + i, any_high_e(hi, __activemask()) ? kepler_f32_x4<true>(m, ee)
+                                                  : kepler_f32_x4<false>(m, ee));
+  }
+  for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
     float s, c;
     const float ei = e[i], Mi = reduce_pi(M[i]);
     if (any_high_e(ei > kEccFast, __activemask()))
@@ -879,7 +908,7 @@ cudaError_t launch_kepler_f64(const double *M, const double *e, int64_t n, doubl
 
 cudaError_t launch_kepler_f32(const float *M, const float *e, int64_t n, float *E,
                               cudaStream_t st) {
-  kepler_f32_kernel<<<elementwise_grid(n), 256, 0, st>>>(M, e, n, E);
+  kepler_f32_kernel<<<elementwise_grid((n + 3) / 4), 256, 0, st>>>(M, e, n, E);
   return cudaGetLastError();
 }
 

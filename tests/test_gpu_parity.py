@@ -309,6 +309,24 @@ def test_kepler_solve_vs_oracle(kc, oracle_mod):
     assert np.max(wrapped) <= 1e-12
 
 
+@pytest.mark.parametrize("offset,n", [(0, 1001), (1, 1000), (3, 4093), (0, 3)])
+def test_kepler_solve_alignment_and_tails(kc, oracle_mod, offset, n):
+    """The single-precision solve takes four elements per thread from
+    16-byte-aligned arrays and one at a time otherwise (views that start
+    off the boundary) and for the tail; both give the solver's result."""
+    rng = np.random.default_rng(63 + offset)
+    M = rng.uniform(-3 * np.pi, 3 * np.pi, n + offset)
+    e = rng.uniform(0.0, 0.97, n + offset)
+    Mf = torch.tensor(M, dtype=torch.float32, device="cuda")[offset:]
+    ef = torch.tensor(e, dtype=torch.float32, device="cuda")[offset:]
+    out = torch.full((n + offset,), np.nan, dtype=torch.float32, device="cuda")[offset:]
+    E32 = kc.kc_kepler_solve(Mf, ef, mode="mixed", out=out).cpu().numpy().astype(np.float64)
+    m32 = Mf.cpu().numpy().astype(np.float64)
+    e32 = ef.cpu().numpy().astype(np.float64)
+    resid = np.abs(np.remainder(E32 - e32 * np.sin(E32) - m32 + np.pi, 2 * np.pi) - np.pi)
+    assert resid.max() <= RESID_TOL, resid.max()
+
+
 def test_kepler_solve_high_eccentricity(kc, oracle_mod):
     """0.95 < e <= 0.999, where the fixed steps alone do not converge from
     Danby's start near pericentre: the solvers' extra steps (taken when any
