@@ -80,12 +80,12 @@ def gn_tensor_flops_per_obs(n_pl: int) -> float:
 
 
 # FP64 path, FP64 FLOPs per planet-observation evaluation (FMA = 2), from its
-# algorithm: mean anomaly 14, table-driven sin/cos 22 (reduction 4, b^2 1,
+# algorithm: mean anomaly 12, table-driven sin/cos 22 (reduction 4, b^2 1,
 # sin b 5, cos b 6, table combination 6), Halley step with a one-Newton-step
 # reciprocal 16, last-step update 10, velocity with a one-Newton-step
 # reciprocal 12, accumulation 2 (the FP32 presolve, the single-precision
 # reciprocal seeds and the per-CTA table are not counted).
-F64_FLOPS_PER_EVAL = 14 + 22 + 16 + 10 + 12 + 2
+F64_FLOPS_PER_EVAL = 12 + 22 + 16 + 10 + 12 + 2
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
