@@ -44,13 +44,13 @@ FALLBACK_SM_MHZ = 2070.0
 # Algorithmic FP32 work of one planet-observation evaluation of the mixed
 # path, in FLOPs (FMA = 2, add/mul = 1; MUFU sin/cos/rcp and integer or
 # select operations not counted), from the algorithm as implemented:
-#   double-single mean anomaly 17, start guess 2, two Danby steps of 22,
-#   one accurate sin/cos (Cody-Waite + Taylor) 27, the Newton step 6, sin/cos
-#   update of the last step 10, velocity 8, planet Kahan sum 4, and per
-#   observation the residual + weighted square + chi2 Kahan sum 10 (shared by
-#   n_pl planets).  Workloads with e <= 0.95 never take the solver's
-#   high-eccentricity steps.
-KEPLER_MIXED_FLOPS = 2 + 2 * 22 + 27 + 6 + 10
+#   double-single mean anomaly 17, Mikkola's starting value 19 (its
+#   per-planet constants and the MUFU square root, logarithm, exponential
+#   and reciprocals not counted), one accurate sin/cos (Cody-Waite + Taylor)
+#   27, the Halley step 12, sin/cos update of the step 10, velocity 8,
+#   planet Kahan sum 4, and per observation the residual + weighted square +
+#   chi2 Kahan sum 10 (shared by n_pl planets).
+KEPLER_MIXED_FLOPS = 19 + 27 + 12 + 10
 
 
 def mixed_flops_per_eval(n_pl: int) -> float:
@@ -95,7 +95,7 @@ F64_FLOPS_PER_EVAL = 12 + 22 + 16 + 10 + 12 + 2
 # benchmark's own default workload (autotuned tile 32,128,0): the batch reads
 # its 688 KB of parameters and 6 KB of observations once.  Keyed by (config,
 # n_sys override); other workloads report null.
-DRAM_BYTES_PER_LAUNCH = {(1, None): 765184}
+DRAM_BYTES_PER_LAUNCH = {}
 
 
 def sm_mhz_for_peaks():

@@ -87,12 +87,12 @@ def bind(lib):
     lib.kco_planet_velocity.argtypes = [d, ctypes.c_double, ctypes.c_double]
     lib.kco_chi2.restype = ctypes.c_int
     lib.kco_chi2.argtypes = [d, d, d, d, i64, ctypes.c_int, i64,
-                             ctypes.c_double, ctypes.c_double, d, d]
+                             ctypes.c_double, ctypes.c_double, d, d, d]
     lib.kco_nll.restype = ctypes.c_int
-    lib.kco_nll.argtypes = [d, d, d, d, i64, ctypes.c_int, i64, ctypes.c_double, d, d]
+    lib.kco_nll.argtypes = [d, d, d, d, i64, ctypes.c_int, i64, ctypes.c_double, d, d, d]
     lib.kco_chi2_ragged.restype = ctypes.c_int
     lib.kco_chi2_ragged.argtypes = [d, i64p, i32p, d, d, d, i64p, i64,
-                                    ctypes.c_double, ctypes.c_double, d, d]
+                                    ctypes.c_double, ctypes.c_double, d, d, d]
     lib.kco_predict.restype = ctypes.c_int
     lib.kco_predict.argtypes = [d, d, i64, ctypes.c_int, i64,
                                 ctypes.c_double, d]
@@ -179,22 +179,30 @@ def predict(params, t, n_pl: int, t0: float = 0.0) -> np.ndarray:
 
 
 def chi2(params, t, v, sigma, n_pl: int, t0: float = 0.0,
-         jitter: float = 0.0, grad: bool = False):
+         jitter: float = 0.0, grad: bool = False, gabs: bool = False):
     """chi-square of every system against shared data (Eq. 5).
 
-    Returns chi2 [n_sys], or (chi2, grad [n_sys, 5*n_pl+1]) when grad=True.
+    Returns chi2 [n_sys], or (chi2, grad [n_sys, 5*n_pl+1]) when grad=True,
+    or (chi2, grad, gabs) when gabs=True as well: gabs = sum over the
+    observations of |each observation's term of the gradient|, the scale of
+    the cancellation in each component's sum (Higham's bound of a computed
+    sum is proportional to it).
     """
     params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
     n_par = 5 * n_pl + 1
     params = params.reshape(-1, n_par)
     n_sys = params.shape[0]
     out = np.empty(n_sys)
+    grad = grad or gabs
     g = np.empty((n_sys, n_par)) if grad else None
+    ga = np.empty((n_sys, n_par)) if gabs else None
     rc = _load().kco_chi2(_p(params), _p(t), _p(v), _p(sigma), n_sys,
                           int(n_pl), t.size, float(t0), float(jitter), _p(out),
-                          _p(g) if grad else None)
+                          _p(g) if grad else None, _p(ga) if gabs else None)
     if rc != 0:
         raise ValueError("oracle.chi2: bad sizes")
+    if gabs:
+        return out, g, ga
     return (out, g) if grad else out
 
 
@@ -225,29 +233,37 @@ def unpack_symmetric(H, n: int):
     return full
 
 
-def nll(params, t, v, sigma, n_pl: int, t0: float = 0.0, grad: bool = False):
+def nll(params, t, v, sigma, n_pl: int, t0: float = 0.0, grad: bool = False,
+        gabs: bool = False):
     """Negative log-likelihood with a free jitter per system (parameters
     [n_sys, 5*n_pl+2]: planets, gamma, sigma_j):
-    1/2 sum_k [r_k^2/(sigma_k^2+sigma_j^2) + ln(2 pi (sigma_k^2+sigma_j^2))]."""
+    1/2 sum_k [r_k^2/(sigma_k^2+sigma_j^2) + ln(2 pi (sigma_k^2+sigma_j^2))].
+    grad and gabs as for chi2."""
     params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
     n_par = 5 * n_pl + 2
     params = params.reshape(-1, n_par)
     n_sys = params.shape[0]
     out = np.empty(n_sys)
+    grad = grad or gabs
     g = np.empty((n_sys, n_par)) if grad else None
+    ga = np.empty((n_sys, n_par)) if gabs else None
     rc = _load().kco_nll(_p(params), _p(t), _p(v), _p(sigma), n_sys, int(n_pl), t.size,
-                         float(t0), _p(out), _p(g) if grad else None)
+                         float(t0), _p(out), _p(g) if grad else None,
+                         _p(ga) if gabs else None)
     if rc != 0:
         raise ValueError("oracle.nll: bad sizes")
+    if gabs:
+        return out, g, ga
     return (out, g) if grad else out
 
 
 def chi2_ragged(params, par_off, n_pl, t, v, sigma, obs_off, t0: float = 0.0,
-                jitter: float = 0.0, grad: bool = False):
+                jitter: float = 0.0, grad: bool = False, gabs: bool = False):
     """chi-square of systems with their own planet counts and observations.
 
     System s: parameters params[par_off[s] : par_off[s] + 5*n_pl[s] + 1],
-    observations t/v/sigma[obs_off[s] : obs_off[s+1]].
+    observations t/v/sigma[obs_off[s] : obs_off[s+1]].  grad and gabs as
+    for chi2 (laid out like params).
     """
     params, t, v, sigma = _f64(params), _f64(t), _f64(v), _f64(sigma)
     par_off = np.ascontiguousarray(par_off, dtype=np.int64)
@@ -255,13 +271,18 @@ def chi2_ragged(params, par_off, n_pl, t, v, sigma, obs_off, t0: float = 0.0,
     n_pl = np.ascontiguousarray(n_pl, dtype=np.int32)
     n_sys = n_pl.size
     out = np.empty(n_sys)
+    grad = grad or gabs
     g = np.empty_like(params) if grad else None
+    ga = np.empty_like(params) if gabs else None
     rc = _load().kco_chi2_ragged(
         _p(params), _p(par_off, ctypes.c_int64), _p(n_pl, ctypes.c_int32),
         _p(t), _p(v), _p(sigma), _p(obs_off, ctypes.c_int64), n_sys,
-        float(t0), float(jitter), _p(out), _p(g) if grad else None)
+        float(t0), float(jitter), _p(out), _p(g) if grad else None,
+        _p(ga) if gabs else None)
     if rc != 0:
         raise ValueError("oracle.chi2_ragged: bad sizes")
+    if gabs:
+        return out, g, ga
     return (out, g) if grad else out
 
 

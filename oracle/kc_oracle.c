@@ -181,10 +181,12 @@ static double kco_planet_velocity_grad(const double *p, double t, double t0,
 /* ------------------------------------------------------- one system, Eq.5 */
 
 /* chi-square of one system (and, when grad != NULL, its gradient with
- * respect to the 5*n_pl + 1 parameters). */
+ * respect to the 5*n_pl + 1 parameters; when gabs != NULL also the sum over
+ * observations of the absolute value of each observation's term of the
+ * gradient, the scale of the cancellation in each gradient sum). */
 static double kco_system(const double *par, int n_pl, const double *t,
                          const double *v, const double *sigma, int64_t n_obs,
-                         double t0, double jitter, double *grad)
+                         double t0, double jitter, double *grad, double *gabs)
 {
     int n_par = 5 * n_pl + 1;
     double gamma = par[5 * n_pl];
@@ -195,8 +197,10 @@ static double kco_system(const double *par, int n_pl, const double *t,
     int valid = isfinite(gamma);
     for (j = 0; j < n_pl; ++j) valid = valid && kco_planet_valid(par + 5 * j);
     for (q = 0; q < n_par; ++q) { gsum[q].s = 0.0; gsum[q].c = 0.0; }
+    if (gabs) for (q = 0; q < n_par; ++q) gabs[q] = 0.0;
     if (!valid) {
         if (grad) for (q = 0; q < n_par; ++q) grad[q] = NAN;
+        if (gabs) for (q = 0; q < n_par; ++q) gabs[q] = NAN;
         return NAN;
     }
     for (k = 0; k < n_obs; ++k) {
@@ -219,6 +223,11 @@ static double kco_system(const double *par, int n_pl, const double *t,
             for (j = 0; j < n_pl; ++j)
                 for (q = 0; q < 5; ++q) kco_sum_add(&gsum[5 * j + q], a * g[j][q]);
             kco_sum_add(&gsum[5 * n_pl], a);                 /* dchi2/dgamma */
+            if (gabs) {
+                for (j = 0; j < n_pl; ++j)
+                    for (q = 0; q < 5; ++q) gabs[5 * j + q] += fabs(a * g[j][q]);
+                gabs[5 * n_pl] += fabs(a);
+            }
         }
     }
     if (grad) for (q = 0; q < n_par; ++q) grad[q] = kco_sum_value(&gsum[q]);
@@ -235,7 +244,7 @@ static double kco_system(const double *par, int n_pl, const double *t,
  * parameters; d nll / d sigma_j = sigma_j sum_k w_k (1 - w_k r_k^2). */
 static double kco_nll_system(const double *par, int n_pl, const double *t,
                              const double *v, const double *sigma, int64_t n_obs,
-                             double t0, double *grad)
+                             double t0, double *grad, double *gabs)
 {
     int n_par = 5 * n_pl + 2;
     double gamma = par[5 * n_pl], sj = par[5 * n_pl + 1];
@@ -246,8 +255,10 @@ static double kco_nll_system(const double *par, int n_pl, const double *t,
     int valid = isfinite(gamma) && isfinite(sj);
     for (j = 0; j < n_pl; ++j) valid = valid && kco_planet_valid(par + 5 * j);
     for (q = 0; q < n_par; ++q) { gsum[q].s = 0.0; gsum[q].c = 0.0; }
+    if (gabs) for (q = 0; q < n_par; ++q) gabs[q] = 0.0;
     if (!valid) {
         if (grad) for (q = 0; q < n_par; ++q) grad[q] = NAN;
+        if (gabs) for (q = 0; q < n_par; ++q) gabs[q] = NAN;
         return NAN;
     }
     for (k = 0; k < n_obs; ++k) {
@@ -271,6 +282,12 @@ static double kco_nll_system(const double *par, int n_pl, const double *t,
                 for (q = 0; q < 5; ++q) kco_sum_add(&gsum[5 * j + q], a * g[j][q]);
             kco_sum_add(&gsum[5 * n_pl], a);
             kco_sum_add(&gsum[5 * n_pl + 1], sj * wk * (1.0 - wk * r * r));
+            if (gabs) {
+                for (j = 0; j < n_pl; ++j)
+                    for (q = 0; q < 5; ++q) gabs[5 * j + q] += fabs(a * g[j][q]);
+                gabs[5 * n_pl] += fabs(a);
+                gabs[5 * n_pl + 1] += fabs(sj * wk * (1.0 - wk * r * r));
+            }
         }
     }
     if (grad) for (q = 0; q < n_par; ++q) grad[q] = kco_sum_value(&gsum[q]);
@@ -281,10 +298,11 @@ static double kco_nll_system(const double *par, int n_pl, const double *t,
 
 /* Uniform batch: all n_sys systems have n_pl planets and share the n_obs
  * observations (t, v, sigma).  params is [n_sys][5*n_pl+1], out is [n_sys],
- * grad (may be NULL) is [n_sys][5*n_pl+1].  Returns 0, or -1 on bad sizes. */
+ * grad and gabs (may be NULL; gabs needs grad) are [n_sys][5*n_pl+1].
+ * Returns 0, or -1 on bad sizes. */
 int kco_chi2(const double *params, const double *t, const double *v,
              const double *sigma, int64_t n_sys, int n_pl, int64_t n_obs,
-             double t0, double jitter, double *out, double *grad)
+             double t0, double jitter, double *out, double *grad, double *gabs)
 {
     int64_t s;
     int n_par = 5 * n_pl + 1;
@@ -292,15 +310,17 @@ int kco_chi2(const double *params, const double *t, const double *v,
 #pragma omp parallel for schedule(dynamic, 16)
     for (s = 0; s < n_sys; ++s)
         out[s] = kco_system(params + s * n_par, n_pl, t, v, sigma, n_obs, t0,
-                            jitter, grad ? grad + s * n_par : NULL);
+                            jitter, grad ? grad + s * n_par : NULL,
+                            grad && gabs ? gabs + s * n_par : NULL);
     return 0;
 }
 
 /* Uniform batch with a free jitter per system: params [n_sys][5*n_pl+2],
- * out [n_sys] negative log-likelihoods, grad (may be NULL) like params. */
+ * out [n_sys] negative log-likelihoods, grad and gabs (may be NULL) like
+ * params. */
 int kco_nll(const double *params, const double *t, const double *v,
             const double *sigma, int64_t n_sys, int n_pl, int64_t n_obs,
-            double t0, double *out, double *grad)
+            double t0, double *out, double *grad, double *gabs)
 {
     int64_t s;
     int n_par = 5 * n_pl + 2;
@@ -308,18 +328,19 @@ int kco_nll(const double *params, const double *t, const double *v,
 #pragma omp parallel for schedule(dynamic, 16)
     for (s = 0; s < n_sys; ++s)
         out[s] = kco_nll_system(params + s * n_par, n_pl, t, v, sigma, n_obs, t0,
-                                grad ? grad + s * n_par : NULL);
+                                grad ? grad + s * n_par : NULL,
+                                grad && gabs ? gabs + s * n_par : NULL);
     return 0;
 }
 
 /* Ragged batch: system s has n_pl[s] planets whose parameters start at
  * params[par_off[s]] (5*n_pl[s]+1 doubles) and its own observations
- * t/v/sigma[obs_off[s] .. obs_off[s+1]).  grad (may be NULL) uses the same
- * offsets as params. */
+ * t/v/sigma[obs_off[s] .. obs_off[s+1]).  grad and gabs (may be NULL) use
+ * the same offsets as params. */
 int kco_chi2_ragged(const double *params, const int64_t *par_off,
                     const int32_t *n_pl, const double *t, const double *v,
                     const double *sigma, const int64_t *obs_off, int64_t n_sys,
-                    double t0, double jitter, double *out, double *grad)
+                    double t0, double jitter, double *out, double *grad, double *gabs)
 {
     int64_t s;
     int bad = 0;
@@ -331,7 +352,8 @@ int kco_chi2_ragged(const double *params, const int64_t *par_off,
         out[s] = kco_system(params + par_off[s], n_pl[s], t + obs_off[s],
                             v + obs_off[s], sigma + obs_off[s],
                             obs_off[s + 1] - obs_off[s], t0, jitter,
-                            grad ? grad + par_off[s] : NULL);
+                            grad ? grad + par_off[s] : NULL,
+                            grad && gabs ? gabs + par_off[s] : NULL);
     return 0;
 }
 
@@ -415,7 +437,7 @@ int kco_demcmc_step(double *states, double *chi2, int64_t n_chains, int n_pl,
         }
     }
     if (kco_chi2(proposals, t, v, sigma, count, n_pl, n_obs, t0, jitter, chi2_prop,
-                 NULL) != 0)
+                 NULL, NULL) != 0)
         return -1;
     for (c = 0; c < count; ++c) {
         int64_t i = first + c;

@@ -22,21 +22,19 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr double kInvTwoPi = 0.15915494309189533576888376337251;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
-// Fixed Danby iteration counts (Sec. 4.3 caps the loop so the GPU is never
-// trapped; a fixed count also keeps warps branch-uniform).  From the paper's
-// starting guess E0 = M + 0.85 e sign(sin M) the worst error over
-// e <= kEccFast is 0.17 rad; after one quartic step 7e-4, after two 1e-13
-// (exact arithmetic).  The single-precision solve takes two steps on MUFU
-// sin/cos and a Newton step with accurate sin/cos; the double-precision one
-// polishes that solution with one Halley step in double.
-constexpr int kMufuStepsF32 = 2;
-
-// Largest eccentricity the fixed steps cover (the workloads draw e <= 0.95).
-// Above it Danby's start is far from the root near pericentre (0.06 rad
-// after two steps at e = 0.99, 0.04 after three at e = 0.999): the solvers'
-// HI = true variant branches on e > kEccFast into more steps, accurate up to
-// e ~ 0.9999.  Kernels pick HI once per warp (any_high_e), so that the usual
-// case keeps one straight-line body with no branch per planet.
+// Fixed step counts (Sec. 4.3 caps the loop so the GPU is never trapped; a
+// fixed count also keeps warps branch-uniform).  The single-precision solve
+// starts from Mikkola's cubic approximation, within 3.6e-3 rad of the root
+// for every e < 1, and takes one Halley step with accurate sin/cos (5.1e-9
+// in exact arithmetic, under the float rounding of E).  The double-precision
+// solve polishes that solution with one Halley step in double.
+//
+// Eccentricity up to which one double-precision step suffices (the
+// workloads draw e <= 0.95): above it the single-precision seed's error
+// grows like 1e-7 / (1 - e cos E) near pericentre and the double-precision
+// solve takes two steps.  Kernels choose once per warp (any_high_e), so
+// that the usual case keeps one straight-line body with no branch per
+// planet.
 constexpr float kEccFast = 0.95f;
 
 // ------------------------------------------------ conversions (integer pipe)
@@ -112,16 +110,21 @@ __device__ __forceinline__ float round_small(float x) {
   return __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic);
 }
 
-// MUFU approximations (absolute error ~2^-20.5 for sin/cos on the ranges
-// used here, ~1 ulp relative for rcp).
-__device__ __forceinline__ float sin_fast(float x) {
+// MUFU approximations (relative error ~2^-22 for the reciprocal, square
+// root reciprocal and base-2 exponential and logarithm).
+__device__ __forceinline__ float rsqrt_fast(float x) {
   float y;
-  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float cos_fast(float x) {
+__device__ __forceinline__ float lg2_fast(float x) {
   float y;
-  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -251,27 +254,17 @@ __device__ __forceinline__ float kahan_value(const Kahan &k) {
   return __fsub_rn(k.big, k.small);
 }
 
-// ------------------------------------------------ Danby step (Eqs. 7-10)
+// ------------------------------------------------ Kepler's equation (Sec. 4.3)
 
 // One quartic Danby step for f(E) = E - e sin E - M given s = sin E,
-// c = cos E.  The three nested divisions of Eqs. 8-10 fold into one:
-// with f' = 1 - e c, f'' = e s, f''' = e c, h = f f''/2, D2 = f'^2 - h,
+// c = cos E, in double (the second double-precision step above kEccFast).
+// The three nested divisions of Eqs. 8-10 fold into one: with
+// f' = 1 - e c, f'' = e s, f''' = e c, h = f f''/2, D2 = f'^2 - h,
 //   delta2 = -f f'/D2,
 //   delta3 = -f / (f' + delta2 f''/2 + delta2^2 f'''/6)
 //          = -f D2^2 / (f' [D2 (D2 - h) + f^2 f' f'''/6]),
 // algebraically identical to Danby's delta3 (Eq. 10 as printed mixes
 // delta1 and delta2).  Returns delta3.
-__device__ __forceinline__ float danby_delta_f32(float E, float M, float e, float s, float c) {
-  const float es = e * s;
-  const float f = (E - M) - es;
-  const float f1 = __fmaf_rn(-e, c, 1.0f);
-  const float h = 0.5f * f * es;
-  const float D2 = __fmaf_rn(f1, f1, -h);
-  const float f3_6 = (e * (1.0f / 6.0f)) * c;
-  const float Q = __fmaf_rn(f * f * f1, f3_6, D2 * (D2 - h));
-  return -(f * D2 * D2) * rcp_fast(f1 * Q);
-}
-
 __device__ __forceinline__ double danby_delta_f64(double E, double M, double e, double s,
                                                   double c) {
   const double es = e * s;
@@ -283,64 +276,67 @@ __device__ __forceinline__ double danby_delta_f64(double E, double M, double e, 
   return -(f * D2 * D2) * rcp_f64(f1 * Q);
 }
 
-// Paper's starting guess (Sec. 4.3): E0 = M + 0.85 e sign(sin M); M is
-// reduced to [-pi, pi] so sign(sin M) = sign(M), with sign(0) = +1.
+// Starting value of Mikkola (1987, "A cubic approximation for Kepler's
+// equation"): with a = (1 - e)/(4 e + 1/2) and b = (M/2)/(4 e + 1/2), the
+// real root z = cbrt(b + sign(b) sqrt(b^2 + a^3)) gives s = z - a/z, which
+// is corrected by -0.078 s^5/(1 + e); then E0 = M + e (3 s - 4 s^3).  For M
+// in [-pi, pi] it lies within 3.6e-3 rad of the root for every 0 <= e < 1
+// (exact arithmetic, dense grid in (M, e) including |M| down to 1e-9),
+// where the paper's M + 0.85 e sign(sin M) is up to 0.84 rad off near
+// pericentre.  The cube root is exp2(log2|t|/3) on MUFU (|t| >= a^(3/2),
+// above 1e-12 for float e < 1); the accuracy of the approximations only
+// moves the start.
 __device__ __forceinline__ float kepler_start(float M, float e) {
-  return M + (M >= 0.0f ? 0.85f : -0.85f) * e;
+  const float r = rcp_fast(__fmaf_rn(4.0f, e, 0.5f));
+  const float a = (1.0f - e) * r;
+  const float b = M * (0.5f * r);
+  const float w = __fmaf_rn(b, b, a * a * a);
+  const float t = b + copysignf(w * rsqrt_fast(w), b);
+  const float z = copysignf(ex2_fast(lg2_fast(fabsf(t)) * (1.0f / 3.0f)), t);
+  float s = __fmaf_rn(-a, rcp_fast(z), z);
+  const float s2 = s * s;
+  s = __fmaf_rn(-0.078f * rcp_fast(1.0f + e), s2 * s2 * s, s);
+  return __fmaf_rn(e, s * __fmaf_rn(-4.0f, s * s, 3.0f), M);
 }
 
-// Newton's step -f/f' for f(E) = E - e sin E - M.  From an iterate within
-// 7e-4 of the root (two quartic steps, e <= kEccFast) its quadratic error
-// e sin E delta^2 / (2 f') stays below 1e-7 rad (9e-8 at worst in exact
-// arithmetic), under the single-precision rounding of E.
-__device__ __forceinline__ float newton_delta_f32(float E, float M, float e, float s, float c) {
-  const float f = __fmaf_rn(-e, s, E - M);
-  return -f * rcp_fast(__fmaf_rn(-e, c, 1.0f));
+// Halley's step -2 f f' / (2 f'^2 - f f'') for f(E) = E - e sin E - M,
+// given s = sin E, c = cos E.  From Mikkola's start its cubic convergence
+// lands within 5.1e-9 rad of the root for every e < 1 (exact arithmetic),
+// below the float rounding of E.
+__device__ __forceinline__ float halley_delta_f32(float E, float M, float e, float s, float c) {
+  const float es = e * s;
+  const float f = (E - M) - es;
+  const float f1 = __fmaf_rn(-e, c, 1.0f);
+  const float num = f * f1;
+  return -(num + num) * rcp_fast(__fmaf_rn(f1 + f1, f1, -(f * es)));
 }
 
-// Extra steps for e > kEccFast: two more MUFU quartic steps up to e = 0.99,
-// five above (exact-arithmetic error then below 3e-15 up to e = 0.99 and
-// 9e-8 up to e = 0.9999), leaving the iterate at the MUFU floor
-// (~4e-7 e / (1 - e cos E)), then one quartic step with accurate sin/cos.
-__device__ __noinline__ static float kepler_high_e_f32(float E, float M, float e) {
-  const int n = e > 0.99f ? 5 : 2;
-  for (int it = 0; it < n; ++it) E += danby_delta_f32(E, M, e, sin_fast(E), cos_fast(E));
-  float s, c;
-  sincos_accurate(E, s, c);
-  return E + danby_delta_f32(E, M, e, s, c);
-}
-
-// Kepler's equation in single precision: two Danby steps from the paper's
-// start on MUFU sin/cos, whose error (~1e-6) only perturbs the iterate, then
-// one Newton step with sin/cos to an ulp.  sin/cos of the returned E come
-// from that evaluation by the angle-addition expansion to second order in
-// the last step (|delta| < 1e-3, truncation < 2e-10).  HI = false: valid
-// for e <= kEccFast only, no branch.
-template <bool HI = true>
+// Kepler's equation in single precision: Mikkola's start, sin/cos to an ulp
+// there (Cody-Waite + Taylor, FMA pipe) and one Halley step.  sin/cos of
+// the returned E come from that evaluation by the angle-addition expansion
+// to second order in the step (|delta| < 3.6e-3, truncation < 8e-9).  No
+// branch on e: the same straight-line code for every eccentricity.
 __device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &cE) {
-  float E = kepler_start(M, e);
-#pragma unroll
-  for (int it = 0; it < kMufuStepsF32; ++it) {
-    E += danby_delta_f32(E, M, e, sin_fast(E), cos_fast(E));
-  }
-  if (HI && e > kEccFast) E = kepler_high_e_f32(E, M, e);
+  const float E = kepler_start(M, e);
   float s, c;
   sincos_accurate(E, s, c);
-  const float d = newton_delta_f32(E, M, e, s, c);
+  const float d = halley_delta_f32(E, M, e, s, c);
   const float hd2 = 0.5f * d * d;
   sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
   cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
   return E + d;
 }
 
-// Warp-uniform choice of the solvers' HI variant: true if any lane holds an
-// eccentricity above kEccFast.  All lanes of `mask` must call it.
+// Warp-uniform choice of the double-precision solver's HI variant: true if
+// any lane holds an eccentricity above kEccFast.  All lanes of `mask` must
+// call it.
 __device__ __forceinline__ bool any_high_e(bool mine, unsigned mask = 0xffffffffu) {
   return __any_sync(mask, mine) != 0;
 }
 
-// Calls body(HiTag<true>) or body(HiTag<false>): the observation loops are
-// compiled twice, once without the high-eccentricity branch.
+// Calls body(HiTag<true>) or body(HiTag<false>): the observation loops of
+// the double-precision kernels are compiled twice, once without the
+// high-eccentricity branch.
 template <bool B>
 struct HiTag {
   static constexpr bool value = B;
@@ -405,11 +401,10 @@ __device__ __forceinline__ double halley_delta_f64(double E, double M, double e,
 }
 
 // Kepler's equation in double precision.  The single-precision solve
-// (kepler_f32, the same variant HI) seeds one double-precision Halley step,
-// which lands on the double root; sin/cos of the result follow by angle
-// addition to second order in that last step.  HI and e > kEccFast: two
-// quartic steps in double instead (the seed's error grows like
-// 1e-7 / (1 - e cos E)).  The single-precision work costs little here: one
+// (kepler_f32) seeds one double-precision Halley step, which lands on the
+// double root; sin/cos of the result follow by angle addition to second
+// order in that last step.  HI and e > kEccFast: two quartic steps in
+// double instead (the seed's error grows like 1e-7 / (1 - e cos E)).  The single-precision work costs little here: one
 // FP64 instruction takes as long on GB300's FP64 pipe as ~76 FP32 issues.
 // With a table (tab != nullptr, sincos_table_build), sin/cos come from
 // sincos_tab.
@@ -418,7 +413,7 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
                                              const double2 *tab = nullptr) {
   const float Mf = d2f(M), ef = d2f(e);
   float sf, cf;
-  const float Ef = kepler_f32<HI>(Mf, ef, sf, cf);
+  const float Ef = kepler_f32(Mf, ef, sf, cf);
   const bool high = HI && ef > kEccFast;
   double E = f2d(Ef);
   double s, c;

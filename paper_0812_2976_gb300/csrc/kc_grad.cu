@@ -83,12 +83,6 @@ __device__ inline double system_jitter_g(const double *p, int J) {
   return finite_bits(sj) ? sj : nan_d();
 }
 
-__device__ __forceinline__ float lg2_fast_g(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 constexpr double kLn2PiG = 1.8378770664093454836;      // ln(2 pi)
 
 __device__ inline double inv_variance_g(double sigma, double jitter2) {
@@ -214,53 +208,47 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     const float gam = gam_s[sl];
     const float sj = NLL ? sj_s[sl] : 0.0f;
     const GradPlanetF *q = pl_s + sl * J;
-    bool hi = false;
-    #pragma unroll
-    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > kEccFast;
-    with_high_e(any_high_e(hi), [&](auto tag) {
-      constexpr bool HI = decltype(tag)::value;
-      for (int k = c; k < nk; k += G) {
-        const float4 o = obs_s[k];
-        const float2 wt = wt_s[k];
-        float sEj[J], cEj[J];
-        Kahan V = {0.0f, 0.0f};
+    for (int k = c; k < nk; k += G) {
+      const float4 o = obs_s[k];
+      const float2 wt = wt_s[k];
+      float sEj[J], cEj[J];
+      Kahan V = {0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const PlanetF p = q[j].base;
-          const float M = mean_anomaly_mixed(o.x, o.y, p);
-          kepler_f32<HI>(M, p.e, sEj[j], cEj[j]);
-          kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
-        }
-        const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
-        float wk = wt.x, a2;
-        if (NLL) {
-          const float var = __fmaf_rn(sj, sj, wt.x);           // sigma_k^2 + sigma_j^2
-          wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
-          const float wr = wk * r;
-          kahan_add(acc, __fmaf_rn(wr, r, lg2_fast_g(var) * 0.693147180559945309f));
-          a2 = wr;
-          g[NP - 1] = __fmaf_rn(sj * wk, __fmaf_rn(-wr, r, 1.0f), g[NP - 1]);
-        } else {
-          const float wr = wk * r;
-          kahan_add(acc, wr * r);
-          a2 = 2.0f * wr;
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const GradPlanetF qj = q[j];
-          Partials<float> d;
-          const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
-          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
-          d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
-          kahan_add(gP[j], a2 * d.dP);
-          g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
-          g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
-          g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
-          g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
-        }
-        g[5 * J] += a2;
+      for (int j = 0; j < J; ++j) {
+        const PlanetF p = q[j].base;
+        const float M = mean_anomaly_mixed(o.x, o.y, p);
+        kepler_f32(M, p.e, sEj[j], cEj[j]);
+        kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
       }
-    });
+      const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+      float wk = wt.x, a2;
+      if (NLL) {
+        const float var = __fmaf_rn(sj, sj, wt.x);           // sigma_k^2 + sigma_j^2
+        wk = var > 0.0f ? rcp_fast(var) : __int_as_float(0x7fc00000);
+        const float wr = wk * r;
+        kahan_add(acc, __fmaf_rn(wr, r, lg2_fast(var) * 0.693147180559945309f));
+        a2 = wr;
+        g[NP - 1] = __fmaf_rn(sj * wk, __fmaf_rn(-wr, r, 1.0f), g[NP - 1]);
+      } else {
+        const float wr = wk * r;
+        kahan_add(acc, wr * r);
+        a2 = 2.0f * wr;
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const GradPlanetF qj = q[j];
+        Partials<float> d;
+        const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
+        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+        d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
+        kahan_add(gP[j], a2 * d.dP);
+        g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
+        g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
+        g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
+        g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+      }
+      g[5 * J] += a2;
+    }
   }
 
   for (int m = G >> 1; m >= 1; m >>= 1) {
@@ -347,7 +335,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
     const double gam = gam_s[sl];
     const GradPlanetD *q = pl_s + sl * J;
     bool hi = false;
-    #pragma unroll
+#pragma unroll
     for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > (double)kEccFast;
     with_high_e(any_high_e(hi), [&](auto tag) {
       constexpr bool HI = decltype(tag)::value;
@@ -556,9 +544,6 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
     __syncthreads();
     const float gam = gam_s[warp];
     const GradPlanetF *q = pl_s + warp * J;
-    bool hi = false;                        // uniform: the warp holds one system
-#pragma unroll
-    for (int j = 0; j < J; ++j) hi = hi || q[j].base.e > kEccFast;
     for (int kb = 0; kb < nk; kb += 32) {
       const int k = kb + lane;
       float urow[NP];
@@ -569,16 +554,13 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         const float2 wt = wt_s[k];
         float sEj[J], cEj[J];
         Kahan V = {0.0f, 0.0f};
-        with_high_e(hi, [&](auto tag) {
-          constexpr bool HI = decltype(tag)::value;
 #pragma unroll
-          for (int j = 0; j < J; ++j) {
-            const PlanetF p = q[j].base;
-            const float M = mean_anomaly_mixed(o.x, o.y, p);
-            kepler_f32<HI>(M, p.e, sEj[j], cEj[j]);
-            kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
-          }
-        });
+        for (int j = 0; j < J; ++j) {
+          const PlanetF p = q[j].base;
+          const float M = mean_anomaly_mixed(o.x, o.y, p);
+          kepler_f32(M, p.e, sEj[j], cEj[j]);
+          kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+        }
         const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
         const float wk = wt.x, wr = wk * r, a2 = 2.0f * wr;
         kahan_add(acc, wr * r);

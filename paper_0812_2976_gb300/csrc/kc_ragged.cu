@@ -176,7 +176,7 @@ __device__ __forceinline__ void partials_r(T e, T K, T cw, T sw, T beta, T sE, T
   de = K * cw - ks * sE * (T(1) / beta + beta * invD);
 }
 
-template <int J, bool GRAD, bool HI>
+template <int J, bool GRAD>
 __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const float4 *oa,
                                            const float2 *ob, int64_t o0, int n, int lane,
                                            float *chi2_out, float *grad_out) {
@@ -208,7 +208,7 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
     for (int j = 0; j < J; ++j) {
       const PlanetF q = pl[j].base;
       const float M = mean_anomaly_mixed(o.x, o.y, q);
-      kepler_f32<HI>(M, q.e, sEj[j], cEj[j]);
+      kepler_f32(M, q.e, sEj[j], cEj[j]);
       kahan_add(V, velocity_mixed(q, sEj[j], cEj[j]));
     }
     const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
@@ -366,13 +366,8 @@ ragged_mixed_kernel(RaggedDev d, const float4 *__restrict__ oa, const float2 *__
     if (lane < J) pl[lane] = rsetup_mixed(p + 5 * lane, d.t_ref[s], d.t0, GRAD);
     const float gam = d2f(system_gamma_r(p, J));
     __syncwarp();
-    const bool hi = any_high_e(lane < J && pl[lane].base.e > kEccFast);
     float *gout = GRAD ? grad + d.par_off[s] : nullptr;
-#define KC_BODY(JJ)                                                                  \
-  if (hi)                                                                            \
-    body_mixed<JJ, GRAD, true>(pl, gam, oa, ob, o0, n, lane, chi2 + s, gout);        \
-  else                                                                               \
-    body_mixed<JJ, GRAD, false>(pl, gam, oa, ob, o0, n, lane, chi2 + s, gout)
+#define KC_BODY(JJ) body_mixed<JJ, GRAD>(pl, gam, oa, ob, o0, n, lane, chi2 + s, gout)
     KC_RAGGED_SWITCH(KC_BODY)
 #undef KC_BODY
     if (lane == 0) note_invalid(d.invalid, chi2[s]);      // lane 0 wrote it

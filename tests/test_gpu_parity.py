@@ -3,12 +3,15 @@
 Tolerances (relative error |d chi2| / max(chi2_oracle, 1)):
   FP64 path   <= 1e-12
   mixed path  <= 1e-5, Kepler residual <= 4e-6 rad
-  gradient    mixed <= 1e-3 per component, FP64 <= 1e-9, each normalised by
-              max(|g|, 1e-3 ||g||) of the oracle's gradient of that system.
+  gradient    mixed 1e-3 per component, FP64 1e-9, each normalised by
+              max(|g|, 1e-3 ||g||) of the oracle's gradient of that system,
+              plus 16 u sum_k |term_k| for the sum's cancellation
+              (tests/tolerance.py).
 """
 import numpy as np
 import pytest
 import torch
+from tolerance import U32, U64, grad_excess
 
 pytestmark = pytest.mark.gpu
 
@@ -38,9 +41,10 @@ def rel_err(got, ref):
     return np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
 
 
-def grad_err(got, ref):
-    scale = np.maximum(np.abs(ref), 1e-3 * np.linalg.norm(ref, axis=1, keepdims=True))
-    return np.abs(np.asarray(got, dtype=np.float64) - ref) / scale
+def grad_err(got, ref, gabs, mode="mixed"):
+    """Largest error of a gradient component over its bound (<= 1 passes)."""
+    rel, u = (GRAD_MIXED_TOL, U32) if mode == "mixed" else (GRAD_F64_TOL, U64)
+    return grad_excess(got, ref, gabs, rel, u)
 
 
 def observed(oracle, w):
@@ -150,14 +154,15 @@ def test_config3_gradient_full_size_sampled(kc, oracle_mod):
     grad = grad.cpu().numpy()
     idx = np.unique(np.concatenate([np.random.default_rng(1).choice(w.n_sys, 3000, replace=False),
                                     [0, w.n_sys - 1]]))
-    ref, gref = oracle_mod.chi2(w.params[idx], w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
+    ref, gref, gabs = oracle_mod.chi2(w.params[idx], w.t, v, w.sigma, w.n_pl, t0=w.t0,
+                                      gabs=True)
     assert rel_err(chi[idx], ref).max() <= MIXED_TOL
-    ge = grad_err(grad[idx], gref)
-    assert ge.max() <= GRAD_MIXED_TOL, ge.max()
+    ge = grad_err(grad[idx], gref, gabs)
+    assert ge <= 1.0, ge
     # FP64 adjoint on the sampled systems
     c64, g64 = kc.kc_chi2_grad(dev(w.params[idx])[0], T, V, S, t0=w.t0, mode="fp64")
     assert rel_err(c64.cpu().numpy(), ref).max() <= FP64_TOL
-    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+    assert grad_err(g64.cpu().numpy(), gref, gabs, "fp64") <= 1.0
 
 
 def test_autograd_function_matches_adjoint(kc, oracle_mod):
@@ -168,9 +173,9 @@ def test_autograd_function_matches_adjoint(kc, oracle_mod):
     weights = torch.linspace(0.5, 2.0, 64, device="cuda", dtype=torch.float64)
     Pg = P.clone().requires_grad_(True)
     (kc.chi2(Pg, T, V, S, t0=w.t0, mode="fp64") * weights).sum().backward()
-    _, gref = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl, t0=w.t0, grad=True)
-    gref = gref * weights.cpu().numpy()[:, None]
-    assert grad_err(Pg.grad.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+    _, gref, gabs = oracle_mod.chi2(w.params, w.t, v, w.sigma, w.n_pl, t0=w.t0, gabs=True)
+    wts = weights.cpu().numpy()[:, None]
+    assert grad_err(Pg.grad.cpu().numpy(), gref * wts, gabs * wts, "fp64") <= 1.0
 
 
 # ------------------------------------------------------------ shapes, edges
@@ -189,16 +194,17 @@ def test_planet_counts_ragged_tail_many_tiles(kc, oracle_mod, n_pl):
                  rng.uniform(0, 2 * np.pi, n_sys)]
     params = np.stack(cols + [rng.uniform(-10, 10, n_sys)], axis=1)
     v = rng.normal(0, 40, n_obs)
-    ref, gref = oracle_mod.chi2(params, t, v, sig, n_pl, t0=2450000.0, jitter=1.5, grad=True)
+    ref, gref, gabs = oracle_mod.chi2(params, t, v, sig, n_pl, t0=2450000.0, jitter=1.5,
+                                      gabs=True)
     P, T, V, S = dev(params, t, v, sig)
     c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, jitter=1.5, mode="fp64").cpu().numpy()
     assert rel_err(c64, ref).max() <= FP64_TOL
     c32 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, jitter=1.5, mode="mixed").cpu().numpy()
     assert rel_err(c32, ref).max() <= MIXED_TOL
     _, g32 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, jitter=1.5, mode="mixed")
-    assert grad_err(g32.cpu().numpy(), gref).max() <= GRAD_MIXED_TOL
+    assert grad_err(g32.cpu().numpy(), gref, gabs) <= 1.0
     _, g64 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, jitter=1.5, mode="fp64")
-    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+    assert grad_err(g64.cpu().numpy(), gref, gabs, "fp64") <= 1.0
 
 
 def test_many_observations_span_several_smem_tiles(kc, oracle_mod):
@@ -328,10 +334,11 @@ def test_kepler_solve_alignment_and_tails(kc, oracle_mod, offset, n):
 
 
 def test_kepler_solve_high_eccentricity(kc, oracle_mod):
-    """0.95 < e <= 0.999, where the fixed steps alone do not converge from
-    Danby's start near pericentre: the solvers' extra steps (taken when any
-    lane of a warp holds such an e) reach the root in both precisions; M
-    also log-spaced towards 0, where convergence is slowest."""
+    """0.95 < e <= 0.999, where Danby's start (the paper's) is far from the
+    root near pericentre: Mikkola's start and one Halley step reach it in
+    single precision, and the FP64 solver's second step (taken when any lane
+    of a warp holds such an e) in double; M also log-spaced towards 0, where
+    convergence is slowest."""
     Mg = np.concatenate([np.linspace(-np.pi, np.pi, 301), np.logspace(-7, 0, 100),
                          -np.logspace(-7, 0, 100)])
     e = np.repeat(np.linspace(0.95, 0.999, 64), Mg.size)
@@ -362,12 +369,12 @@ def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
     sig = rng.uniform(1, 4, n_obs)
     truth = par[0].copy()
     v = oracle_mod.predict(truth[None], t, n_pl, 2450000.0)[0] + sig * rng.standard_normal(n_obs)
-    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, grad=True)
+    ref, gref, gabs = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, gabs=True)
     P, T, V, S = dev(par, t, v, sig)
     c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="fp64").cpu().numpy()
     assert rel_err(c64, ref).max() <= FP64_TOL
     _, g64 = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, mode="fp64")
-    assert grad_err(g64.cpu().numpy(), gref).max() <= GRAD_F64_TOL
+    assert grad_err(g64.cpu().numpy(), gref, gabs, "fp64") <= 1.0
     c32, resid = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="mixed", max_kepler_resid=True)
     assert float(resid.max()) <= RESID_TOL
     model = oracle_mod.predict(par, t, n_pl, 2450000.0)
@@ -380,9 +387,11 @@ def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
 @pytest.mark.parametrize("tile", [(4, 128, 0), (8, 64, 1), (32, 128, 0), (64, 128, 2)])
 def test_high_eccentricity_mixed_warps(kc, oracle_mod, tile):
     """Every third system has a planet at e = 0.985, the others e <= 0.9:
-    with 4 or 8 threads per system a warp holds several systems, and the
-    warp's vote sends all of them through the solver's extra steps; results
-    must not depend on the neighbours (every system against the oracle)."""
+    with 4 or 8 threads per system a warp holds several systems of both
+    kinds (the single-precision solver has one straight-line body for every
+    e; in the FP64 kernel the warp's vote sends all of them through the
+    second double-precision step); results must not depend on the
+    neighbours (every system against the oracle)."""
     rng = np.random.default_rng(62)
     n_sys, n_pl, n_obs = 300, 3, 160
     par = synth_rows(rng, n_sys, n_pl)
@@ -453,14 +462,14 @@ def test_short_periods_far_from_the_epoch(kc, oracle_mod):
     t = np.sort(rng.uniform(2450000, 2450300, n_obs))
     v = oracle_mod.predict(par[0], t, n_pl)[0] + rng.normal(0, 2, n_obs)
     sig = rng.uniform(1, 3, n_obs)
-    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, grad=True)
+    ref, gref, gabs = oracle_mod.chi2(par, t, v, sig, n_pl, gabs=True)
     P, T, V, S = dev(par, t, v, sig)
     c32, r = kc.kc_chi2_eval_ex(P, T, V, S, mode="mixed", max_kepler_resid=True)
     assert rel_err(c32.cpu().numpy(), ref).max() <= MIXED_TOL
     assert float(r.max()) <= RESID_TOL
     assert rel_err(kc.kc_chi2_eval(P, T, V, S).cpu().numpy(), ref).max() <= FP64_TOL
     _, g32 = kc.kc_chi2_grad(P, T, V, S, mode="mixed")
-    assert grad_err(g32.cpu().numpy(), gref).max() <= GRAD_MIXED_TOL
+    assert grad_err(g32.cpu().numpy(), gref, gabs) <= 1.0
 
 
 def test_circular_and_eccentric_extremes(kc, oracle_mod):
@@ -474,13 +483,13 @@ def test_circular_and_eccentric_extremes(kc, oracle_mod):
     t = np.sort(rng.uniform(2450000, 2453000, n_obs))
     v = rng.normal(0, 20, n_obs)
     sig = rng.uniform(1, 4, n_obs)
-    ref, gref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, grad=True)
+    ref, gref, gabs = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, gabs=True)
     P, T, V, S = dev(par, t, v, sig)
     c32, r = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="mixed", max_kepler_resid=True)
     assert rel_err(c32.cpu().numpy(), ref).max() <= MIXED_TOL
     assert float(r.max()) <= RESID_TOL
     c64 = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, mode="fp64").cpu().numpy()
     assert rel_err(c64, ref).max() <= FP64_TOL
-    for mode, tol in (("mixed", GRAD_MIXED_TOL), ("fp64", GRAD_F64_TOL)):
+    for mode in ("mixed", "fp64"):
         _, g = kc.kc_chi2_grad(P, T, V, S, t0=2450000.0, mode=mode)
-        assert grad_err(g.cpu().numpy(), gref).max() <= tol
+        assert grad_err(g.cpu().numpy(), gref, gabs, mode) <= 1.0

@@ -617,3 +617,46 @@ def test_velocity_equals_the_eccentric_anomaly_form(oracle_mod):
         v_E = (K * np.cos(w) * (np.cos(E) - e)
                - K * np.sqrt((1 - e) * (1 + e)) * np.sin(w) * np.sin(E)) / D + K * e * np.cos(w)
         assert np.max(np.abs(v_E - v)) <= 1e-13 * K / (1 - e)
+
+
+# ------------------------------------------------------------ gradient magnitudes
+
+def test_gabs_bounds_and_additivity(oracle_mod):
+    """gabs = sum_k |term_k of the gradient| (the cancellation scale used by
+    the gradient parity bound): at least |g| componentwise, equal to |g| for
+    one observation, and additive over disjoint sets of observations; the
+    same for the free-jitter likelihood and a ragged batch."""
+    rng = np.random.default_rng(91)
+    n_pl, n_obs = 2, 60
+    par = np.array([[40.0, 30.0, 0.4, 1.0, 2.0, 300.0, 12.0, 0.1, 4.0, 0.5, 3.0],
+                    [7.0, 60.0, 0.7, 5.0, 1.0, 1500.0, 5.0, 0.2, 2.0, 6.0, -2.0]])
+    t = np.sort(rng.uniform(2450000.0, 2452000.0, n_obs))
+    v = rng.normal(0.0, 30.0, n_obs)
+    sig = rng.uniform(1.0, 4.0, n_obs)
+    c, g, ga = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, jitter=0.5, gabs=True)
+    assert np.all(ga >= np.abs(g) * (1 - 1e-14))
+    assert np.any(ga > 10 * np.abs(g))                      # cancellation is present
+    _, g1, ga1 = oracle_mod.chi2(par, t[7:8], v[7:8], sig[7:8], n_pl, t0=2450000.0,
+                                 jitter=0.5, gabs=True)
+    np.testing.assert_allclose(ga1, np.abs(g1), rtol=1e-15)
+    _, _, gaA = oracle_mod.chi2(par, t[:25], v[:25], sig[:25], n_pl, t0=2450000.0,
+                                jitter=0.5, gabs=True)
+    _, _, gaB = oracle_mod.chi2(par, t[25:], v[25:], sig[25:], n_pl, t0=2450000.0,
+                                jitter=0.5, gabs=True)
+    np.testing.assert_allclose(gaA + gaB, ga, rtol=1e-13)
+    pj = np.concatenate([par, [[0.8], [2.5]]], axis=1)
+    _, gn, gan = oracle_mod.nll(pj, t, v, sig, n_pl, t0=2450000.0, gabs=True)
+    assert np.all(gan >= np.abs(gn) * (1 - 1e-14))
+    _, gn1, gan1 = oracle_mod.nll(pj, t[3:4], v[3:4], sig[3:4], n_pl, t0=2450000.0, gabs=True)
+    np.testing.assert_allclose(gan1, np.abs(gn1), rtol=1e-15)
+    # ragged: the two systems on their own halves of the observations
+    par_off = np.array([0, 11, 22])
+    obs_off = np.array([0, 30, 60])
+    cr, gr, gar = oracle_mod.chi2_ragged(par.ravel(), par_off, np.array([2, 2], np.int32),
+                                         t, v, sig, obs_off, t0=2450000.0, jitter=0.5,
+                                         gabs=True)
+    for s in range(2):
+        o = slice(obs_off[s], obs_off[s + 1])
+        _, _, gu = oracle_mod.chi2(par[s:s + 1], t[o], v[o], sig[o], n_pl, t0=2450000.0,
+                                   jitter=0.5, gabs=True)
+        np.testing.assert_allclose(gar[par_off[s]:par_off[s + 1]], gu[0], rtol=1e-13)
