@@ -583,16 +583,21 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
   const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
-  // powers of two, plus G = 12, 24, 48 with 96- and 192-thread blocks: with
-  // 96 registers a thread, 24 threads per system fit 4096 systems of 256
-  // observations into one wave of 152 SMs where 32 would need 1.3 waves
+  // powers of two, plus G = 12, 24, 48 with 96- and 192-thread blocks, and
+  // G = 8, 16, 32 with 160- and 224-thread blocks: the CTA count of a
+  // batch that fills about one wave then spreads more evenly over the 152
+  // SMs (4096 systems at 16 threads: 293 CTAs of 224 threads, two per SM on
+  // 141 SMs, where 256 CTAs of 256 threads leave 48 SMs with one)
   std::vector<kc_tile> cands;
   for (int split = 0; split <= 2; ++split) {
     for (int B : {32, 64, 128, 256})
       for (int G = 1; G <= (split == 2 ? 1024 : B); G <<= 1) cands.push_back(kc_tile{G, B, split});
-    if (split < 2)
+    if (split < 2) {
       for (int B : {96, 192})
         for (int G : {12, 24, 48}) cands.push_back(kc_tile{G, B, split});
+      for (int B : {160, 224})
+        for (int G : {8, 16, 32}) cands.push_back(kc_tile{G, B, split});
+    }
   }
   for (const kc_tile &cand : cands) {
     const int G = cand.threads_per_system, B = cand.block, split = cand.split;

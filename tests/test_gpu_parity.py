@@ -428,7 +428,7 @@ def test_rv_predict_vs_oracle(kc, oracle_mod):
 @pytest.mark.parametrize("tile", [(8, 64, 1), (32, 32, 1), (64, 256, 1), (1, 128, 1),
                                   (32, 128, 2), (128, 64, 2), (256, 256, 2), (1024, 32, 2),
                                   (24, 96, 0), (12, 192, 0), (48, 96, 0), (24, 192, 1),
-                                  (3, 96, 0)])
+                                  (3, 96, 0), (16, 224, 0), (32, 160, 0), (8, 224, 1)])
 def test_split_variant_matches_oracle(kc, oracle_mod, tile):
     """The two-pass (preparation + main) variant of the mixed kernel and the
     fused kernel with a thread count per system that is not a power of two
