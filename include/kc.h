@@ -8,9 +8,12 @@
  * Processing Units":
  *
  *   M_jk  = 2 pi frac((t_k - t0)/P_j) + M0_j              (Eqs. 4 and 6)
- *   E_jk  - e_j sin E_jk = M_jk                            (Eq. 1, solved by
- *                                                           Danby's quartic
- *                                                           iteration, Eqs. 7-10)
+ *   E_jk  - e_j sin E_jk = M_jk                            (Eq. 1; the paper
+ *                                                           iterates Danby's
+ *                                                           step, Eqs. 7-10;
+ *                                                           here a fixed-count
+ *                                                           solve to the same
+ *                                                           root, Sec. 4.3)
  *   v_jk  = K_j [cos(omega_j + f_jk) + e_j cos omega_j]    (Eq. 3)
  *   V_k   = gamma + sum_j v_jk                             (Eq. 2)
  *   chi2  = sum_k (V_k - v_k)^2 / (sigma_jit^2 + sigma_k^2) (Eq. 5)

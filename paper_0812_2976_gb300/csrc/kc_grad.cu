@@ -5,7 +5,7 @@
 // goodness-of-fit statistic in parallel for derivative-based searches.  This
 // kernel does it in the same pass as chi2, without storing anything per
 // observation: per (observation, planet) it solves Kepler's equation (the
-// same fixed-count Danby solver as the forward kernel), keeps sin E and cos E
+// same fixed-count solver as the forward kernel), keeps sin E and cos E
 // in registers until the residual r_k of the observation is known, then adds
 // 2 w_k r_k dv/dtheta to per-thread accumulators.  The derivatives follow
 // from implicit differentiation of Kepler's equation,
