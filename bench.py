@@ -222,7 +222,8 @@ def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):
     """DE-MC (two-half differential evolution) over the batch's 4096 model
     systems as a population: generations per second with graph replay."""
     import torch
-    mc = kc.DEMCMC(P, T, V, S, mode="mixed", eps_scale=1e-6, hop_every=0, seed=5)
+    mc = kc.DEMCMC(P, T, V, S, mode="mixed", eps_scale=1e-6, hop_every=0, seed=5,
+                   autotune=True)
     mc.run(3)                                        # includes the graph capture
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -488,10 +488,14 @@ class DEMCMC:
     x^2) per parameter (``eps_scale`` a number or one value per parameter; 0
     together with equal values in every chain holds a parameter fixed).
     Random draws come from a torch generator on the device; the step itself
-    is kc_demcmc_step."""
+    is kc_demcmc_step.  ``autotune``: time the chi2 tiles once for the size
+    class of half the population (what each step evaluates) and keep the
+    fastest; off by default, since the pick depends on timing and so can
+    change the summation order from one run to the next."""
 
     def __init__(self, states, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
-                 mode="mixed", eps_scale: float = 1e-6, hop_every: int = 10, seed: int = 0):
+                 mode="mixed", eps_scale: float = 1e-6, hop_every: int = 10, seed: int = 0,
+                 autotune: bool = False):
         self.states = _dev_f64("states", states, 2).clone()
         n = self.states.shape[0]
         if n < 8 or n % 2:
@@ -506,6 +510,9 @@ class DEMCMC:
         self.hop_every = int(hop_every)
         self.gen = torch.Generator(device=self.states.device)
         self.gen.manual_seed(seed)
+        if autotune:
+            kc_autotune(self.states[:self.half], self.t, self.v, self.sigma, kernel="chi2",
+                        mode=mode)
         self.chi2 = kc_chi2_eval_ex(self.states, self.t, self.v, self.sigma, self.t0,
                                     self.jitter, mode)
         dev = self.states.device
