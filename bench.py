@@ -507,18 +507,19 @@ def run_kc(args):
     value = evals * args.steps * world / t_sum
     ms_per_step = 1e3 * t_sum / args.steps
 
-    # end-to-end through the public API from pinned host buffers
-    hP = torch.tensor(w.params).pin_memory()
-    hT, hV, hS = T.cpu().pin_memory(), V.cpu().pin_memory(), S.cpu().pin_memory()
+    # end-to-end through the public API from pinned host memory: the step's
+    # inputs (parameters, times, velocities, uncertainties) packed in one
+    # pinned buffer and sent with one copy into one device buffer, whose
+    # views the library reads; chi2 comes back with one copy
+    n_par, n_obs = P.numel(), T.numel()
+    hbuf = torch.cat([torch.tensor(w.params).ravel(), T.cpu(), V.cpu(), S.cpu()]).pin_memory()
+    dbuf = torch.empty_like(hbuf, device=dev)
+    dP = dbuf[:n_par].view(P.shape)
+    dT, dV, dS = (dbuf[n_par + i * n_obs:n_par + (i + 1) * n_obs] for i in range(3))
     hout = torch.empty(w.n_sys, dtype=torch.float32).pin_memory()
-    dP, dT, dV, dS = (torch.empty_like(P), torch.empty_like(T), torch.empty_like(V),
-                      torch.empty_like(S))
 
     def e2e_step():
-        dP.copy_(hP, non_blocking=True)
-        dT.copy_(hT, non_blocking=True)
-        dV.copy_(hV, non_blocking=True)
-        dS.copy_(hS, non_blocking=True)
+        dbuf.copy_(hbuf, non_blocking=True)
         kc.kc_chi2_eval_mixed(dP, dT, dV, dS, out=out, stream=stream)
         hout.copy_(out, non_blocking=True)
 
@@ -535,7 +536,7 @@ def run_kc(args):
         e_ev[i][1].record(stream)
     torch.cuda.synchronize(dev)
     e2e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
-    h2d = hP.numel() * 8 + 3 * hT.numel() * 8
+    h2d = hbuf.numel() * 8
     d2h = hout.numel() * 4
     e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
@@ -705,18 +706,20 @@ def run_kc_ragged(args):
     extras = {}
     if not args.no_extras:
         extras = ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev)
-    # end to end: host parameters in, host chi2 + gradient out
+    # end to end: host parameters in, host chi2 + gradient out (the plan
+    # writes both into views of one device buffer, returned with one copy)
     hP = torch.tensor(w.params).pin_memory()
-    hchi = torch.empty_like(chi, device="cpu").pin_memory()
-    hgrad = torch.empty_like(grad, device="cpu").pin_memory() if want_grad else None
     dP = torch.empty_like(P)
+    n_out = chi.numel() + (grad.numel() if want_grad else 0)
+    dout = torch.empty(n_out, dtype=chi.dtype, device=dev)
+    echi = dout[:chi.numel()]
+    egrad = dout[chi.numel():] if want_grad else None
+    hout = torch.empty(n_out, dtype=chi.dtype).pin_memory()
 
     def e2e_step():
         dP.copy_(hP, non_blocking=True)
-        plan.run(dP, chi, grad)
-        hchi.copy_(chi, non_blocking=True)
-        if want_grad:
-            hgrad.copy_(grad, non_blocking=True)
+        plan.run(dP, echi, egrad)
+        hout.copy_(dout, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
@@ -736,7 +739,7 @@ def run_kc_ragged(args):
                    if shape else "default"},
         "e2e": {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
                 "h2d_bytes_per_step": hP.numel() * 8,
-                "d2h_bytes_per_step": (hchi.numel() + (hgrad.numel() if want_grad else 0)) * 4},
+                "d2h_bytes_per_step": hout.numel() * 4},
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
