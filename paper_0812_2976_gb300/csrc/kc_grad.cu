@@ -32,14 +32,15 @@ namespace {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Planet constants for the gradient, single precision.
+// ibeta = 1/beta, once per planet: the partials need it per observation.
 struct GradPlanetF {
   PlanetF base;    // phase and velocity constants of the forward path
-  float K, cw, sw, beta, n2;   // n2 = (1/P)^2
+  float K, cw, sw, beta, n2, ibeta;   // n2 = (1/P)^2
 };
 
 struct GradPlanetD {
   PlanetD base;
-  double K, cw, sw, n2;
+  double K, cw, sw, n2, ibeta;
 };
 
 __device__ inline GradPlanetF grad_setup_mixed(const double *p, double t_ref, double t0) {
@@ -54,6 +55,7 @@ __device__ inline GradPlanetF grad_setup_mixed(const double *p, double t_ref, do
   g.K = d2f(p[1]);
   const float e = g.base.e;
   g.beta = sqrtf((1.0f - e) * (1.0f + e));
+  g.ibeta = 1.0f / g.beta;
   const float n = g.base.n_hi;
   g.n2 = n * n;
   return g;
@@ -65,6 +67,7 @@ __device__ inline GradPlanetD grad_setup_f64(const double *p, double dref) {
   sincos(p[3], &g.sw, &g.cw);
   g.K = p[1];
   g.n2 = g.base.inv_P * g.base.inv_P;
+  g.ibeta = 1.0 / g.base.beta;
   return g;
 }
 
@@ -98,7 +101,7 @@ struct Partials {
 // Partials of one planet's velocity from sin E, cos E and 1/D,
 // D = 1 - e cos E (shared by both precisions).
 template <typename T>
-__device__ __forceinline__ void velocity_partials(T e, T K, T cw, T sw, T beta, T sE, T cE,
+__device__ __forceinline__ void velocity_partials(T e, T K, T cw, T sw, T beta, T ibeta, T sE, T cE,
                                                   T invD, Partials<T> &d) {
   const T cf = (cE - e) * invD;           // cos f
   const T sf = beta * sE * invD;          // sin f
@@ -108,7 +111,7 @@ __device__ __forceinline__ void velocity_partials(T e, T K, T cw, T sw, T beta, 
   d.dw = -K * (s_wf + e * sw);
   const T ks = K * s_wf * invD;
   d.dM = -ks * beta * invD;
-  d.de = K * cw - ks * sE * (T(1) / beta + beta * invD);
+  d.de = K * cw - ks * sE * (ibeta + beta * invD);
 }
 
 struct MixedGradLayout {
@@ -239,7 +242,8 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
         const GradPlanetF qj = q[j];
         Partials<float> d;
         const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
-        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+        velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, qj.ibeta, sEj[j], cEj[j], invD,
+                            d);
         d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
         kahan_add(gP[j], a2 * d.dP);
         g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
@@ -368,7 +372,8 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
           const GradPlanetD qj = q[j];
           Partials<double> d;
           const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
-          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, qj.ibeta, sEj[j], cEj[j],
+                            invD, d);
           d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
           g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
           g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);
@@ -570,7 +575,8 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
           const GradPlanetF qj = q[j];
           Partials<float> d;
           const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
-          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, sEj[j], cEj[j], invD, d);
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, qj.ibeta, sEj[j], cEj[j], invD,
+                            d);
           d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
           kahan_add(gP[j], a2 * d.dP);
           g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
@@ -749,7 +755,8 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
           const GradPlanetD qj = q[j];
           Partials<double> d;
           const double invD = 1.0 / fma(-qj.base.e, cEj[j], 1.0);
-          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, sEj[j], cEj[j], invD, d);
+          velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.base.beta, qj.ibeta, sEj[j], cEj[j],
+                            invD, d);
           d.dP = d.dM * (-kTwoPi * o.dt * qj.n2);
           g[5 * j + 0] = fma(a2, d.dP, g[5 * j + 0]);
           g[5 * j + 1] = fma(a2, d.dK, g[5 * j + 1]);

@@ -124,18 +124,18 @@ __global__ void predict_ragged_kernel(const double *__restrict__ params,
 
 struct RPlanetF {
   PlanetF base;
-  float K, cw, sw, beta, n2;
+  float K, cw, sw, beta, n2, ibeta;   // ibeta = 1/beta
 };
 
 struct RPlanetD {
   PlanetD base;
-  double K, cw, sw, n2;
+  double K, cw, sw, n2, ibeta;
 };
 
 __device__ inline RPlanetF rsetup_mixed(const double *p, double t_ref, double t0, bool grad) {
   RPlanetF g;
   g.base = planet_setup_mixed(p, t_ref, t0);
-  g.K = g.cw = g.sw = g.beta = g.n2 = 0.0f;
+  g.K = g.cw = g.sw = g.beta = g.n2 = g.ibeta = 0.0f;
   if (grad) {
     float w_hi, w_lo;
     split_d(p[3], w_hi, w_lo);
@@ -145,6 +145,7 @@ __device__ inline RPlanetF rsetup_mixed(const double *p, double t_ref, double t0
     g.cw = __fmaf_rn(-w_lo, sw, cw);
     g.K = d2f(p[1]);
     g.beta = sqrtf((1.0f - g.base.e) * (1.0f + g.base.e));
+    g.ibeta = 1.0f / g.beta;
     g.n2 = g.base.n_hi * g.base.n_hi;
   }
   return g;
@@ -153,17 +154,19 @@ __device__ inline RPlanetF rsetup_mixed(const double *p, double t_ref, double t0
 __device__ inline RPlanetD rsetup_f64(const double *p, double dref, bool grad) {
   RPlanetD g;
   g.base = planet_setup_f64(p, dref);
-  g.K = g.cw = g.sw = g.n2 = 0.0;
+  g.K = g.cw = g.sw = g.n2 = g.ibeta = 0.0;
   if (grad) {
     sincos(p[3], &g.sw, &g.cw);
     g.K = p[1];
     g.n2 = g.base.inv_P * g.base.inv_P;
+    g.ibeta = 1.0 / g.base.beta;
   }
   return g;
 }
 
 template <typename T>
-__device__ __forceinline__ void partials_r(T e, T K, T cw, T sw, T beta, T sE, T cE, T invD,
+__device__ __forceinline__ void partials_r(T e, T K, T cw, T sw, T beta, T ibeta, T sE, T cE,
+                                           T invD,
                                            T &dK, T &dw, T &dM, T &de) {
   const T cf = (cE - e) * invD;
   const T sf = beta * sE * invD;
@@ -173,7 +176,7 @@ __device__ __forceinline__ void partials_r(T e, T K, T cw, T sw, T beta, T sE, T
   dw = -K * (s_wf + e * sw);
   const T ks = K * s_wf * invD;
   dM = -ks * beta * invD;
-  de = K * cw - ks * sE * (T(1) / beta + beta * invD);
+  de = K * cw - ks * sE * (ibeta + beta * invD);
 }
 
 template <int J, bool GRAD>
@@ -227,7 +230,8 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
         const RPlanetF q = pl[j];
         float dK, dw, dM, de;
         const float invD = rcp_fast(__fmaf_rn(-q.base.e, cEj[j], 1.0f));
-        partials_r(q.base.e, q.K, q.cw, q.sw, q.beta, sEj[j], cEj[j], invD, dK, dw, dM, de);
+        partials_r(q.base.e, q.K, q.cw, q.sw, q.beta, q.ibeta, sEj[j], cEj[j], invD, dK, dw,
+                   dM, de);
         const float dP = dM * (-kTwoPiF * wt.y * q.n2);
         kahan_add(gP[GRAD ? j : 0], a2 * dP);
         g[5 * j + 1] = __fmaf_rn(a2, dK, g[5 * j + 1]);
@@ -298,7 +302,8 @@ __device__ __forceinline__ void body_f64(const RPlanetD *pl, double gam, const O
         const RPlanetD q = pl[j];
         double dK, dw, dM, de;
         const double invD = 1.0 / fma(-q.base.e, cEj[j], 1.0);
-        partials_r(q.base.e, q.K, q.cw, q.sw, q.base.beta, sEj[j], cEj[j], invD, dK, dw, dM, de);
+        partials_r(q.base.e, q.K, q.cw, q.sw, q.base.beta, q.ibeta, sEj[j], cEj[j], invD, dK,
+                   dw, dM, de);
         const double dP = dM * (-kTwoPi * o.dt * q.n2);
         g[5 * j + 0] = fma(a2, dP, g[5 * j + 0]);
         g[5 * j + 1] = fma(a2, dK, g[5 * j + 1]);
