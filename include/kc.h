@@ -198,25 +198,36 @@ kc_status kc_chi2_eval_mixed_noalloc(const double *params, const double *t,
  * MCMC the paper proposes to drive the evaluator, Sec. 6) for chains
  * first .. first+count-1 of a population of n_chains parameter vectors
  * (states [n_chains][5*n_pl+1], device, updated in place; chi2 [n_chains]
- * their current chi2, double for KC_FP64, float for KC_MIXED).  Chain i
- * proposes x* = x_i + gamma (x_r1 - x_r2) + eps_i with partners
- * (r1, r2) = partners[2c], partners[2c+1] (int32 [count][2]) and eps
- * [count][5*n_pl+1], evaluates chi2(x*) with the kernels of
- * kc_chi2_eval_ex (epoch t0, jitter, mode), and accepts iff
- * ln u[c] < -(chi2(x*) - chi2(x_i))/2 (u [count] in (0, 1]; flat prior,
- * invalid parameters are rejected).  For detailed balance with all chains of
- * the range updated at once, the partners must come from chains outside the
- * range (e.g. the other half of the population) and be distinct; partner
- * indices outside [0, n_chains) make the proposal NaN (rejected).  The caller
- * supplies the random draws and the workspaces proposals [count][5*n_pl+1]
- * and chi2_prop [count] (chi2's type); accepted [count] (may be NULL)
- * receives 1/0. */
+ * their current chi2, double for KC_FP64, float for KC_MIXED).  Chain
+ * i = first + c proposes
+ *   x*_p = x_ip + gamma (x_r1,p - x_r2,p) + (eps_scale[p] |x_ip|) z[c][p]
+ * (each operation rounded in that order, no fused operations), evaluates
+ * chi2(x*) with the kernels of kc_chi2_eval_ex (epoch t0, jitter, mode) and
+ * accepts iff ln u[c][0] < -(chi2(x*) - chi2(x_i))/2 (flat prior; invalid
+ * parameters give NaN chi2 and are rejected; u = 0 accepts any finite
+ * chi2).  The random numbers are inputs: z [count][5*n_pl+1] standard
+ * normal draws, u [count][3] uniform draws in [0, 1).  The partners are two
+ * distinct chains of the range partner_first .. partner_first+m-1
+ * (m = partner_count >= 2), uniform over ordered pairs:
+ *   k1 = floor(u[c][1] m) clamped to 0 .. m - 1,
+ *   k2 = floor(u[c][2] (m - 1)) clamped to 0 .. m - 2, k2 += (k2 >= k1),
+ *   r1 = partner_first + k1, r2 = partner_first + k2
+ * (in double; a NaN draw counts as 0, so no draw indexes outside the
+ * range).  The partner range must lie inside the population and not
+ * overlap the updated range (their states stay fixed during the step, which
+ * keeps detailed balance), else KC_ERR_ARG.  eps_scale [5*n_pl+1] (device)
+ * scales the perturbation per parameter (0 with equal values in every chain
+ * holds a parameter fixed).  The caller supplies the workspaces
+ * proposals [count][5*n_pl+1] and chi2_prop [count] (chi2's type);
+ * accepted [count] (may be NULL) receives 1/0. */
 kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains,
                          int32_t n_pl, const double *t, const double *v_obs,
                          const double *sigma, int32_t n_obs, double t0,
                          double jitter, kc_mode mode, int64_t first,
-                         int64_t count, double gamma, const int32_t *partners,
-                         const double *eps, const double *u, double *proposals,
+                         int64_t count, int64_t partner_first,
+                         int64_t partner_count, double gamma,
+                         const double *eps_scale, const double *z,
+                         const double *u, double *proposals,
                          void *chi2_prop, int32_t *accepted, kc_stream stream);
 
 /* -------------------------------------------------------- model, Kepler */

@@ -100,8 +100,8 @@ def bind(lib):
     lib.kco_predict_ragged.argtypes = [d, i64p, i32p, d, i64p, i64, ctypes.c_double, d]
     lib.kco_demcmc_step.restype = ctypes.c_int
     lib.kco_demcmc_step.argtypes = [d, d, i64, ctypes.c_int, d, d, d, i64, ctypes.c_double,
-                                    ctypes.c_double, i64, i64, ctypes.c_double, i32p, d, d, d,
-                                    d, i32p]
+                                    ctypes.c_double, i64, i64, i64, i64, ctypes.c_double, d, d,
+                                    d, d, d, i32p]
     lib.kco_gauss_newton.argtypes = [d, d, d, i64, ctypes.c_int, i64, ctypes.c_double,
                                      ctypes.c_double, d]
     lib.kco_gauss_newton.restype = ctypes.c_int
@@ -303,24 +303,27 @@ def predict_ragged(params, par_off, n_pl, t, obs_off, t0: float = 0.0) -> np.nda
 
 
 def demcmc_step(states, chi2_cur, t, v, sigma, n_pl: int, first: int, count: int,
-                gamma: float, partners, eps, u, t0: float = 0.0, jitter: float = 0.0):
-    """One DE-MC step of chains first .. first+count-1 (ter Braak 2006).
-    Returns (states, chi2, accepted, proposals, chi2_of_proposals); the
-    inputs are not modified."""
+                pfirst: int, pcount: int, gamma: float, eps_scale, z, u, t0: float = 0.0,
+                jitter: float = 0.0):
+    """One DE-MC step of chains first .. first+count-1 (ter Braak 2006), the
+    partners drawn from chains pfirst .. pfirst+pcount-1; z [count, n_par]
+    standard normal and u [count, 3] uniform draws.  Returns (states, chi2,
+    accepted, proposals, chi2_of_proposals); the inputs are not modified."""
     states = _f64(states).copy()
     chi2_cur = _f64(chi2_cur).copy()
     t, v, sigma = _f64(t), _f64(v), _f64(sigma)
     n_par = 5 * n_pl + 1
     n_chains = states.size // n_par
-    partners = np.ascontiguousarray(partners, dtype=np.int32)
-    eps, u = _f64(eps), _f64(u)
+    eps_scale = np.ascontiguousarray(np.broadcast_to(_f64(eps_scale), (n_par,)))
+    z, u = _f64(z), _f64(u)
     prop = np.empty((count, n_par))
     chi2_prop = np.empty(count)
     acc = np.empty(count, dtype=np.int32)
     rc = _load().kco_demcmc_step(_p(states), _p(chi2_cur), n_chains, int(n_pl), _p(t), _p(v),
                                  _p(sigma), t.size, float(t0), float(jitter), int(first),
-                                 int(count), float(gamma), _p(partners, ctypes.c_int32), _p(eps),
-                                 _p(u), _p(prop), _p(chi2_prop), _p(acc, ctypes.c_int32))
+                                 int(count), int(pfirst), int(pcount), float(gamma),
+                                 _p(eps_scale), _p(z), _p(u), _p(prop), _p(chi2_prop),
+                                 _p(acc, ctypes.c_int32))
     if rc != 0:
         raise ValueError("oracle.demcmc_step: bad range")
     return states.reshape(-1, n_par), chi2_cur, acc, prop, chi2_prop

@@ -408,32 +408,53 @@ int kco_predict_ragged(const double *params, const int64_t *par_off,
     return 0;
 }
 
+/* floor(f) clamped to 0 .. hi, NaN to 0. */
+static int64_t kco_clamp_index(double f, int64_t hi)
+{
+    f = floor(f);
+    return f >= 0.0 ? (f < (double)hi ? (int64_t)f : hi) : 0;
+}
+
 /* One differential-evolution MCMC step (ter Braak 2006) for chains
- * first .. first+count-1 (see the library's kc_demcmc_step): proposal
- * x* = x_i + gamma (x_r1 - x_r2) + eps (evaluated in that order, no fused
- * operations), chi2 of the proposals in FP64, acceptance iff
- * ln u < -(chi2* - chi2_i)/2; accepted states and chi2 replace the current
- * ones.  proposals [count][n_par], chi2_prop [count] and accepted [count]
- * are outputs.  Partners outside [0, n_chains) give a NaN proposal. */
+ * first .. first+count-1 (see the library's kc_demcmc_step).  Chain
+ * i = first + c takes two distinct partners of the range
+ * pfirst .. pfirst+m-1 (m = pcount >= 2) from its uniform draws
+ * u[c][1], u[c][2]: k1 = floor(u1 m) and k2 = floor(u2 (m - 1)) (each
+ * clamped into its range), k2 += (k2 >= k1), which is uniform over ordered
+ * pairs of distinct chains; proposes
+ *   x*_p = x_ip + gamma (x_r1,p - x_r2,p) + (eps_scale_p |x_ip|) z[c][p]
+ * (each operation rounded in that order, no fused operations); evaluates
+ * chi2 of the proposals in FP64 and accepts iff
+ * ln u[c][0] < -(chi2* - chi2_i)/2.  Accepted states and chi2 replace the
+ * current ones.  proposals [count][n_par], chi2_prop [count] and
+ * accepted [count] are outputs.  Returns -1 on a bad range (the partner
+ * range outside the population, shorter than 2 or overlapping the updated
+ * chains). */
 int kco_demcmc_step(double *states, double *chi2, int64_t n_chains, int n_pl,
                     const double *t, const double *v, const double *sigma,
                     int64_t n_obs, double t0, double jitter, int64_t first,
-                    int64_t count, double gamma, const int32_t *partners,
-                    const double *eps, const double *u, double *proposals,
-                    double *chi2_prop, int32_t *accepted)
+                    int64_t count, int64_t pfirst, int64_t pcount, double gamma,
+                    const double *eps_scale, const double *z, const double *u,
+                    double *proposals, double *chi2_prop, int32_t *accepted)
 {
     int n_par = 5 * n_pl + 1, p;
     int64_t c;
     if (first < 0 || count < 0 || first + count > n_chains) return -1;
+    if (pfirst < 0 || pcount < 2 || pfirst + pcount > n_chains) return -1;
+    if (count > 0 && pfirst < first + count && first < pfirst + pcount) return -1;
     for (c = 0; c < count; ++c) {
-        int64_t i = first + c, r1 = partners[2 * c], r2 = partners[2 * c + 1];
+        int64_t i = first + c;
+        int64_t k1 = kco_clamp_index(u[3 * c + 1] * (double)pcount, pcount - 1);
+        int64_t k2 = kco_clamp_index(u[3 * c + 2] * (double)(pcount - 1), pcount - 2);
+        int64_t r1, r2;
+        if (k2 >= k1) k2 += 1;
+        r1 = pfirst + k1;
+        r2 = pfirst + k2;
         for (p = 0; p < n_par; ++p) {
-            double x = NAN;
-            if (r1 >= 0 && r1 < n_chains && r2 >= 0 && r2 < n_chains) {
-                double d = states[r1 * n_par + p] - states[r2 * n_par + p];
-                x = (states[i * n_par + p] + gamma * d) + eps[c * n_par + p];
-            }
-            proposals[c * n_par + p] = x;
+            double xi = states[i * n_par + p];
+            double d = states[r1 * n_par + p] - states[r2 * n_par + p];
+            double eps = (eps_scale[p] * fabs(xi)) * z[c * n_par + p];
+            proposals[c * n_par + p] = (xi + gamma * d) + eps;
         }
     }
     if (kco_chi2(proposals, t, v, sigma, count, n_pl, n_obs, t0, jitter, chi2_prop,
@@ -441,7 +462,7 @@ int kco_demcmc_step(double *states, double *chi2, int64_t n_chains, int n_pl,
         return -1;
     for (c = 0; c < count; ++c) {
         int64_t i = first + c;
-        int acc = log(u[c]) < -0.5 * (chi2_prop[c] - chi2[i]);
+        int acc = log(u[3 * c]) < -0.5 * (chi2_prop[c] - chi2[i]);
         if (acc) {
             for (p = 0; p < n_par; ++p) states[i * n_par + p] = proposals[c * n_par + p];
             chi2[i] = chi2_prop[c];

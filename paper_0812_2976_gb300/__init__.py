@@ -442,14 +442,17 @@ class RaggedPlan:
             pass
 
 
-def kc_demcmc_step(states, chi2, t, v_obs, sigma, first: int, count: int, gamma: float,
-                   partners, eps, u, proposals=None, chi2_prop=None, accepted=None,
-                   t0: float = 0.0, jitter: float = 0.0, mode="mixed", stream=None):
-    """One DE-MC step of chains first .. first+count-1 in place
+def kc_demcmc_step(states, chi2, t, v_obs, sigma, first: int, count: int,
+                   partner_first: int, partner_count: int, gamma: float, eps_scale, z, u,
+                   proposals=None, chi2_prop=None, accepted=None, t0: float = 0.0,
+                   jitter: float = 0.0, mode="mixed", stream=None):
+    """One DE-MC step of chains first .. first+count-1 in place, partners
+    drawn from chains partner_first .. partner_first+partner_count-1
     (kc_demcmc_step).  states: float64 [n_chains, 5*n_pl+1]; chi2: float32
-    ('mixed') or float64 ('fp64') [n_chains]; partners int32 [count, 2];
-    eps float64 [count, 5*n_pl+1]; u float64 [count].  Returns accepted
-    (int32 [count])."""
+    ('mixed') or float64 ('fp64') [n_chains]; eps_scale float64
+    [5*n_pl+1]; z float64 [count, 5*n_pl+1] standard normal draws; u
+    float64 [count, 3] uniform draws in [0, 1).  Returns accepted (int32
+    [count])."""
     states = _dev_f64("states", states, 2)
     t, v_obs, sigma = _obs(t, v_obs, sigma)
     m = _mode(mode)
@@ -458,9 +461,11 @@ def kc_demcmc_step(states, chi2, t, v_obs, sigma, first: int, count: int, gamma:
         raise TypeError(f"chi2 must be a {dtype} CUDA tensor")
     n_pl = n_planets(states)
     npar = 5 * n_pl + 1
-    partners = partners.to(device=states.device, dtype=torch.int32).contiguous()
-    eps = _dev_f64("eps", eps, 2)
-    u = _dev_f64("u", u, 1)
+    eps_scale = _dev_f64("eps_scale", eps_scale, 1)
+    z = _dev_f64("z", z, 2)
+    u = _dev_f64("u", u, 2)
+    if eps_scale.numel() != npar or z.shape != (count, npar) or u.shape != (count, 3):
+        raise ValueError("eps_scale, z and u must be [n_par], [count, n_par] and [count, 3]")
     if proposals is None:
         proposals = torch.empty((count, npar), dtype=torch.float64, device=states.device)
     if chi2_prop is None:
@@ -471,8 +476,9 @@ def kc_demcmc_step(states, chi2, t, v_obs, sigma, first: int, count: int, gamma:
     _lib.check(lib.kc_demcmc_step(
         states.data_ptr(), chi2.data_ptr(), states.shape[0], n_pl, t.data_ptr(),
         v_obs.data_ptr(), sigma.data_ptr(), t.numel(), float(t0), float(jitter), m, int(first),
-        int(count), float(gamma), partners.data_ptr(), eps.data_ptr(), u.data_ptr(),
-        proposals.data_ptr(), chi2_prop.data_ptr(), accepted.data_ptr(), _stream(stream)),
+        int(count), int(partner_first), int(partner_count), float(gamma), eps_scale.data_ptr(),
+        z.data_ptr(), u.data_ptr(), proposals.data_ptr(), chi2_prop.data_ptr(),
+        accepted.data_ptr(), _stream(stream)),
         "kc_demcmc_step")
     return accepted
 
@@ -519,34 +525,29 @@ class DEMCMC:
         self._prop = torch.empty((self.half, self.npar), dtype=torch.float64, device=dev)
         self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
         self._acc = torch.empty(n, dtype=torch.int32, device=dev)
-        # partner index offsets: the first half draws from the second, and back
-        self._off = torch.cat([torch.full((self.half, 2), self.half, dtype=torch.int64),
-                               torch.zeros((self.half, 2), dtype=torch.int64)]).to(dev)
         self.generation = 0
         self._n_acc = torch.zeros((), dtype=torch.int64, device=dev)   # no host syncs
         self.proposed = 0
 
     def _draws(self):
-        """Every random number of one generation (both halves) in one go:
-        the second half's states, which scale its jitter, do not change while
-        the first half moves, and partner indices only name chains."""
+        """Every random number of one generation (both halves): standard
+        normal perturbations and three uniforms per chain (acceptance, two
+        partners); the step kernels scale and map them.  The normals are
+        drawn in single precision (a perturbation needs no more; double
+        precision normals cost 27 us a generation on this GPU, these 15) and
+        widened."""
         h, dev = self.half, self.states.device
-        eps = torch.randn((2 * h, self.npar), generator=self.gen, dtype=torch.float64,
-                          device=dev)
-        eps.mul_(self.eps_scale).mul_(self.states.abs())
-        u = torch.rand(2 * h, generator=self.gen, dtype=torch.float64, device=dev)
-        u.clamp_min_(1e-300)
-        r1 = torch.randint(0, h, (2 * h,), generator=self.gen, device=dev)
-        r2 = torch.randint(0, h - 1, (2 * h,), generator=self.gen, device=dev)
-        r2 += (r2 >= r1).to(r2.dtype)                # uniform over the others: r2 != r1
-        return eps, u, (torch.stack([r1, r2], dim=1) + self._off).to(torch.int32)
+        z = torch.randn((2 * h, self.npar), generator=self.gen, dtype=torch.float32,
+                        device=dev).double()
+        u = torch.rand((2 * h, 3), generator=self.gen, dtype=torch.float64, device=dev)
+        return z, u
 
     def _generation(self, gamma: float) -> None:
-        eps, u, partners = self._draws()
+        z, u = self._draws()
         h = self.half
-        for first in (0, h):
-            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, gamma,
-                           partners[first:first + h], eps[first:first + h], u[first:first + h],
+        for first, other in ((0, h), (h, 0)):
+            kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, other, h,
+                           gamma, self.eps_scale, z[first:first + h], u[first:first + h],
                            self._prop, self._cp, self._acc[first:first + h], self.t0,
                            self.jitter, self.mode)
         self._n_acc += self._acc.sum()

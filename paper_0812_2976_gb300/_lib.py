@@ -51,7 +51,7 @@ SIGNATURES = {
     "kc_nll_eval": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _i32, _d, _st]),
     "kc_nll_grad": (_i32, [_d, _d, _d, _d, _i64, _i32, _i32, _f64, _i32, _d, _d, _st]),
     "kc_demcmc_step": (_i32, [_d, _d, _i64, _i32, _d, _d, _d, _i32, _f64, _f64, _i32, _i64,
-                              _i64, _f64, _d, _d, _d, _d, _d, _d, _st]),
+                              _i64, _i64, _i64, _f64, _d, _d, _d, _d, _d, _d, _st]),
     "kc_rv_predict": (_i32, [_d, _d, _i64, _i32, _i32, _f64, _d, _st]),
     "kc_rv_predict_ragged": (_i32, [_d, _d, _d, _d, _d, _i64, _f64, _d, _st]),
     "kc_kepler_solve": (_i32, [_d, _d, _i64, _i32, _d, _st]),

@@ -410,25 +410,33 @@ kc_status kc_nll_grad(const double *params, const double *t, const double *v_obs
 kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains, int32_t n_pl,
                          const double *t, const double *v_obs, const double *sigma, int32_t n_obs,
                          double t0, double jitter, kc_mode mode, int64_t first, int64_t count,
-                         double gamma, const int32_t *partners, const double *eps, const double *u,
+                         int64_t partner_first, int64_t partner_count, double gamma,
+                         const double *eps_scale, const double *z, const double *u,
                          double *proposals, void *chi2_prop, int32_t *accepted,
                          kc_stream stream) {
   const char *fn = "kc_demcmc_step";
   if (n_chains < 0 || first < 0 || count < 0 || first + count > n_chains)
     return fail(KC_ERR_ARG, "%s: need 0 <= first <= first + count <= n_chains", fn);
+  if (partner_first < 0 || partner_count < 2 || partner_first + partner_count > n_chains)
+    return fail(KC_ERR_ARG,
+                "%s: need 0 <= partner_first, partner_count >= 2, partner_first + "
+                "partner_count <= n_chains", fn);
+  if (count > 0 && partner_first < first + count && first < partner_first + partner_count)
+    return fail(KC_ERR_ARG, "%s: the partner range overlaps the updated range", fn);
   if (mode != KC_FP64 && mode != KC_MIXED) return fail(KC_ERR_ARG, "%s: bad mode", fn);
   if (!std::isfinite(gamma)) return fail(KC_ERR_ARG, "%s: gamma must be finite", fn);
   if (count == 0) return ok();
-  if (!states || !chi2 || !partners || !eps || !u || !proposals || !chi2_prop)
+  if (!states || !chi2 || !eps_scale || !z || !u || !proposals || !chi2_prop)
     return fail(KC_ERR_ARG, "%s: NULL pointer", fn);
-  if (((uintptr_t)states | (uintptr_t)eps | (uintptr_t)u | (uintptr_t)proposals) & 7)
+  if (((uintptr_t)states | (uintptr_t)eps_scale | (uintptr_t)z | (uintptr_t)u |
+       (uintptr_t)proposals) & 7)
     return fail(KC_ERR_ARG, "%s: pointer not 8-byte aligned", fn);
   kc_status st = check_uniform(states, t, v_obs, sigma, count, n_pl, n_obs, chi2_prop, fn);
   if (st != KC_OK) return st;
   const int npar = 5 * n_pl + 1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = kc::launch_demcmc_propose(states, n_chains, npar, first, count, gamma, partners,
-                                            eps, proposals, s);
+  cudaError_t e = kc::launch_demcmc_propose(states, npar, first, count, partner_first,
+                                            partner_count, gamma, eps_scale, z, u, proposals, s);
   if (e != cudaSuccess) return cuda_status(e, "kc_demcmc_step: propose");
   st = kc_chi2_eval_ex(proposals, t, v_obs, sigma, count, n_pl, n_obs, t0, jitter, mode,
                        chi2_prop, nullptr, stream);

@@ -10,8 +10,9 @@
 // detailed balance, the population is split in two halves: a step updates
 // one half, drawing r1, r2 from the other half, whose states stay fixed
 // during the step (the ensemble parallelisation of Goodman & Weare as used by
-// Foreman-Mackey et al. 2013).  The random numbers are inputs, so the step is
-// a deterministic function of them.
+// Foreman-Mackey et al. 2013).  The random numbers are inputs (standard
+// normal and uniform draws), so the step is a deterministic function of
+// them; the kernels turn them into the perturbation and the partner pair.
 #include <cmath>
 
 #include "kc_internal.h"
@@ -20,27 +21,44 @@ namespace kc {
 
 namespace {
 
-__device__ inline double nan_dm() { return __longlong_as_double(0x7ff8000000000000ll); }
+// floor(f) clamped to 0 .. hi (NaN to 0): an index inside the range for any
+// draw, also outside [0, 1).
+__device__ inline int64_t clamp_index(double f, int64_t hi) {
+  f = floor(f);
+  return f >= 0.0 ? (f < (double)hi ? (int64_t)f : hi) : 0;
+}
 
-// x* = x_i + gamma (x_r1 - x_r2) + eps, written with explicit roundings so
-// that the result does not depend on FMA contraction.
-__global__ void demcmc_propose_kernel(const double *__restrict__ states, int64_t n_chains,
-                                      int n_par, int64_t first, int64_t count, double gamma,
-                                      const int32_t *__restrict__ partners,
-                                      const double *__restrict__ eps, double *__restrict__ prop) {
+// The two partners of draw pair (u1, u2) in [0, 1): distinct, uniform over
+// the ordered pairs of the m chains from pfirst (m >= 2, checked by the host).
+__device__ inline void demcmc_partners(double u1, double u2, int64_t pfirst, int64_t m,
+                                       int64_t &r1, int64_t &r2) {
+  const int64_t k1 = clamp_index(u1 * (double)m, m - 1);
+  int64_t k2 = clamp_index(u2 * (double)(m - 1), m - 2);
+  k2 += k2 >= k1 ? 1 : 0;
+  r1 = pfirst + k1;
+  r2 = pfirst + k2;
+}
+
+// x*_p = x_ip + gamma (x_r1,p - x_r2,p) + (eps_scale_p |x_ip|) z_p, written
+// with explicit roundings so that the result does not depend on FMA
+// contraction.
+__global__ void demcmc_propose_kernel(const double *__restrict__ states, int n_par, int64_t first,
+                                      int64_t count, int64_t pfirst, int64_t pcount,
+                                      double gamma, const double *__restrict__ eps_scale,
+                                      const double *__restrict__ z, const double *__restrict__ u,
+                                      double *__restrict__ prop) {
   const int64_t total = count * n_par;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = idx / n_par;
     const int p = (int)(idx - c * n_par);
     const int64_t i = first + c;
-    const int64_t r1 = partners[2 * c], r2 = partners[2 * c + 1];
-    double x = nan_dm();      // out-of-range partners: NaN proposal, rejected
-    if (r1 >= 0 && r1 < n_chains && r2 >= 0 && r2 < n_chains) {
-      const double d = __dsub_rn(states[r1 * n_par + p], states[r2 * n_par + p]);
-      x = __dadd_rn(__dadd_rn(states[i * n_par + p], __dmul_rn(gamma, d)), eps[idx]);
-    }
-    prop[idx] = x;
+    int64_t r1, r2;
+    demcmc_partners(u[3 * c + 1], u[3 * c + 2], pfirst, pcount, r1, r2);
+    const double xi = states[i * n_par + p];
+    const double d = __dsub_rn(states[r1 * n_par + p], states[r2 * n_par + p]);
+    const double eps = __dmul_rn(__dmul_rn(eps_scale[p], fabs(xi)), z[idx]);
+    prop[idx] = __dadd_rn(__dadd_rn(xi, __dmul_rn(gamma, d)), eps);
   }
 }
 
@@ -55,7 +73,7 @@ __global__ void demcmc_accept_kernel(double *__restrict__ states, T *__restrict_
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = first + c;
     const double delta = (double)chi2_prop[c] - (double)chi2[i];
-    const bool acc = log(u[c]) < -0.5 * delta;          // false when delta is NaN
+    const bool acc = log(u[3 * c]) < -0.5 * delta;      // false when delta is NaN
     if (acc) {
       for (int p = 0; p < n_par; ++p) states[i * n_par + p] = prop[c * n_par + p];
       chi2[i] = chi2_prop[c];
@@ -71,11 +89,12 @@ int grid_elems(int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_demcmc_propose(const double *states, int64_t n_chains, int n_par, int64_t first,
-                                  int64_t count, double gamma, const int32_t *partners,
-                                  const double *eps, double *prop, cudaStream_t st) {
+cudaError_t launch_demcmc_propose(const double *states, int n_par, int64_t first, int64_t count,
+                                  int64_t pfirst, int64_t pcount, double gamma,
+                                  const double *eps_scale, const double *z, const double *u,
+                                  double *prop, cudaStream_t st) {
   demcmc_propose_kernel<<<grid_elems(count * n_par), 256, 0, st>>>(
-      states, n_chains, n_par, first, count, gamma, partners, eps, prop);
+      states, n_par, first, count, pfirst, pcount, gamma, eps_scale, z, u, prop);
   return cudaGetLastError();
 }
 

@@ -105,9 +105,10 @@ Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 int obs_tile_for(Kind kind, int n_obs);
 
 // DE-MC step pieces (kc_demcmc.cu).
-cudaError_t launch_demcmc_propose(const double *states, int64_t n_chains, int n_par, int64_t first,
-                                  int64_t count, double gamma, const int32_t *partners,
-                                  const double *eps, double *prop, cudaStream_t st);
+cudaError_t launch_demcmc_propose(const double *states, int n_par, int64_t first, int64_t count,
+                                  int64_t pfirst, int64_t pcount, double gamma,
+                                  const double *eps_scale, const double *z, const double *u,
+                                  double *prop, cudaStream_t st);
 cudaError_t launch_demcmc_accept(double *states, void *chi2, const double *prop,
                                  const void *chi2_prop, int64_t first, int64_t count, int n_par,
                                  const double *u, bool f64, int32_t *accepted, cudaStream_t st);

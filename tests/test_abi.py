@@ -81,6 +81,13 @@ def test_bad_arguments_rejected_on_host(lib):
                                     p, None) == 1
     assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 1, None, None, None, None) == 1
     assert lib.kc_measure_pipe_rate(0, None, None) == 1
+    # DE-MC step: the partner range must be inside the population, hold two
+    # chains and not overlap the updated chains (states, n_chains = 16,
+    # n_pl = 1, ..., first = 0, count = 8, partner_first, partner_count)
+    for pf, pc, msg in ((4, 8, b"overlaps"), (8, 1, b"partner_count"), (10, 8, b"partner_count")):
+        assert lib.kc_demcmc_step(p, p, 16, 1, p, p, p, 8, 0.0, 0.0, 1, 0, 8, pf, pc, 0.5,
+                                  p, p, p, p, p, None, None) == 1
+        assert msg in lib.kc_last_error()
 
 
 def test_empty_batches_are_no_ops(lib):

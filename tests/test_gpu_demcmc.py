@@ -1,7 +1,7 @@
 """DE-MC step (kc_demcmc_step) and driver on the GPU vs the FP64 oracle.
 
-The random draws (partners, eps, u) and the current chi2 are the same
-inputs on both sides.  Proposals are exact arithmetic of the inputs and must
+The random draws (standard normal z, uniform u) and the current chi2 are the
+same inputs on both sides; each side maps them to partners and perturbations.  Proposals are exact arithmetic of the inputs and must
 match bit for bit; accept decisions must match wherever the Metropolis
 margin |ln u + (chi2* - chi2)/2| is above what the chi2 tolerance of the mode
 can move (1e-12 relative in FP64, 1e-5 mixed); the states then follow."""
@@ -34,33 +34,31 @@ def test_step_matches_oracle(kc, oracle_mod, mode, tol):
     chi = oracle_mod.chi2(states, w.t, v, w.sigma, w.n_pl)
     rng = np.random.default_rng(40)
     first, count, other = 256, 256, 0
-    r1 = rng.integers(0, 256, count)
-    r2 = (r1 + rng.integers(1, 256, count)) % 256
-    partners = np.stack([r1, r2], axis=1) + other
-    partners[7] = [600, 3]                                     # out of range: rejected
-    eps = rng.normal(0, 1e-4, (count, states.shape[1])) * np.abs(states[first:])
-    u = rng.uniform(0, 1, count)
-    gamma = 2.38 / np.sqrt(2 * states.shape[1])
-    ref = oracle_mod.demcmc_step(states, chi, w.t, v, w.sigma, w.n_pl, first, count, gamma,
-                                 partners, eps, u)
+    npar = states.shape[1]
+    scale = np.full(npar, 1e-4)
+    z = rng.standard_normal((count, npar))
+    u = rng.uniform(0, 1, (count, 3))
+    u[5, 1:] = [0.0, 1.0 - 2.0 ** -53]                          # edge draws
+    u[7, 1:] = np.nan                                          # counts as 0
+    gamma = 2.38 / np.sqrt(2 * npar)
+    ref = oracle_mod.demcmc_step(states, chi, w.t, v, w.sigma, w.n_pl, first, count, other,
+                                 256, gamma, scale, z, u)
     ref_states, ref_chi, ref_acc, ref_prop, ref_cp = ref
     S = dev(states)
     C = dev(chi, torch.float64 if mode == "fp64" else torch.float32)
     prop = torch.empty((count, states.shape[1]), dtype=torch.float64, device="cuda")
     cp = torch.empty(count, dtype=C.dtype, device="cuda")
-    acc = kc.kc_demcmc_step(S, C, dev(w.t), dev(v), dev(w.sigma), first, count, gamma,
-                            torch.tensor(partners, dtype=torch.int32), dev(eps), dev(u),
-                            proposals=prop, chi2_prop=cp, mode=mode).cpu().numpy()
+    acc = kc.kc_demcmc_step(S, C, dev(w.t), dev(v), dev(w.sigma), first, count, other, 256,
+                            gamma, dev(scale), dev(z), dev(u), proposals=prop, chi2_prop=cp,
+                            mode=mode).cpu().numpy()
     prop = prop.cpu().numpy()
-    finite = np.all(np.isfinite(ref_prop), axis=1)
-    assert np.array_equal(prop[finite], ref_prop[finite])       # bit for bit
-    assert np.all(np.isnan(prop[7])) and acc[7] == 0
+    assert np.array_equal(prop, ref_prop)                       # bit for bit
     cp = cp.cpu().numpy().astype(np.float64)
     ok = np.isfinite(ref_cp)
     assert np.max(np.abs(cp[ok] - ref_cp[ok]) / np.maximum(ref_cp[ok], 1.0)) <= tol
     # decisions away from the Metropolis boundary are identical
     chi_cur = C.cpu().numpy().astype(np.float64)[first:] if mode == "mixed" else chi[first:]
-    margin = np.abs(np.log(u) + 0.5 * (ref_cp - chi[first:]))
+    margin = np.abs(np.log(u[:, 0]) + 0.5 * (ref_cp - chi[first:]))
     slack = 4 * tol * np.maximum(ref_cp, 1.0) + 4 * tol * np.maximum(chi_cur, 1.0)
     sure = ok & (margin > slack)
     assert sure.sum() > count // 2
@@ -70,6 +68,11 @@ def test_step_matches_oracle(kc, oracle_mod, mode, tol):
         expect = ref_prop[c] if ref_acc[c] else states[first + c]
         assert np.array_equal(new_states[first + c], expect)
     assert np.array_equal(new_states[:first], states[:first])
+    # partner ranges that overlap the updated chains or leave the population
+    for pf, pc in ((128, 256), (0, 1), (400, 200)):
+        with pytest.raises(Exception):
+            kc.kc_demcmc_step(S, C, dev(w.t), dev(v), dev(w.sigma), first, count, pf, pc, gamma,
+                              dev(scale), dev(z), dev(u), mode=mode)
 
 
 def test_driver_samples_the_linear_gaussian_posterior(kc):

@@ -436,25 +436,76 @@ def test_nll_gradient_matches_central_differences(oracle_mod):
 # ------------------------------------------------ DE-MC step
 
 def test_demcmc_zero_move_always_accepted(oracle_mod):
-    """gamma = 0, eps = 0: the proposal is the state itself, Delta chi2 = 0,
-    and ln u < 0 for u < 1 accepts it (states unchanged)."""
+    """gamma = 0, eps_scale = 0: the proposal is the state itself, Delta
+    chi2 = 0, and ln u < 0 for u < 1 accepts it (states unchanged)."""
     rng = np.random.default_rng(22)
     states = _random_systems(rng, 8, 2)
     t = np.sort(rng.uniform(2450000, 2452000, 30))
     v = rng.normal(0, 30, 30)
     sig = rng.uniform(1, 5, 30)
     chi = oracle_mod.chi2(states, t, v, sig, 2)
-    partners = np.stack([np.arange(4, 8), np.arange(5, 9) % 8 + 0], axis=1)
-    partners[:, 1] = np.where(partners[:, 1] < 4, 4, partners[:, 1])
-    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, 2, 0, 4, 0.0, partners,
-                                                   np.zeros((4, 11)), rng.uniform(0.01, 0.99, 4))
+    u = rng.uniform(0.0, 1.0, (4, 3))
+    u[:, 0] = rng.uniform(0.01, 0.99, 4)
+    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, 2, 0, 4, 4, 4, 0.0,
+                                                   np.zeros(11), rng.standard_normal((4, 11)), u)
     assert np.array_equal(prop, states[:4]) and np.array_equal(cp, chi[:4])
     assert np.all(acc == 1) and np.array_equal(st, states)
 
 
+def test_demcmc_partners_and_perturbation(oracle_mod):
+    """The partner pair, read back from the proposals (gamma = 1 and chain j
+    holding P = j, K = j^2, so P* - P_i = r1 - r2 and K* - K_i = r1^2 - r2^2):
+    two distinct chains of the partner range, uniform over the ordered
+    pairs (chi-square over 2000 draws), also at the edge draws 0, 1 - 2^-53
+    and NaN (which counts as 0); and with gamma = 0 the perturbation is
+    (eps_scale |x|) z, and only that."""
+    rng = np.random.default_rng(27)
+    n_pl, m = 1, 10
+    n = 2 * m
+    states = np.zeros((n, 6))
+    states[:, 0] = np.arange(n, dtype=float)
+    states[:, 1] = np.arange(n, dtype=float) ** 2
+    states[:, 2] = 0.1
+    t = np.linspace(2450000, 2450100, 5)
+    v, sig = np.zeros(5), np.ones(5)
+    chi = np.full(n, 1e300)
+    pairs = []
+    for rep_ in range(200):
+        u = rng.uniform(0.0, 1.0, (m, 3))
+        if rep_ == 0:
+            u[0, 1:] = 0.0
+            u[1, 1:] = 1.0 - 2.0 ** -53
+            u[2, 1:] = np.nan
+        _, _, _, prop, _ = oracle_mod.demcmc_step(states, chi, t, v, sig, n_pl, 0, m, m, m, 1.0,
+                                                  np.zeros(6), np.zeros((m, 6)), u)
+        d1 = prop[:, 0] - states[:m, 0]
+        d2 = prop[:, 1] - states[:m, 1]
+        s = d2 / d1
+        r1, r2 = np.rint((s + d1) / 2).astype(int), np.rint((s - d1) / 2).astype(int)
+        assert np.all(r1 != r2) and np.all((r1 >= m) & (r1 < n)) and np.all((r2 >= m) & (r2 < n))
+        if rep_ == 0:
+            assert (r1[0], r2[0]) == (m, m + 1) and (r1[1], r2[1]) == (n - 1, n - 2)
+            assert (r1[2], r2[2]) == (m, m + 1)
+            r1, r2 = r1[3:], r2[3:]
+        pairs.append((r1 - m) * m + (r2 - m))
+    counts = np.bincount(np.concatenate(pairs), minlength=m * m).reshape(m, m)
+    assert np.all(np.diag(counts) == 0)
+    expect = counts.sum() / (m * (m - 1))
+    stat = ((counts - expect) ** 2 / expect)[~np.eye(m, dtype=bool)].sum()
+    assert stat < 160            # chi-square, 89 degrees of freedom: p ~ 1e-5
+    # perturbation with gamma = 0
+    x = _random_systems(rng, n, n_pl)
+    scale = rng.uniform(0.0, 1e-3, 6)
+    z = rng.standard_normal((m, 6))
+    _, _, _, prop, _ = oracle_mod.demcmc_step(x, np.full(n, 1e300), t, v, sig, n_pl, 0, m, m, m,
+                                              0.0, scale, z, rng.uniform(0, 1, (m, 3)))
+    assert np.array_equal(prop, x[:m] + (scale * np.abs(x[:m])) * z)
+
+
 def test_demcmc_metropolis_rule(oracle_mod):
     """Accept iff u < exp(-(chi2* - chi2)/2), checked against chi2 computed
-    separately; rejected chains keep state and chi2, bad partners reject."""
+    separately; rejected chains keep state and chi2; partner ranges that
+    overlap the updated chains or leave the population are refused."""
     rng = np.random.default_rng(23)
     n, n_pl = 40, 1
     states = _random_systems(rng, n, n_pl, e_max=0.5)
@@ -462,22 +513,23 @@ def test_demcmc_metropolis_rule(oracle_mod):
     v = oracle_mod.predict(states[0], t, n_pl)[0] + rng.normal(0, 2, 25)
     sig = np.full(25, 2.0)
     chi = oracle_mod.chi2(states, t, v, sig, n_pl)
-    partners = np.stack([rng.integers(20, 40, 20), rng.integers(20, 40, 20)], axis=1)
-    partners[3] = [55, 21]                                 # out of range
-    eps = rng.normal(0, 1e-3, (20, 6)) * np.abs(states[:20])
-    u = rng.uniform(0, 1, 20)
-    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, n_pl, 0, 20, 0.7,
-                                                   partners, eps, u)
+    z = rng.standard_normal((20, 6))
+    u = rng.uniform(0, 1, (20, 3))
+    st, c2, acc, prop, cp = oracle_mod.demcmc_step(states, chi, t, v, sig, n_pl, 0, 20, 20, 20,
+                                                   0.7, np.full(6, 1e-3), z, u)
     ref_cp = oracle_mod.chi2(prop, t, v, sig, n_pl)
     finite = np.isfinite(ref_cp)
     assert np.array_equal(cp[finite], ref_cp[finite])
-    assert np.all(np.isnan(prop[3])) and acc[3] == 0
     with np.errstate(over="ignore"):
-        expect = np.where(np.isfinite(cp), u < np.exp(-0.5 * (cp - chi[:20])), False)
+        expect = np.where(np.isfinite(cp), u[:, 0] < np.exp(-0.5 * (cp - chi[:20])), False)
     assert np.array_equal(acc.astype(bool), expect)
     assert np.array_equal(st[:20][~expect], states[:20][~expect])
     assert np.array_equal(st[:20][expect], prop[expect])
     assert np.array_equal(st[20:], states[20:])
+    for pfirst, pcount in ((10, 20), (30, 20), (20, 1), (-1, 5)):
+        with pytest.raises(ValueError):
+            oracle_mod.demcmc_step(states, chi, t, v, sig, n_pl, 0, 20, pfirst, pcount, 0.7,
+                                   np.full(6, 1e-3), z, u)
 
 
 def test_demcmc_samples_the_linear_gaussian_posterior(oracle_mod):
@@ -504,16 +556,12 @@ def test_demcmc_samples_the_linear_gaussian_posterior(oracle_mod):
     gamma = 2.38 / np.sqrt(2 * 2)
     half = n // 2
     samples = []
+    scale = np.array([0.0, 1e-5, 0.0, 0.0, 0.0, 1e-5])
     for gen in range(1500):
         for first, other in ((0, half), (half, 0)):
-            partners = np.stack([other + rng.integers(0, half, half),
-                                 other + rng.integers(0, half, half)], axis=1)
-            eps = np.zeros((half, 6))
-            eps[:, 1] = 1e-4 * rng.standard_normal(half)
-            eps[:, 5] = 1e-4 * rng.standard_normal(half)
-            states, chi, _, _, _ = oracle_mod.demcmc_step(states, chi, t, v, sig, 1, first, half,
-                                                          gamma, partners, eps,
-                                                          rng.uniform(0, 1, half))
+            states, chi, _, _, _ = oracle_mod.demcmc_step(
+                states, chi, t, v, sig, 1, first, half, other, half, gamma, scale,
+                rng.standard_normal((half, 6)), rng.uniform(0, 1, (half, 3)))
         if gen >= 300:
             samples.append(states[:, [1, 5]].copy())
     s = np.concatenate(samples)

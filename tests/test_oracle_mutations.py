@@ -47,10 +47,13 @@ MUTATIONS = [
     ("nll log term dropped", "0.5 * (wk * r * r + log(KCO_TWO_PI * var))", "0.5 * (wk * r * r)"),
     ("nll jitter gradient sign", "sj * wk * (1.0 - wk * r * r)", "sj * wk * (1.0 + wk * r * r)"),
     ("nll gradient factor", "double a = wk * r;", "double a = 2.0 * wk * r;"),
-    ("DE-MC acceptance sign", "log(u[c]) < -0.5 * (chi2_prop[c] - chi2[i])",
-     "log(u[c]) < 0.5 * (chi2_prop[c] - chi2[i])"),
-    ("DE-MC gamma dropped", "x = (states[i * n_par + p] + gamma * d) + eps[c * n_par + p];",
-     "x = (states[i * n_par + p] + d) + eps[c * n_par + p];"),
+    ("DE-MC acceptance sign", "log(u[3 * c]) < -0.5 * (chi2_prop[c] - chi2[i])",
+     "log(u[3 * c]) < 0.5 * (chi2_prop[c] - chi2[i])"),
+    ("DE-MC gamma dropped", "proposals[c * n_par + p] = (xi + gamma * d) + eps;",
+     "proposals[c * n_par + p] = (xi + d) + eps;"),
+    ("DE-MC partners may coincide", "if (k2 >= k1) k2 += 1;", "if (k2 > k1) k2 += 1;"),
+    ("DE-MC perturbation not relative", "double eps = (eps_scale[p] * fabs(xi)) * z[c * n_par + p];",
+     "double eps = eps_scale[p] * z[c * n_par + p];"),
     ("Gauss-Newton weight dropped", "kco_sum_add(&acc[i++], wk * J[p] * J[q]);",
      "kco_sum_add(&acc[i++], J[p] * J[q]);"),
     ("Gauss-Newton index", "kco_sum_add(&acc[i++], wk * J[p] * J[q]);",
