@@ -110,9 +110,12 @@ def hold_gpu(stream, host_us):
     the step's work already queued, so the CUDA events bracket GPU work, not
     host-side launch latency (or a host stalled by the clock sampler)."""
     import torch
+    sleep = getattr(torch.cuda, "_sleep", None)
+    if sleep is None:            # not in this torch build: time without the hold
+        return
     cycles = int(max(2000.0, host_us) * sm_mhz_for_peaks())
     with torch.cuda.stream(stream):
-        torch.cuda._sleep(cycles)
+        sleep(cycles)
 
 
 def kepler_throughput(kc, dev, stream, n=1 << 24):
