@@ -412,8 +412,11 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
 // accumulators.  Mixed path: that update is a rank-32 dense contraction per
 // batch on the tensor cores (mma.sync m16n8k8, TF32 inputs in the three-
 // product split hi*hi + hi*lo + lo*hi, FP32 accumulation), only the tiles
-// on or above the diagonal.  FP64 path: FMAs on the FP64 pipe, the packed
-// upper-triangle entries spread over the lanes.
+// on or above the diagonal.  Each element of U is split into its (hi, lo)
+// pair once, when its row is written; since B = U and A = U^T cover the
+// same elements, the B fragments are halves of the A fragments.  FP64 path:
+// FMAs on the FP64 pipe, the packed upper-triangle entries spread over the
+// lanes.
 
 constexpr int kGnWarps = 4;      // mixed: systems (warps) per CTA
 constexpr int kGnWarpsD = 2;     // FP64
@@ -422,11 +425,10 @@ constexpr int kGnObsTile = 256;
 __host__ __device__ constexpr int gn_np(int J) { return 5 * J + 1; }
 __host__ __device__ constexpr int gn_mt(int J) { return (gn_np(J) + 15) / 16; }
 __host__ __device__ constexpr int gn_nt(int J) { return (gn_np(J) + 7) / 8; }
-// Row stride of U (floats): covers the tiled width and is 8 mod 32, so the
-// fragment loads of a warp (8 rows x 4 columns of a tile) hit 32 banks.
-__host__ __device__ constexpr int gn_row(int J) {
-  return ((gn_mt(J) * 16 > gn_nt(J) * 8 ? gn_mt(J) * 16 : gn_nt(J) * 8) + 23) / 32 * 32 + 8;
-}
+// Row stride of U in (hi, lo) pairs: the tiled width 16 MT (>= 8 NT) plus 4,
+// which is 4 mod 16 pairs, so that with the column swizzle below the 64-bit
+// row writes and fragment loads of each half-warp hit 32 different banks.
+__host__ __device__ constexpr int gn_row2(int J) { return gn_mt(J) * 16 + 4; }
 
 struct GnMixedLayout {
   size_t pl, gam, obs, w, u, total;
@@ -435,8 +437,8 @@ struct GnMixedLayout {
     gam = pl + sizeof(GradPlanetF) * kGnWarps * J;
     obs = align_up(gam + sizeof(float) * kGnWarps, 16);
     w = obs + sizeof(float4) * obs_tile;
-    u = align_up(w + sizeof(float2) * obs_tile, 16);
-    total = align_up(u + sizeof(float) * kGnWarps * 32 * gn_row(J), 16);
+    u = align_up(w + sizeof(float4) * obs_tile, 16);
+    total = align_up(u + sizeof(float2) * kGnWarps * 32 * gn_row2(J), 16);
   }
 };
 
@@ -458,16 +460,16 @@ __device__ __forceinline__ int tri_index(int np, int p, int q) {
   return p * np - (p * (p - 1)) / 2 + (q - p);
 }
 
-__device__ __forceinline__ unsigned tf32_rna(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// x = hi + lo with both TF32 (lo carries the next 11 bits of x).
-__device__ __forceinline__ void tf32_split(float x, unsigned &hi, unsigned &lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
+// x = hi + lo + err with hi, lo TF32 numbers (FP32 with the 13 low
+// significand bits zero): hi keeps the leading 11 significant bits of x, so
+// |x - hi| < 2^-10 |x| and x - hi is exact in FP32; lo keeps the leading 11
+// bits of x - hi, so |err| < 2^-20 |x|.  A product from the three terms
+// hi*hi + hi*lo + lo*hi is then within about 3 * 2^-20 of the FP32 one.
+__device__ __forceinline__ float2 tf32_pair(float x) {
+  constexpr unsigned kTf32Mask = 0xffffe000u;
+  const float hi = __uint_as_float(__float_as_uint(x) & kTf32Mask);
+  const float lo = __uint_as_float(__float_as_uint(__fsub_rn(x, hi)) & kTf32Mask);
+  return make_float2(hi, lo);
 }
 
 // D = A B + D for one 16 x 8 tile, A 16 x 8 (row), B 8 x 8 (col), TF32.
@@ -484,15 +486,15 @@ template <int J>
 __global__ void __launch_bounds__(kGnWarps * 32)
 gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__ grad_out,
                 float *__restrict__ jtj_out) {
-  constexpr int NP = gn_np(J), MT = gn_mt(J), NT = gn_nt(J), ROW = gn_row(J);
+  constexpr int NP = gn_np(J), MT = gn_mt(J), NT = gn_nt(J), ROW2 = gn_row2(J);
   constexpr int NTRI = NP * (NP + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   const GnMixedLayout L(J, kGnObsTile);
   GradPlanetF *pl_s = reinterpret_cast<GradPlanetF *>(smem + L.pl);
   float *gam_s = reinterpret_cast<float *>(smem + L.gam);
   float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
-  float2 *wt_s = reinterpret_cast<float2 *>(smem + L.w);
-  float *u_all = reinterpret_cast<float *>(smem + L.u);
+  float4 *wt_s = reinterpret_cast<float4 *>(smem + L.w);
+  float2 *u_all = reinterpret_cast<float2 *>(smem + L.u);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int block = kGnWarps * 32;
@@ -511,14 +513,16 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
   }
   for (int i = tid; i < kGnWarps; i += block)
     gam_s[i] = sys0 + i < a.n_sys ? d2f(system_gamma_g(a.params + (sys0 + i) * NP, J)) : 0.0f;
-  for (int i = tid; i < kGnWarps * 32 * ROW; i += block) u_all[i] = 0.0f;   // incl. padding
+  for (int i = tid; i < kGnWarps * 32 * ROW2; i += block)
+    u_all[i] = make_float2(0.0f, 0.0f);                           // incl. padding
 
-  // Element (row r, column c) of U sits at r * ROW + (c ^ ((r >> 2) & 7)):
-  // with ROW = 8 mod 32 both the row writes (one row per lane) and the
-  // fragment loads touch 32 different banks.
-  float *u = u_all + warp * 32 * ROW;
+  // The (hi, lo) pair of element (row r, column c) of U sits at
+  // r * ROW2 + (c ^ ((r >> 2) & 3)): with ROW2 = 4 mod 16 both the row writes
+  // (one row per lane) and the fragment loads touch 32 different banks in
+  // each half-warp.
+  float2 *u = u_all + warp * 32 * ROW2;
   const int gid = lane >> 2, tig = lane & 3;
-  const int sw_row = (lane >> 2) & 7;
+  const int sw_row = (lane >> 2) & 3;
   Kahan acc = {0.0f, 0.0f};
   Kahan gP[J];
   float g[NP];
@@ -544,7 +548,8 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
       obs_s[k] = make_float4(th, tl, vh, vl);
       const float sg = d2f(a.sigma[k0 + k]);
       const float var = __fmaf_rn(sg, sg, jit2);
-      wt_s[k] = make_float2(var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000), th + dref_f);
+      const float wk = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+      wt_s[k] = make_float4(wk, th + dref_f, sqrtf(wk), 0.0f);
     }
     __syncthreads();
     const float gam = gam_s[warp];
@@ -556,7 +561,7 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
       for (int i = 0; i < NP; ++i) urow[i] = 0.0f;
       if (k < nk) {
         const float4 o = obs_s[k];
-        const float2 wt = wt_s[k];
+        const float4 wt = wt_s[k];
         float sEj[J], cEj[J];
         Kahan V = {0.0f, 0.0f};
 #pragma unroll
@@ -569,7 +574,7 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
         const float wk = wt.x, wr = wk * r, a2 = 2.0f * wr;
         kahan_add(acc, wr * r);
-        const float sw = sqrtf(wk);
+        const float sw = wt.z;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const GradPlanetF qj = q[j];
@@ -593,27 +598,30 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         urow[5 * J] = sw;
       }
 #pragma unroll
-      for (int i = 0; i < NP; ++i) u[lane * ROW + (i ^ sw_row)] = urow[i];
+      for (int i = 0; i < NP; ++i) u[lane * ROW2 + (i ^ sw_row)] = tf32_pair(urow[i]);
       __syncwarp();
       // H += U^T U: k-steps of 8 rows; A = U^T (16 x 8 per m-tile), B = U (8 x 8 per n-tile)
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const float *r0 = u + (ks * 8 + tig) * ROW;
-        const float *r1 = r0 + 4 * ROW;
-        const int g0 = gid ^ ((2 * ks) & 7), g1 = gid ^ ((2 * ks + 1) & 7);   // row swizzles
+        const float2 *r0 = u + (ks * 8 + tig) * ROW2;
+        const float2 *r1 = r0 + 4 * ROW2;
+        const int g0 = gid ^ ((2 * ks) & 3), g1 = gid ^ ((2 * ks + 1) & 3);   // row swizzles
         unsigned ah[MT][4], al[MT][4];
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
-          tf32_split(r0[16 * mt + g0], ah[mt][0], al[mt][0]);
-          tf32_split(r0[16 * mt + g0 + 8], ah[mt][1], al[mt][1]);
-          tf32_split(r1[16 * mt + g1], ah[mt][2], al[mt][2]);
-          tf32_split(r1[16 * mt + g1 + 8], ah[mt][3], al[mt][3]);
+          const float2 x[4] = {r0[16 * mt + g0], r0[16 * mt + g0 + 8], r1[16 * mt + g1],
+                               r1[16 * mt + g1 + 8]};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            ah[mt][i] = __float_as_uint(x[i].x);
+            al[mt][i] = __float_as_uint(x[i].y);
+          }
         }
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          unsigned bh[2], bl[2];
-          tf32_split(r0[8 * nt + g0], bh[0], bl[0]);
-          tf32_split(r1[8 * nt + g1], bh[1], bl[1]);
+          // columns 8 nt .. 8 nt + 7 of U: half h of m-tile nt / 2
+          const int m = nt >> 1, h = nt & 1;
+          const unsigned bh[2] = {ah[m][h], ah[m][2 + h]}, bl[2] = {al[m][h], al[m][2 + h]};
 #pragma unroll
           for (int mt = 0; mt < MT; ++mt) {
             if (8 * nt + 7 >= 16 * mt) {        // a tile on or above the diagonal

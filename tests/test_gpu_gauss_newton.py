@@ -5,8 +5,8 @@ H entries are compared on the correlation scale: |dH_pq| / sqrt(H_pp H_qq)
 (an entry that cancels to ~0 cannot carry relative accuracy).  Tolerances:
 the mixed path forms J_k in FP32 (relative error ~1e-6, the period column
 ~1e-5 through (t - t0)/P^2) and the update on the tensor cores with the
-two-term TF32 split (~5e-7 per product), so 1e-4 leaves an order of
-magnitude; FP64: 1e-10."""
+two-term TF32 split by truncation (< 3 * 2^-20 ~ 3e-6 per product), so 1e-4
+leaves an order of magnitude; FP64: 1e-10."""
 import numpy as np
 import pytest
 import torch
