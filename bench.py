@@ -82,12 +82,15 @@ def gn_tensor_flops_per_obs(n_pl: int) -> float:
 
 
 # FP64 path, FP64 FLOPs per planet-observation evaluation (FMA = 2), from its
-# algorithm: mean anomaly 12, table-driven sin/cos 22 (reduction 4, b^2 1,
+# algorithm: mean anomaly 10 (the two roundings to an integer counted as one
+# each; the low part of the phase scaled in single precision), table-driven
+# sin/cos 22 (reduction 4, b^2 1,
 # sin b 5, cos b 6, table combination 6), Halley step with a one-Newton-step
-# reciprocal 16, last-step update 10, velocity with a one-Newton-step
-# reciprocal 12, accumulation 2 (the FP32 presolve, the single-precision
-# reciprocal seeds and the per-CTA table are not counted).
-F64_FLOPS_PER_EVAL = 12 + 22 + 16 + 10 + 12 + 2
+# reciprocal 13, last-step update 8, velocity with a one-Newton-step
+# reciprocal and the planet sum's addition 11 (the FP32 presolve, the
+# single-precision correction terms and reciprocal seeds and the per-CTA
+# table are not counted).
+F64_FLOPS_PER_EVAL = 10 + 22 + 13 + 8 + 11
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of

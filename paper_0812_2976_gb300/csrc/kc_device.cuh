@@ -386,26 +386,32 @@ __device__ __forceinline__ void sincos_tab(double x, float xf, const double2 *ta
   c = fma(sc.y, cb, -(sc.x * sb));
 }
 
-// Halley's step -2 f f' / (2 f'^2 - f f'') for f(E) = E - e sin E - M, in
-// double: 16 FP64 FLOPs against 26 for Danby's quartic step.  From the
-// single-precision solution (within 7e-7 of the root for e <= kEccFast,
-// M rounded to float included) its cubic error is below double rounding
-// (5e-16 |f'| at worst in a float emulation of the seed over 4e5 (M, e)).
+// Halley's step -2 f f' / (2 f'^2 - f f'') = -f f' / (f'^2 - f e sin E / 2)
+// for f(E) = E - e sin E - M, in double: 8 FP64 operations (13 FLOPs)
+// against 26 FLOPs for Danby's quartic step.  From the single-precision
+// solution (within 7e-7 of the root for e <= kEccFast, M rounded to float
+// included) its cubic error is below double rounding (5e-16 |f'| at worst in
+// a float emulation of the seed over 4e5 (M, e)).  f = (E - M) - e sin E
+// takes one rounding (of E - M) with the product inside the FMA.  The term
+// h = f e sin E / 2 is below 4e-7 f' (|f| ~ f' |E - root| < 7e-7 f'), at most
+// 7e-6 of f'^2 (f' >= 1 - e >= 0.05): formed in single precision from
+// ef = e and sf, the seed's sine (within 1e-6 of sin E), its error moves the
+// step by less than 1e-11 of itself.
 __device__ __forceinline__ double halley_delta_f64(double E, double M, double e, double s,
-                                                   double c) {
-  const double es = e * s;
-  const double f = (E - M) - es;
+                                                   double c, float ef, float sf) {
+  const double f = fma(-e, s, E - M);
   const double f1 = fma(-e, c, 1.0);
-  const double num = f * f1;
-  return -(num + num) * rcp_f64(fma(f1 + f1, f1, -(f * es)));
+  const double h = f2d(0.5f * d2f(f) * (ef * sf));
+  return -(f * f1) * rcp_f64(fma(f1, f1, -h));
 }
 
 // Kepler's equation in double precision.  The single-precision solve
 // (kepler_f32) seeds one double-precision Halley step, which lands on the
 // double root; sin/cos of the result follow by angle addition to second
 // order in that last step.  HI and e > kEccFast: two quartic steps in
-// double instead (the seed's error grows like 1e-7 / (1 - e cos E)).  The single-precision work costs little here: one
-// FP64 instruction takes as long on GB300's FP64 pipe as ~76 FP32 issues.
+// double instead (the seed's error grows like 1e-7 / (1 - e cos E)).  The
+// single-precision work costs little here: one FP64 instruction takes as
+// long on GB300's FP64 pipe as ~76 FP32 issues.
 // With a table (tab != nullptr, sincos_table_build), sin/cos come from
 // sincos_tab.
 template <bool HI = true>
@@ -430,9 +436,12 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
       sincos_f64(E, s, c);
     d = danby_delta_f64(E, M, e, s, c);
   } else {
-    d = halley_delta_f64(E, M, e, s, c);
+    d = halley_delta_f64(E, M, e, s, c, ef, sf);
   }
-  const double hd2 = 0.5 * d * d;
+  // d^2/2 < 2.5e-13 (|d| < 7e-7 in the Halley step, far smaller in the
+  // second quartic step): single precision leaves it below 1e-19 absolute
+  const float df = d2f(d);
+  const double hd2 = f2d(0.5f * df * df);
   sE = fma(d, c, fma(-hd2, s, s));
   cE = fma(-d, s, fma(-hd2, c, c));
   return E + d;
@@ -444,15 +453,16 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
 // at time t is (t - t_ref) * (inv_P + inv_P_lo) + c0 cycles (Eqs. 4/6 with
 // the epoch moved from t0 to a reference time t_ref of the observations):
 // inv_P + inv_P_lo = 1/P to ~1e-32 relative, and c0 in [-1/2, 1/2] holds
-// frac((t_ref - t0)/P) + M0/(2 pi).  A, B, C give the velocity in the
+// frac((t_ref - t0)/P) + M0/(2 pi).  A and B give the velocity in the
 // eccentric-anomaly form of Eq. 3:
-//   v = [A (cos E - e) - B sin E] / (1 - e cos E) + C,
-//   A = K cos w, B = K sqrt((1-e)(1+e)) sin w, C = K e cos w,
+//   v = (A cos E - B sin E) / (1 - e cos E),
+//   A = K cos w (1-e)(1+e), B = K sqrt((1-e)(1+e)) sin w,
 // which equals K [cos(w + f) + e cos w] with cos f = (cos E - e)/D,
-// sin f = sqrt(1-e^2) sin E / D, D = 1 - e cos E; (1-e)(1+e) limits
-// round-off for small e, as Sec. 4.4 advises.
+// sin f = sqrt(1-e^2) sin E / D, D = 1 - e cos E (the e cos w term and the
+// -e of cos f combine: (cos E - e) + e D = (1 - e^2) cos E); (1-e)(1+e)
+// limits round-off for small e, as Sec. 4.4 advises.
 struct PlanetD {
-  double inv_P, inv_P_lo, c0, e, A, B, C, beta;
+  double inv_P, inv_P_lo, c0, e, A, B, beta;
 };
 
 // Single-precision constants of one planet for the mixed path: 1/P and the
@@ -519,10 +529,10 @@ __device__ __forceinline__ PlanetD planet_setup_f64(const double *p, double dref
   q.e = e;
   double sw, cw;
   sincos(w, &sw, &cw);
-  q.beta = sqrt((1.0 - e) * (1.0 + e));
-  q.A = K * cw;
+  const double b2 = (1.0 - e) * (1.0 + e);
+  q.beta = sqrt(b2);
+  q.A = K * cw * b2;
   q.B = K * q.beta * sw;
-  q.C = K * e * cw;
   return q;
 }
 
@@ -721,15 +731,20 @@ __device__ __forceinline__ float mean_anomaly_single(float tau, const PlanetF &q
   return x * kTwoPiF;
 }
 
+// p = tau/P keeps its exact FMA remainder pe; the low part
+// lo = pe + tau inv_P_lo, |lo| <= ulp(p)/2 + 2^-52 p, enters the last FMA
+// already scaled by 2 pi in single precision: below 2e-12 cycles for
+// p < 6000 (a 6000-day span at P >= 1 d), so the float error stays under
+// 1e-17 rad (5e-16 rad at p = 1e6).  p - rint(p) is exact, adding c0
+// rounds once (error below 1.2e-16 cycles) and u - rint(u) is exact, so M
+// lies in [-pi, pi] up to 2 pi |lo|.
 __device__ __forceinline__ double mean_anomaly_f64(double tau, const PlanetD &q) {
   const double p = __dmul_rn(tau, q.inv_P);
   const double pe = fma(tau, q.inv_P, -p);
-  const double lo = fma(tau, q.inv_P_lo, pe);
-  // p - rint(p) is exact; the two additions round (|u| < 1.1, error below
-  // 2.3e-16 cycles) and one wrap brings u back to [-1/2, 1/2]
-  double u = ((p - rint(p)) + q.c0) + lo;
+  const float lo2pi = __fmaf_rn(d2f(tau), d2f(q.inv_P_lo), d2f(pe)) * kTwoPiF;
+  double u = (p - rint(p)) + q.c0;
   u -= rint(u);
-  return u * kTwoPi;
+  return fma(u, kTwoPi, f2d(lo2pi));
 }
 
 // ------------------------------------------------ velocity (Eq. 3)
@@ -740,9 +755,11 @@ __device__ __forceinline__ float velocity_mixed(const PlanetF &q, float sE, floa
   return __fmaf_rn(num, rcp_fast(D), q.C);
 }
 
-__device__ __forceinline__ double velocity_f64(const PlanetD &q, double sE, double cE) {
+// V + v for one planet (the planet sum's addition inside the last FMA).
+__device__ __forceinline__ double velocity_add_f64(const PlanetD &q, double sE, double cE,
+                                                   double V) {
   const double D = fma(-q.e, cE, 1.0);
-  return fma(fma(q.A, cE - q.e, -(q.B * sE)), rcp_f64(D), q.C);
+  return fma(fma(q.A, cE, -(q.B * sE)), rcp_f64(D), V);
 }
 
 // ------------------------------------------------ warp helpers

@@ -473,7 +473,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   for (int i = setup_slot(tid, block >> 5); i < ST * J; i += block) {
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
-    PlanetD q = {0, 0, 0, 0, 0, 0, 0, 0};
+    PlanetD q = {};
     if (s < a.n_sys) q = planet_setup_f64(a.params + s * npar + 5 * j, dref);
     pl_s[i] = q;
   }
@@ -516,7 +516,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
           double sE, cE;
           const double E = kepler_f64<HI>(M, p.e, sE, cE, tab_s);
           if (want_resid) rmax = fmax(rmax, fabs((E - M) - p.e * sE));
-          V += velocity_f64(p, sE, cE);
+          V = velocity_add_f64(p, sE, cE, V);
         }
         const double r = V - o.v;
         if (NLL) {
@@ -578,7 +578,7 @@ __global__ void rv_predict_kernel(const double *__restrict__ params, const doubl
       const double M = mean_anomaly_f64(t[k] - t_ref, q);
       double sE, cE;
       kepler_f64(M, q.e, sE, cE);
-      V += velocity_f64(q, sE, cE);
+      V = velocity_add_f64(q, sE, cE, V);
     }
     v_out[i] = V;
   }

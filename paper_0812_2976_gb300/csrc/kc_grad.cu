@@ -352,7 +352,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
           const PlanetD p = q[j].base;
           const double M = mean_anomaly_f64(o.tau, p);
           kepler_f64<HI>(M, p.e, sEj[j], cEj[j], tab_s);
-          V += velocity_f64(p, sEj[j], cEj[j]);
+          V = velocity_add_f64(p, sEj[j], cEj[j], V);
         }
         const double r = V - o.v;
         double a2;
@@ -751,7 +751,7 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
             const PlanetD p = q[j].base;
             const double M = mean_anomaly_f64(o.tau, p);
             kepler_f64<HI>(M, p.e, sEj[j], cEj[j]);
-            V += velocity_f64(p, sEj[j], cEj[j]);
+            V = velocity_add_f64(p, sEj[j], cEj[j], V);
           }
         });
         const double r = V - o.v;

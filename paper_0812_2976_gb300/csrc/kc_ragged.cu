@@ -113,7 +113,7 @@ __global__ void predict_ragged_kernel(const double *__restrict__ params,
         const PlanetD q = planet_setup_f64(p + 5 * j, tr - t0);
         double sE, cE;
         kepler_f64(mean_anomaly_f64(t[k] - tr, q), q.e, sE, cE);
-        V += velocity_f64(q, sE, cE);
+        V = velocity_add_f64(q, sE, cE, V);
       }
       v_out[k] = V;
     }
@@ -291,7 +291,7 @@ __device__ __forceinline__ void body_f64(const RPlanetD *pl, double gam, const O
       const PlanetD q = pl[j].base;
       const double M = mean_anomaly_f64(o.tau, q);
       kepler_f64<HI>(M, q.e, sEj[j], cEj[j]);
-      V += velocity_f64(q, sEj[j], cEj[j]);
+      V = velocity_add_f64(q, sEj[j], cEj[j], V);
     }
     const double r = V - o.v;
     acc = fma(o.w * r, r, acc);
