@@ -433,17 +433,24 @@ kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains, int32_t n
     return fail(KC_ERR_ARG, "%s: pointer not 8-byte aligned", fn);
   kc_status st = check_uniform(states, t, v_obs, sigma, count, n_pl, n_obs, chi2_prop, fn);
   if (st != KC_OK) return st;
+  if (!std::isfinite(t0) || !std::isfinite(jitter))
+    return fail(KC_ERR_ARG, "%s: t0 and jitter must be finite", fn);
   const int npar = 5 * n_pl + 1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = kc::launch_demcmc_propose(states, npar, first, count, partner_first,
                                             partner_count, gamma, eps_scale, z, u, proposals, s);
   if (e != cudaSuccess) return cuda_status(e, "kc_demcmc_step: propose");
-  st = kc_chi2_eval_ex(proposals, t, v_obs, sigma, count, n_pl, n_obs, t0, jitter, mode,
-                       chi2_prop, nullptr, stream);
-  if (st != KC_OK) return st;
-  e = kc::launch_demcmc_accept(states, chi2, proposals, chi2_prop, first, count, npar, u,
-                               mode == KC_FP64, accepted, s);
-  return cuda_status(e, "kc_demcmc_step: accept");
+  // chi2 of the proposals with the Metropolis step in the kernel's epilogue
+  UniformArgs a{proposals, t,   v_obs, sigma, count, n_pl, n_obs, t0, jitter * jitter,
+                kc::invalid_counter(), kc::DemcAccept{states, chi2, u, accepted, first}};
+  if (mode == KC_FP64) {
+    const Tile tile = kc::choose_tile(Kind::Chi2F64, count, n_pl, n_obs);
+    e = kc::launch_chi2_f64(a, tile, static_cast<double *>(chi2_prop), nullptr, s);
+  } else {
+    const Tile tile = kc::choose_tile(Kind::Chi2Mixed, count, n_pl, n_obs);
+    e = kc::launch_chi2_mixed(a, tile, static_cast<float *>(chi2_prop), nullptr, s);
+  }
+  return cuda_status(e, "kc_demcmc_step");
 }
 
 kc_status kc_rv_predict(const double *params, const double *t, int64_t n_sys, int32_t n_pl,

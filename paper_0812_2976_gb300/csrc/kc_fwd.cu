@@ -103,6 +103,23 @@ struct MixedPrep {
   const float *w;        // [n_obs]
 };
 
+// The Metropolis decision of DE-MC in the epilogue of the chi2 kernel that
+// has just evaluated proposal s (demcmc_accept_kernel's rule and
+// arithmetic, applied to the value the kernel stores).
+template <typename T>
+__device__ __forceinline__ void demc_accept(const UniformArgs &a, int64_t s, int npar, T value) {
+  const DemcAccept &d = a.demc;
+  const int64_t i = d.first + s;
+  T *chi2 = static_cast<T *>(d.chi2);
+  const double delta = (double)value - (double)chi2[i];
+  const bool acc = log(d.u[3 * s]) < -0.5 * delta;      // false when delta is NaN
+  if (acc) {
+    for (int p = 0; p < npar; ++p) d.states[i * npar + p] = a.params[s * npar + p];
+    chi2[i] = value;
+  }
+  if (d.accepted) d.accepted[s] = acc ? 1 : 0;
+}
+
 // PRE = false: each CTA computes its planets' constants (FP64) and converts
 // the observations itself.  PRE = true (split variant): both come from
 // prep_mixed_kernel, launched just before with programmatic dependent
@@ -318,6 +335,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     out[s] = value;
     note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = rmax;
+    if (!NLL && !SINGLE && a.demc.states) demc_accept(a, s, npar, value);
   }
 }
 
@@ -552,9 +570,11 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
   }
   if (c == 0 && s < a.n_sys) {
     const double poison = 0.0 * gam_s[sl] + (NLL ? 0.0 * s2_s[sl] : 0.0);
-    out[s] = NLL ? 0.5 * (acc + a.n_obs * kLn2Pi) + poison : acc + poison;
-    note_invalid(a.invalid, out[s]);
+    const double value = NLL ? 0.5 * (acc + a.n_obs * kLn2Pi) + poison : acc + poison;
+    out[s] = value;
+    note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = (float)rmax;
+    if (!NLL && a.demc.states) demc_accept(a, s, 5 * J + 1, value);
   }
 }
 
@@ -787,6 +807,11 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile_in, float *
         scratch_alloc(&scratch, mixed_scratch_bytes(a.n_sys, a.n_pl, a.n_obs, tile), st);
     if (err != cudaSuccess) return err;
     err = launch_chi2_mixed_prepared(a, tile, scratch, out, resid, st);
+    // the chunked two-pass variant has no per-system epilogue: a DE-MC
+    // Metropolis step runs as its own kernel after it
+    if (err == cudaSuccess && tile.split == 2 && a.demc.states)
+      err = launch_demcmc_accept(a.demc.states, a.demc.chi2, a.params, out, a.demc.first,
+                                 a.n_sys, 5 * a.n_pl + 1, a.demc.u, false, a.demc.accepted, st);
     cudaError_t err2 = cudaFreeAsync(scratch, st);
     return err != cudaSuccess ? err : err2;
   }

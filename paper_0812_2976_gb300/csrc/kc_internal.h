@@ -20,6 +20,19 @@ struct Tile {
   int split = 0;   // mixed chi2 only: 1, 2 = two-pass variants (see kc_fwd.cu)
 };
 
+// Metropolis step of DE-MC carried by a chi2 launch: the batch's systems
+// are proposals for chains first .. first + n_sys - 1, and each system's
+// chi2 is compared with its chain's (accept iff ln u[3 c] < -(chi2* -
+// chi2)/2), the accepted proposal copied over the chain's state.  states
+// == NULL: a plain evaluation.
+struct DemcAccept {
+  double *states;          // [n_chains][5 n_pl + 1]
+  void *chi2;              // [n_chains], float (mixed) or double (FP64)
+  const double *u;         // [n_sys][3]
+  int32_t *accepted;       // [n_sys] or NULL
+  int64_t first;
+};
+
 struct UniformArgs {
   const double *params;
   const double *t;
@@ -33,6 +46,7 @@ struct UniformArgs {
   // device counter of systems whose result is NaN (invalid inputs); may be
   // NULL (kc_last_device_error reads it)
   unsigned long long *invalid;
+  DemcAccept demc = {};
 };
 
 // The library's per-device invalid-system counter (kc_api.cu); NULL if its

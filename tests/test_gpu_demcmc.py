@@ -25,8 +25,26 @@ def dev(a, dtype=torch.float64):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-@pytest.mark.parametrize("mode,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
-def test_step_matches_oracle(kc, oracle_mod, mode, tol):
+@pytest.mark.parametrize("mode,tol,tile", [
+    ("fp64", 1e-12, None), ("mixed", 1e-5, None),
+    ("mixed", 1e-5, (16, 128, 1)),      # prepared two-pass: accept in the main kernel
+    ("mixed", 1e-5, (64, 64, 2)),       # chunked two-pass: accept as its own kernel
+])
+def test_step_matches_oracle(kc, oracle_mod, mode, tol, tile):
+    """The Metropolis step runs in the chi2 kernel's epilogue, or after the
+    chunked two-pass variant as its own kernel; every launch shape gives
+    the oracle's step."""
+    if tile is not None:
+        kc.kc_set_tile("chi2", mode, 256, 4, 256, tile)
+        assert kc.kc_get_tile("chi2", mode, 256, 4, 256) == tile
+    try:
+        _step_matches_oracle(kc, oracle_mod, mode, tol)
+    finally:
+        if tile is not None:
+            kc.kc_set_tile("chi2", mode, 256, 4, 256, None)
+
+
+def _step_matches_oracle(kc, oracle_mod, mode, tol):
     from paper_0812_2976_gb300 import synth
     w = synth.uniform(1, n_sys=512)
     v = oracle_mod.predict(w.truth, w.t, w.n_pl)[0] + w.noise
