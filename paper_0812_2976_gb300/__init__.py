@@ -526,7 +526,9 @@ class DEMCMC:
         self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
         self._acc = torch.empty(n, dtype=torch.int32, device=dev)
         self.generation = 0
-        self._n_acc = torch.zeros((), dtype=torch.int64, device=dev)   # no host syncs
+        # acceptances per chain, summed only when read: one element-wise add
+        # a generation (a reduction and an add were two launches)
+        self._n_acc = torch.zeros(n, dtype=torch.int64, device=dev)
         self.proposed = 0
 
     def _draws(self):
@@ -550,7 +552,7 @@ class DEMCMC:
                            gamma, self.eps_scale, z[first:first + h], u[first:first + h],
                            self._prop, self._cp, self._acc[first:first + h], self.t0,
                            self.jitter, self.mode)
-        self._n_acc += self._acc.sum()
+        self._n_acc += self._acc
 
     def _gamma(self) -> float:
         hop = self.hop_every and (self.generation + 1) % self.hop_every == 0
@@ -595,7 +597,7 @@ class DEMCMC:
     @property
     def acceptance(self) -> float:
         """Fraction of accepted proposals so far (synchronises)."""
-        return int(self._n_acc) / max(self.proposed, 1)
+        return int(self._n_acc.sum()) / max(self.proposed, 1)
 
 
 class _Chi2Fn(torch.autograd.Function):
