@@ -230,7 +230,7 @@ def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):
     import torch
     mc = kc.DEMCMC(P, T, V, S, mode="mixed", eps_scale=1e-6, hop_every=0, seed=5,
                    autotune=True)
-    mc.run(3)                                        # includes the graph capture
+    mc.run(4)        # one eager generation, one to align the draw buffers, one captured pair
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     hold_gpu(torch.cuda.current_stream(dev), generations * 300.0)

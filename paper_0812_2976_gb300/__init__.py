@@ -494,7 +494,9 @@ class DEMCMC:
     x^2) per parameter (``eps_scale`` a number or one value per parameter; 0
     together with equal values in every chain holds a parameter fixed).
     Random draws come from a torch generator on the device; the step itself
-    is kc_demcmc_step.  ``autotune``: time the chi2 tiles once for the size
+    is kc_demcmc_step.  The draws do not depend on the chains, so those of
+    generation g + 1 are made on a side stream while generation g steps
+    (two buffers), in the same order as one generation after another.  ``autotune``: time the chi2 tiles once for the size
     class of half the population (what each step evaluates) and keep the
     fastest; off by default, since the pick depends on timing and so can
     change the summation order from one run to the next."""
@@ -530,22 +532,33 @@ class DEMCMC:
         # a generation (a reduction and an add were two launches)
         self._n_acc = torch.zeros(n, dtype=torch.int64, device=dev)
         self.proposed = 0
+        self._graph = None
+        self._side = torch.cuda.Stream(device=dev)
+        self._z32 = torch.empty((n, self.npar), dtype=torch.float32, device=dev)
+        self._z = [torch.empty((n, self.npar), dtype=torch.float64, device=dev) for _ in (0, 1)]
+        self._u = [torch.empty((n, 3), dtype=torch.float64, device=dev) for _ in (0, 1)]
+        self._buf = 0                    # the buffer holding the next generation's draws
+        self._draws(0)
 
-    def _draws(self):
-        """Every random number of one generation (both halves): standard
-        normal perturbations and three uniforms per chain (acceptance, two
-        partners); the step kernels scale and map them.  The normals are
-        drawn in single precision (a perturbation needs no more; double
-        precision normals cost 27 us a generation on this GPU, these 15) and
-        widened."""
-        h, dev = self.half, self.states.device
-        z = torch.randn((2 * h, self.npar), generator=self.gen, dtype=torch.float32,
-                        device=dev).double()
-        u = torch.rand((2 * h, 3), generator=self.gen, dtype=torch.float64, device=dev)
-        return z, u
+    def _draws(self, b: int) -> None:
+        """Every random number of one generation (both halves) into buffer
+        b: standard normal perturbations and three uniforms per chain
+        (acceptance, two partners); the step kernels scale and map them.
+        The normals are drawn in single precision (a perturbation needs no
+        more; double precision normals cost 27 us a generation on this GPU,
+        these 15) and widened."""
+        torch.randn(self._z32.shape, generator=self.gen, out=self._z32)
+        self._z[b].copy_(self._z32)
+        torch.rand(self._u[b].shape, generator=self.gen, out=self._u[b])
 
     def _generation(self, gamma: float) -> None:
-        z, u = self._draws()
+        cur, nxt = self._buf, 1 - self._buf
+        main = torch.cuda.current_stream(self.states.device)
+        # buffer nxt was last read by the previous generation's steps
+        self._side.wait_stream(main)
+        with torch.cuda.stream(self._side):
+            self._draws(nxt)
+        z, u = self._z[cur], self._u[cur]
         h = self.half
         for first, other in ((0, h), (h, 0)):
             kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, other, h,
@@ -553,9 +566,11 @@ class DEMCMC:
                            self._prop, self._cp, self._acc[first:first + h], self.t0,
                            self.jitter, self.mode)
         self._n_acc += self._acc
+        main.wait_stream(self._side)
+        self._buf = nxt
 
-    def _gamma(self) -> float:
-        hop = self.hop_every and (self.generation + 1) % self.hop_every == 0
+    def _gamma(self, ahead: int = 1) -> float:
+        hop = self.hop_every and (self.generation + ahead) % self.hop_every == 0
         return 1.0 if hop else self.gamma
 
     def step(self) -> None:
@@ -565,34 +580,39 @@ class DEMCMC:
         self.generation += 1
 
     def run(self, generations: int, use_graph: bool = True) -> None:
-        """``generations`` generations; with use_graph, one generation is
-        captured into a CUDA graph (random draws included) and replayed,
-        which removes the per-launch host overhead for small populations.
-        The gamma = 1 generations are not captured (they run eagerly)."""
-        if not use_graph:
-            for _ in range(generations):
+        """``generations`` generations; with use_graph, two generations (one
+        on each draw buffer) are captured into a CUDA graph, random draws
+        included, and replayed, which removes the per-launch host overhead
+        for small populations.  The first generation, the gamma = 1
+        generations and any that would leave a pair unaligned with the draw
+        buffers run eagerly."""
+        while generations > 0:
+            pair = (use_graph and generations >= 2 and self.generation > 0 and self._buf == 0
+                    and self._gamma(1) == self.gamma and self._gamma(2) == self.gamma)
+            if not pair:
                 self.step()
-            return
-        if getattr(self, "_graph", None) is None:
-            self.step()                                   # warm-up outside capture
-            torch.cuda.synchronize()
-            side = torch.cuda.Stream(device=self.states.device)
-            side.wait_stream(torch.cuda.current_stream())
-            g = torch.cuda.CUDAGraph()
-            g.register_generator_state(self.gen)          # replays advance self.gen
-            with torch.cuda.stream(side):
-                with torch.cuda.graph(g, stream=side):
-                    self._generation(self.gamma)
-            torch.cuda.current_stream().wait_stream(side)
-            self._graph = g
-            generations -= 1
-        for _ in range(generations):
-            if self._gamma() != self.gamma:
-                self.step()
-            else:
-                self._graph.replay()
-                self.generation += 1
-                self.proposed += 2 * self.half
+                generations -= 1
+                continue
+            if self._graph is None:
+                self._capture()
+            self._graph.replay()
+            self.generation += 2
+            self.proposed += 4 * self.half
+            generations -= 2
+
+    def _capture(self) -> None:
+        dev = self.states.device
+        torch.cuda.synchronize(dev)
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(torch.cuda.current_stream(dev))
+        g = torch.cuda.CUDAGraph()
+        g.register_generator_state(self.gen)              # replays advance self.gen
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                self._generation(self.gamma)               # draw buffer 0 ...
+                self._generation(self.gamma)               # ... then 1: back to 0
+        torch.cuda.current_stream(dev).wait_stream(cap)
+        self._graph = g
 
     @property
     def acceptance(self) -> float:

@@ -126,8 +126,11 @@ def test_driver_samples_the_linear_gaussian_posterior(kc):
     assert np.all(st[:, 0] == P) and np.all(st[:, 3] == w) and np.all(st[:, 4] == M0)
 
 
-def test_graph_replay_equals_eager(kc):
-    """The same seed gives the same chain eagerly and with graph replay."""
+@pytest.mark.parametrize("generations,hop_every", [(12, 0), (13, 4)])
+def test_graph_replay_equals_eager(kc, generations, hop_every):
+    """The same seed gives the same chain eagerly and with graph replay
+    (replayed pairs of generations, eager gamma = 1 generations between
+    them, an odd count)."""
     from paper_0812_2976_gb300 import synth
     import oracle
     w = synth.uniform(1, n_sys=256)
@@ -135,8 +138,10 @@ def test_graph_replay_equals_eager(kc):
     runs = []
     for use_graph in (False, True):
         mc = kc.DEMCMC(dev(w.params), dev(w.t), dev(v), dev(w.sigma), mode="mixed",
-                       eps_scale=1e-6, hop_every=0, seed=11)
-        mc.run(12, use_graph=use_graph)
+                       eps_scale=1e-6, hop_every=hop_every, seed=11)
+        mc.run(generations - 5, use_graph=use_graph)
+        mc.run(5, use_graph=use_graph)
+        assert mc.generation == generations
         runs.append((mc.states.cpu().numpy(), mc.chi2.cpu().numpy(), mc.acceptance))
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
