@@ -526,10 +526,11 @@ class DEMCMC:
         dev = self.states.device
         self._prop = torch.empty((self.half, self.npar), dtype=torch.float64, device=dev)
         self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
-        self._acc = torch.empty(n, dtype=torch.int32, device=dev)
         self.generation = 0
         # acceptances per chain, summed only when read: one element-wise add
-        # a generation (a reduction and an add were two launches)
+        # a generation, on the side stream (a generation's accepted flags
+        # are added while the next one steps; two flag buffers)
+        self._acc = [torch.zeros(n, dtype=torch.int32, device=dev) for _ in (0, 1)]
         self._n_acc = torch.zeros(n, dtype=torch.int64, device=dev)
         self.proposed = 0
         self._graph = None
@@ -554,18 +555,18 @@ class DEMCMC:
     def _generation(self, gamma: float) -> None:
         cur, nxt = self._buf, 1 - self._buf
         main = torch.cuda.current_stream(self.states.device)
-        # buffer nxt was last read by the previous generation's steps
+        # buffers nxt were last used by the previous generation's steps
         self._side.wait_stream(main)
         with torch.cuda.stream(self._side):
+            self._n_acc += self._acc[nxt]          # the previous generation's flags
             self._draws(nxt)
-        z, u = self._z[cur], self._u[cur]
+        z, u, acc = self._z[cur], self._u[cur], self._acc[cur]
         h = self.half
         for first, other in ((0, h), (h, 0)):
             kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, other, h,
                            gamma, self.eps_scale, z[first:first + h], u[first:first + h],
-                           self._prop, self._cp, self._acc[first:first + h], self.t0,
+                           self._prop, self._cp, acc[first:first + h], self.t0,
                            self.jitter, self.mode)
-        self._n_acc += self._acc
         main.wait_stream(self._side)
         self._buf = nxt
 
@@ -617,7 +618,8 @@ class DEMCMC:
     @property
     def acceptance(self) -> float:
         """Fraction of accepted proposals so far (synchronises)."""
-        return int(self._n_acc.sum()) / max(self.proposed, 1)
+        last = self._acc[1 - self._buf] if self.generation else self._acc[0][:0]
+        return (int(self._n_acc.sum()) + int(last.sum())) / max(self.proposed, 1)
 
 
 class _Chi2Fn(torch.autograd.Function):
