@@ -435,14 +435,15 @@ kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains, int32_t n
   if (st != KC_OK) return st;
   if (!std::isfinite(t0) || !std::isfinite(jitter))
     return fail(KC_ERR_ARG, "%s: t0 and jitter must be finite", fn);
-  const int npar = 5 * n_pl + 1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = kc::launch_demcmc_propose(states, npar, first, count, partner_first,
-                                            partner_count, gamma, eps_scale, z, u, proposals, s);
-  if (e != cudaSuccess) return cuda_status(e, "kc_demcmc_step: propose");
-  // chi2 of the proposals with the Metropolis step in the kernel's epilogue
+  // the proposals formed in the mixed kernel's prologue (by the proposal
+  // kernel before the other launch paths), their chi2, and the Metropolis
+  // step in the kernel's epilogue
   UniformArgs a{proposals, t,   v_obs, sigma, count, n_pl, n_obs, t0, jitter * jitter,
-                kc::invalid_counter(), kc::DemcAccept{states, chi2, u, accepted, first}};
+                kc::invalid_counter(),
+                kc::DemcAccept{states, chi2, u, accepted, first, z, eps_scale, partner_first,
+                               partner_count, gamma}};
+  cudaError_t e;
   if (mode == KC_FP64) {
     const Tile tile = kc::choose_tile(Kind::Chi2F64, count, n_pl, n_obs);
     e = kc::launch_chi2_f64(a, tile, static_cast<double *>(chi2_prop), nullptr, s);

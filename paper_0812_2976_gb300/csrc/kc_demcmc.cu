@@ -15,33 +15,15 @@
 // them; the kernels turn them into the perturbation and the partner pair.
 #include <cmath>
 
+#include "kc_device.cuh"
 #include "kc_internal.h"
 
 namespace kc {
 
 namespace {
 
-// floor(f) clamped to 0 .. hi (NaN to 0): an index inside the range for any
-// draw, also outside [0, 1).
-__device__ inline int64_t clamp_index(double f, int64_t hi) {
-  f = floor(f);
-  return f >= 0.0 ? (f < (double)hi ? (int64_t)f : hi) : 0;
-}
-
-// The two partners of draw pair (u1, u2) in [0, 1): distinct, uniform over
-// the ordered pairs of the m chains from pfirst (m >= 2, checked by the host).
-__device__ inline void demcmc_partners(double u1, double u2, int64_t pfirst, int64_t m,
-                                       int64_t &r1, int64_t &r2) {
-  const int64_t k1 = clamp_index(u1 * (double)m, m - 1);
-  int64_t k2 = clamp_index(u2 * (double)(m - 1), m - 2);
-  k2 += k2 >= k1 ? 1 : 0;
-  r1 = pfirst + k1;
-  r2 = pfirst + k2;
-}
-
-// x*_p = x_ip + gamma (x_r1,p - x_r2,p) + (eps_scale_p |x_ip|) z_p, written
-// with explicit roundings so that the result does not depend on FMA
-// contraction.
+// One thread per (proposal, parameter): the partner pair (demc_partners)
+// and the proposal (demc_proposal, kc_device.cuh).
 __global__ void demcmc_propose_kernel(const double *__restrict__ states, int n_par, int64_t first,
                                       int64_t count, int64_t pfirst, int64_t pcount,
                                       double gamma, const double *__restrict__ eps_scale,
@@ -54,11 +36,8 @@ __global__ void demcmc_propose_kernel(const double *__restrict__ states, int n_p
     const int p = (int)(idx - c * n_par);
     const int64_t i = first + c;
     int64_t r1, r2;
-    demcmc_partners(u[3 * c + 1], u[3 * c + 2], pfirst, pcount, r1, r2);
-    const double xi = states[i * n_par + p];
-    const double d = __dsub_rn(states[r1 * n_par + p], states[r2 * n_par + p]);
-    const double eps = __dmul_rn(__dmul_rn(eps_scale[p], fabs(xi)), z[idx]);
-    prop[idx] = __dadd_rn(__dadd_rn(xi, __dmul_rn(gamma, d)), eps);
+    demc_partners(u[3 * c + 1], u[3 * c + 2], pfirst, pcount, r1, r2);
+    prop[idx] = demc_proposal(states, n_par, i, r1, r2, p, gamma, eps_scale[p], z[idx]);
   }
 }
 

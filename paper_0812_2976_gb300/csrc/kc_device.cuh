@@ -762,6 +762,40 @@ __device__ __forceinline__ double velocity_add_f64(const PlanetD &q, double sE, 
   return fma(fma(q.A, cE, -(q.B * sE)), rcp_f64(D), V);
 }
 
+// ------------------------------------------------ DE-MC proposal
+
+// floor(f) clamped to 0 .. hi (NaN to 0): an index inside the range for any
+// draw, also outside [0, 1).
+__device__ __forceinline__ int64_t demc_clamp_index(double f, int64_t hi) {
+  f = floor(f);
+  return f >= 0.0 ? (f < (double)hi ? (int64_t)f : hi) : 0;
+}
+
+// The two partners of draw pair (u1, u2) in [0, 1): distinct, uniform over
+// the ordered pairs of the m chains from pfirst (m >= 2, checked by the host).
+__device__ __forceinline__ void demc_partners(double u1, double u2, int64_t pfirst, int64_t m,
+                                              int64_t &r1, int64_t &r2) {
+  const int64_t k1 = demc_clamp_index(u1 * (double)m, m - 1);
+  int64_t k2 = demc_clamp_index(u2 * (double)(m - 1), m - 2);
+  k2 += k2 >= k1 ? 1 : 0;
+  r1 = pfirst + k1;
+  r2 = pfirst + k2;
+}
+
+// Parameter p of chain i's proposal,
+// x*_p = x_ip + gamma (x_r1,p - x_r2,p) + (eps_scale_p |x_ip|) z,
+// with explicit roundings so that the result does not depend on FMA
+// contraction (the proposal kernel and the fused chi2 prologue agree bit for
+// bit).
+__device__ __forceinline__ double demc_proposal(const double *states, int npar, int64_t i,
+                                                int64_t r1, int64_t r2, int p, double gamma,
+                                                double eps_scale, double z) {
+  const double xi = states[i * npar + p];
+  const double d = __dsub_rn(states[r1 * npar + p], states[r2 * npar + p]);
+  const double eps = __dmul_rn(__dmul_rn(eps_scale, fabs(xi)), z);
+  return __dadd_rn(__dadd_rn(xi, __dmul_rn(gamma, d)), eps);
+}
+
 // ------------------------------------------------ warp helpers
 
 __device__ __forceinline__ float shfl_xor(float x, int m) {

@@ -120,6 +120,24 @@ __device__ __forceinline__ void demc_accept(const UniformArgs &a, int64_t s, int
   if (d.accepted) d.accepted[s] = acc ? 1 : 0;
 }
 
+// Parameters p0 .. p0 + N - 1 of proposal s, formed in the fused kernel's
+// prologue (the proposal kernel's arithmetic, demc_proposal) and stored to
+// the proposals, which params points at (the caller's writable buffer).
+template <int N>
+__device__ __forceinline__ void demc_form(const UniformArgs &a, int64_t s, int p0, int npar,
+                                          double (&out)[N]) {
+  const DemcAccept &d = a.demc;
+  int64_t r1, r2;
+  demc_partners(d.u[3 * s + 1], d.u[3 * s + 2], d.partner_first, d.partner_count, r1, r2);
+  double *prop = const_cast<double *>(a.params) + s * npar;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    out[k] = demc_proposal(d.states, npar, d.first + s, r1, r2, p0 + k, d.gamma,
+                           d.eps_scale[p0 + k], d.z[s * npar + p0 + k]);
+    prop[p0 + k] = out[k];
+  }
+}
+
 // PRE = false: each CTA computes its planets' constants (FP64) and converts
 // the observations itself.  PRE = true (split variant): both come from
 // prep_mixed_kernel, launched just before with programmatic dependent
@@ -207,7 +225,13 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       const int64_t s = sys0 + sl;
       PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
       if (s < a.n_sys) {
-        const double *p = a.params + s * npar + 5 * j;
+        double p[5];
+        if (!NLL && !SINGLE && a.demc.z) {
+          demc_form(a, s, 5 * j, npar, p);        // DE-MC: this planet's proposal
+        } else {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) p[k] = a.params[s * npar + 5 * j + k];
+        }
         q = planet_setup_mixed(p, t_ref, a.t0);
         if (SINGLE) {     // 1/P and M0/(2 pi) in float, the phase taken from t - t0
           q.n_hi = 1.0f / d2f(p[0]);
@@ -223,8 +247,12 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       const int64_t s = sys0 + i;
       float g = 0.0f;
       if (s < a.n_sys) {
-        const double gd = a.params[s * npar + 5 * J];
-        g = finite_bits(gd) ? d2f(gd) : __int_as_float(0x7fc00000);
+        double gd[1];
+        if (!NLL && !SINGLE && a.demc.z)
+          demc_form(a, s, 5 * J, npar, gd);
+        else
+          gd[0] = a.params[s * npar + 5 * J];
+        g = finite_bits(gd[0]) ? d2f(gd[0]) : __int_as_float(0x7fc00000);
       }
       gam_s[i] = g;
       if (NLL) s2_s[i] = s < a.n_sys ? system_jitter2_f(a.params + s * npar, J) : 0.0f;
@@ -786,8 +814,23 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
   return cudaGetLastError();
 }
 
-cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile_in, float *out,
+// DE-MC proposals still to be formed (a.demc.z != NULL), for launch paths
+// whose kernels do not form them: the proposal kernel runs first and a
+// marks them as formed.
+static cudaError_t form_proposals(UniformArgs &a, cudaStream_t st) {
+  if (!a.demc.states || !a.demc.z) return cudaSuccess;
+  const DemcAccept &d = a.demc;
+  cudaError_t err = launch_demcmc_propose(d.states, 5 * a.n_pl + 1, d.first, a.n_sys,
+                                          d.partner_first, d.partner_count, d.gamma,
+                                          d.eps_scale, d.z, d.u,
+                                          const_cast<double *>(a.params), st);
+  a.demc.z = nullptr;
+  return err;
+}
+
+cudaError_t launch_chi2_mixed(const UniformArgs &a_in, const Tile &tile_in, float *out,
                               float *resid, cudaStream_t st) {
+  UniformArgs a = a_in;
   Tile tile = tile_in;
   if (tile.split) {
     // No stream-ordered allocation inside a graph being captured: the fused
@@ -801,10 +844,11 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile_in, float *
     }
   }
   if (tile.split) {
+    cudaError_t err = form_proposals(a, st);
+    if (err != cudaSuccess) return err;
     // stream-ordered scratch from the library's pool (kept cached between calls)
     void *scratch = nullptr;
-    cudaError_t err =
-        scratch_alloc(&scratch, mixed_scratch_bytes(a.n_sys, a.n_pl, a.n_obs, tile), st);
+    err = scratch_alloc(&scratch, mixed_scratch_bytes(a.n_sys, a.n_pl, a.n_obs, tile), st);
     if (err != cudaSuccess) return err;
     err = launch_chi2_mixed_prepared(a, tile, scratch, out, resid, st);
     // the chunked two-pass variant has no per-system epilogue: a DE-MC
@@ -830,11 +874,15 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile_in, float *
   return cudaGetLastError();
 }
 
-cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out, float *resid,
-                            cudaStream_t st) {
+cudaError_t launch_chi2_f64(const UniformArgs &a_in, const Tile &tile, double *out,
+                            float *resid, cudaStream_t st) {
+  // the FP64 kernel checks gamma against the whole parameter row, so its
+  // proposals are formed before it
+  UniformArgs a = a_in;
+  cudaError_t err = form_proposals(a, st);
+  if (err != cudaSuccess) return err;
   const size_t smem = smem_chi2_f64(a.n_pl, tile);
   const int grid = grid_for(a.n_sys, tile.block / tile.G);
-  cudaError_t err = cudaSuccess;
 #define KC_LAUNCH(JJ)                                                                \
   err = set_smem(chi2_f64_kernel<JJ>, smem);                                         \
   if (err == cudaSuccess)                                                            \

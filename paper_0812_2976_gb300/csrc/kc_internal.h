@@ -20,17 +20,24 @@ struct Tile {
   int split = 0;   // mixed chi2 only: 1, 2 = two-pass variants (see kc_fwd.cu)
 };
 
-// Metropolis step of DE-MC carried by a chi2 launch: the batch's systems
-// are proposals for chains first .. first + n_sys - 1, and each system's
-// chi2 is compared with its chain's (accept iff ln u[3 c] < -(chi2* -
-// chi2)/2), the accepted proposal copied over the chain's state.  states
-// == NULL: a plain evaluation.
+// DE-MC step carried by a chi2 launch: the batch's systems are proposals
+// for chains first .. first + n_sys - 1 (params points at them), and each
+// system's chi2 is compared with its chain's (accept iff ln u[3 c] <
+// -(chi2* - chi2)/2), the accepted proposal copied over the chain's state.
+// With z != NULL the proposals are still to be formed from the states, the
+// partner range and the draws: the fused mixed kernel forms them in its
+// prologue, every other launch path with the proposal kernel first.
+// states == NULL: a plain evaluation.
 struct DemcAccept {
   double *states;          // [n_chains][5 n_pl + 1]
   void *chi2;              // [n_chains], float (mixed) or double (FP64)
   const double *u;         // [n_sys][3]
   int32_t *accepted;       // [n_sys] or NULL
   int64_t first;
+  const double *z = nullptr;          // [n_sys][5 n_pl + 1] standard normal draws
+  const double *eps_scale = nullptr;  // [5 n_pl + 1]
+  int64_t partner_first = 0, partner_count = 0;
+  double gamma = 0.0;
 };
 
 struct UniformArgs {
