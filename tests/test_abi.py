@@ -88,6 +88,12 @@ def test_bad_arguments_rejected_on_host(lib):
         assert lib.kc_demcmc_step(p, p, 16, 1, p, p, p, 8, 0.0, 0.0, 1, 0, 8, pf, pc, 0.5,
                                   p, p, p, p, p, None, None) == 1
         assert msg in lib.kc_last_error()
+    # ... and gamma, the epoch and the jitter finite
+    for t0, jit, g, msg in ((0.0, 0.0, float("inf"), b"gamma"), (float("nan"), 0.0, 0.5, b"t0"),
+                            (0.0, float("inf"), 0.5, b"jitter")):
+        assert lib.kc_demcmc_step(p, p, 16, 1, p, p, p, 8, t0, jit, 1, 0, 8, 8, 8, g,
+                                  p, p, p, p, p, None, None) == 1
+        assert msg in lib.kc_last_error()
 
 
 def test_empty_batches_are_no_ops(lib):
