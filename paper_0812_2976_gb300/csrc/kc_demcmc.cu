@@ -13,6 +13,9 @@
 // Foreman-Mackey et al. 2013).  The random numbers are inputs (standard
 // normal and uniform draws), so the step is a deterministic function of
 // them; the kernels turn them into the perturbation and the partner pair.
+// In a mixed-precision step the fused chi2 kernel forms the proposals in its
+// prologue and takes the Metropolis decision in its epilogue (kc_fwd.cu);
+// the two kernels here serve the other launch paths.
 #include <cmath>
 
 #include "kc_device.cuh"
