@@ -650,9 +650,12 @@ def test_gauss_newton_structure(oracle_mod):
 def test_velocity_equals_the_eccentric_anomaly_form(oracle_mod):
     """The kernels evaluate Eq. 3 in its eccentric-anomaly form
     [K cos w (cos E - e) - K sqrt(1 - e^2) sin w sin E]/(1 - e cos E)
-    + K e cos w; the oracle uses the true anomaly f explicitly.  The two are
+    + K e cos w (mixed path) or, with the e cos w term folded in,
+    [K cos w (1 - e^2) cos E - K sqrt(1 - e^2) sin w sin E]/(1 - e cos E)
+    (FP64 path); the oracle uses the true anomaly f explicitly.  They are
     algebraically identical (cos f = (cos E - e)/D, sin f = sqrt(1-e^2)
-    sin E / D), so they must agree to rounding."""
+    sin E / D, (cos E - e) + e D = (1 - e^2) cos E), so they must agree to
+    rounding."""
     rng = np.random.default_rng(41)
     for _ in range(20):
         P, K = np.exp(rng.uniform(0, np.log(3000))), rng.uniform(1, 100)
@@ -662,9 +665,12 @@ def test_velocity_equals_the_eccentric_anomaly_form(oracle_mod):
         M = oracle_mod.mean_anomaly(t, 0.0, P, M0)
         E = oracle_mod.kepler_E(M, e)
         D = 1 - e * np.cos(E)
+        b2 = (1 - e) * (1 + e)
         v_E = (K * np.cos(w) * (np.cos(E) - e)
-               - K * np.sqrt((1 - e) * (1 + e)) * np.sin(w) * np.sin(E)) / D + K * e * np.cos(w)
+               - K * np.sqrt(b2) * np.sin(w) * np.sin(E)) / D + K * e * np.cos(w)
+        v_folded = (K * np.cos(w) * b2 * np.cos(E) - K * np.sqrt(b2) * np.sin(w) * np.sin(E)) / D
         assert np.max(np.abs(v_E - v)) <= 1e-13 * K / (1 - e)
+        assert np.max(np.abs(v_folded - v)) <= 1e-13 * K / (1 - e)
 
 
 # ------------------------------------------------------------ gradient magnitudes
