@@ -37,7 +37,6 @@ sys.path.insert(0, ROOT)
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the headline metric; both arms (this library and the oracle) report it
 METRIC_PAPER_BATCH = "planet-obs evals/s (chi2, npl=4, nobs=256) mixed vs FP64"
-N_SM = 152
 FP32_LANES_PER_SM = 128
 FALLBACK_SM_MHZ = 2070.0
 
@@ -100,6 +99,12 @@ F64_FLOPS_PER_EVAL = 10 + 20 + 13 + 8 + 11
 # granularity of the 168-byte parameter rows).  Keyed by (config, n_sys
 # override); other workloads report null.
 DRAM_BYTES_PER_LAUNCH = {(1, None): 765440}
+
+
+def sm_count() -> int:
+    """SMs of the current CUDA device (queried, not assumed)."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def sm_mhz_for_peaks():
@@ -171,7 +176,7 @@ def grid_sweep_throughput(kc, synth, dev, stream, args):
     sec = a.elapsed_time(b) / 1e3 / steps
     evals = w.n_sys * w.n_pl * w.n_obs
     val = evals / sec
-    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
     return {"value": val, "unit": "planet-obs evals/s", "ms_per_step": 1e3 * sec,
             "n_sys": w.n_sys, "roofline_frac": val * mixed_flops_per_eval(w.n_pl) / 1e12 / peak,
             "inputs": "176 MB of parameters > L2"}
@@ -213,7 +218,7 @@ def gradient_throughput(kc, synth, dev, stream, args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         out[name] = evals * reps / (a.elapsed_time(b) / 1e3)
-    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
     out["roofline_alu"] = {
         "peak": peak, "unit": "TFLOP/s",
         "chi2_grad_frac": out["chi2_grad"] * grad_flops_per_eval(w.n_pl) / 1e12 / peak,
@@ -571,7 +576,7 @@ def run_kc(args):
         # pipe probe, x 2 FLOP x SMs x maximum SM clock
         f64_rate = kc.kc_measure_pipe_rate("fp64", stream=stream)
         f32_rate = kc.kc_measure_pipe_rate("fp32", stream=stream)
-        f64_peak = 2 * f64_rate * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+        f64_peak = 2 * f64_rate * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
         extras["fp64"] = {"value": f64_val, "unit": "planet-obs evals/s",
                           "ms_per_step": 1e3 * f_s / len(f_ev),
                           "roofline": {"bound": "fp64", "achieved": f64_val * F64_FLOPS_PER_EVAL
@@ -579,7 +584,7 @@ def run_kc(args):
                                        "frac": f64_val * F64_FLOPS_PER_EVAL / 1e12 / f64_peak,
                                        "flops_per_eval": F64_FLOPS_PER_EVAL,
                                        "peak_basis": f"measured DFMA rate {f64_rate:.2f} per SM "
-                                                     f"per clock x 2 FLOP x {N_SM} SMs x max SM clock"}}
+                                                     f"per clock x 2 FLOP x {sm_count()} SMs x max SM clock"}}
         extras["pipe_rates_per_sm_clock"] = {"fp32_fma": f32_rate, "fp64_fma": f64_rate}
         extras["kepler_only"] = kepler_throughput(kc, dev, stream)
         extras["grid_sweep"] = grid_sweep_throughput(kc, synth, dev, stream, args)
@@ -588,14 +593,14 @@ def run_kc(args):
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
-    peak_tflops = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz * 1e6 / 1e12
+    peak_tflops = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz * 1e6 / 1e12
     flops = mixed_flops_per_eval(w.n_pl) * evals
     achieved = flops / (t_sum / args.steps) / 1e12          # one GPU's launch
     traffic = DRAM_BYTES_PER_LAUNCH.get((args.config, args.n_sys)) if world == 1 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": f"chi2_mixed_kernel<{w.n_pl}>",
-                "peak_basis": f"FP32 FMA pipe: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP "
+                "peak_basis": f"FP32 FMA pipe: {sm_count()} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP "
                               f"x {sm_mhz:.0f} MHz ({pk_kind} max SM clock)",
                 "flops_per_eval": mixed_flops_per_eval(w.n_pl)}
 
@@ -756,7 +761,7 @@ def run_kc_ragged(args):
     per_planet = (grad_flops_per_eval(1) - 12.0) if want_grad else (mixed_flops_per_eval(1) - 10.0)
     per_obs = 12.0 if want_grad else 10.0
     flops_step = float(np.sum(n_obs_s * (npl_s * per_planet + per_obs)))
-    peak = 2 * FP32_LANES_PER_SM * N_SM * sm_mhz_for_peaks() * 1e6 / 1e12
+    peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
     achieved = flops_step / (t_sum / args.steps) / 1e12
     line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": achieved / peak, "traffic": None,

@@ -40,7 +40,9 @@
  *    by kc_last_device_error.
  *  - n_sys == 0 is a no-op.  n_obs == 0 gives chi2 = 0 (NaN if invalid).
  *  - Calls are thread-safe; concurrent calls on different streams do not
- *    share device memory.
+ *    share device memory, with one exception: every call of
+ *    kc_chi2_eval_mixed_noalloc uses the same fixed array (see its
+ *    declaration), so its calls must not overlap on the device.
  */
 #ifndef KC_H
 #define KC_H

@@ -61,6 +61,16 @@ def _dev_f64(name: str, x: torch.Tensor, dim: int) -> torch.Tensor:
     return x.contiguous()
 
 
+def _out_f32(name: str, x, n: int, device) -> None:
+    """A caller-provided float32 output of at least n elements on `device`."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.device != device:
+        raise TypeError(f"{name} must be a CUDA tensor on {device}")
+    if x.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if not x.is_contiguous() or x.numel() < n:
+        raise ValueError(f"{name} must be contiguous with at least {n} elements")
+
+
 def n_planets(params: torch.Tensor) -> int:
     """n_pl from a [n_sys, 5*n_pl+1] parameter batch."""
     n = params.shape[-1] - 1
@@ -166,9 +176,20 @@ def kc_chi2_eval_mixed_noalloc(params, t, v_obs, sigma, out, t0: float = 0.0,
     evaluating.  ``out`` (float32 [n_sys]) and the optional float32
     ``max_kepler_resid`` must be provided by the caller; intermediate data
     go to a fixed array inside libkc.so, so problems are limited to
-    KC_NOALLOC_SCRATCH_BYTES of it and overlapping calls must be serialised."""
-    params = _dev_f64("params", params, 2)
-    t, v_obs, sigma = _obs(t, v_obs, sigma)
+    KC_NOALLOC_SCRATCH_BYTES of it and overlapping calls must be serialised.
+    Inputs must already be contiguous (a copy would allocate) and the
+    outputs float32 CUDA tensors on the parameters' device."""
+    for name, x, dim in (("params", params, 2), ("t", t, 1), ("v_obs", v_obs, 1),
+                         ("sigma", sigma, 1)):
+        _dev_f64(name, x, dim)
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous: this call makes no copy")
+    if not (t.numel() == v_obs.numel() == sigma.numel()):
+        raise ValueError("t, v_obs and sigma must have the same length")
+    n_sys = params.shape[0]
+    _out_f32("out", out, n_sys, params.device)
+    if max_kepler_resid is not None:
+        _out_f32("max_kepler_resid", max_kepler_resid, n_sys, params.device)
     lib = _lib.load()
     _lib.check(lib.kc_chi2_eval_mixed_noalloc(
         params.data_ptr(), t.data_ptr(), v_obs.data_ptr(), sigma.data_ptr(), params.shape[0],

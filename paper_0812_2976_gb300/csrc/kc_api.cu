@@ -82,6 +82,29 @@ std::mutex g_inv_mu;
 std::map<int, unsigned long long *> g_inv_addr;
 }  // namespace
 
+namespace {
+std::mutex g_sm_mu;
+std::map<int, int> g_sm_count;
+}  // namespace
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> lk(g_sm_mu);
+  auto it = g_sm_count.find(dev);
+  if (it != g_sm_count.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  g_sm_count[dev] = n;
+  return n;
+}
+
 unsigned long long *invalid_counter() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -139,13 +162,13 @@ int obs_tile_for(Kind kind, int n_obs) {
 }
 
 // Built-in launch shape.  G threads share one system; enough threads to fill
-// the 152 SMs a few times over, but each thread keeps at least four
+// the device's SMs a few times over, but each thread keeps at least four
 // observations so the per-system combine stays cheap.
 Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
   const bool grad = kind == Kind::GradF64 || kind == Kind::GradMixed;
   Tile t;
   t.block = 256;
-  const int64_t want_threads = int64_t(152) * 2048 * 2;
+  const int64_t want_threads = int64_t(sm_count()) * 2048 * 2;
   int G = 1;
   while (G < 256 && n_sys * G < want_threads) G <<= 1;
   const int max_g_obs = n_obs >= 4 ? n_obs / 4 : 1;
@@ -601,9 +624,10 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   cudaError_t err = cudaSuccess;
   // powers of two, plus G = 12, 24, 48 with 96- and 192-thread blocks, and
   // G = 8, 16, 32 with 160- and 224-thread blocks: the CTA count of a
-  // batch that fills about one wave then spreads more evenly over the 152
-  // SMs (4096 systems at 16 threads: 293 CTAs of 224 threads, two per SM on
-  // 141 SMs, where 256 CTAs of 256 threads leave 48 SMs with one)
+  // batch that fills about one wave then spreads more evenly over the
+  // SMs (on a GB300, 4096 systems at 16 threads: 293 CTAs of 224 threads,
+  // two per SM on 141 of its SMs, where 256 CTAs of 256 threads leave 48
+  // SMs with one)
   std::vector<kc_tile> cands;
   for (int split = 0; split <= 2; ++split) {
     for (int B : {32, 64, 128, 256})

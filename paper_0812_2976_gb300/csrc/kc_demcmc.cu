@@ -66,7 +66,8 @@ __global__ void demcmc_accept_kernel(double *__restrict__ states, T *__restrict_
 
 int grid_elems(int64_t n) {
   const int64_t b = (n + 255) / 256;
-  return (int)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+  const int64_t cap = (int64_t)sm_count() * 32;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 }  // namespace

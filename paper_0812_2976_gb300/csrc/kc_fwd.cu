@@ -711,7 +711,8 @@ int grid_for(int64_t n_sys, int ST) { return (int)((n_sys + ST - 1) / ST); }
 
 int elementwise_grid(int64_t n) {
   const int64_t blocks = (n + 255) / 256;
-  return (int)(blocks < 152 * 32 ? (blocks > 0 ? blocks : 1) : 152 * 32);
+  const int64_t cap = (int64_t)sm_count() * 32;
+  return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
 }  // namespace
@@ -777,7 +778,7 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
   // so the items are spread thinly over every SM (64-thread CTAs, one item
   // per thread) rather than packed into a few full CTAs.
   const int64_t items = std::max<int64_t>(a.n_sys * a.n_pl, std::max<int64_t>(a.n_obs, 1));
-  const int prep_grid = (int)std::min<int64_t>((items + 63) / 64, 152 * 16);
+  const int prep_grid = (int)std::min<int64_t>((items + 63) / 64, (int64_t)sm_count() * 16);
   prep_mixed_kernel<<<prep_grid, 64, 0, st>>>(a, pl, gam, obs, w, cs.count);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;

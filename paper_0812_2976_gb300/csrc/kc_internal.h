@@ -56,6 +56,12 @@ struct UniformArgs {
   DemcAccept demc = {};
 };
 
+// Number of SMs of the current device (cudaDevAttrMultiProcessorCount),
+// queried once per device and cached (kc_api.cu).  Launch heuristics size
+// their grids with it; 1 if no device can be queried (host-only use of the
+// tile table), which still gives valid launch shapes.
+int sm_count();
+
 // The library's per-device invalid-system counter (kc_api.cu); NULL if its
 // address cannot be obtained.
 unsigned long long *invalid_counter();

@@ -56,6 +56,9 @@ extern "C" kc_status kc_chi2_eval_mixed_noalloc(const double *params, const doub
                                                 float *max_kepler_resid, kc_stream stream) {
   const char *fn = "kc_chi2_eval_mixed_noalloc";
   if (n_sys < 0) return kc::fail(KC_ERR_ARG, "%s: n_sys < 0", fn);
+  // the same upper bound as every other uniform call: it keeps the scratch
+  // size below (the products of n_sys in size_t) from wrapping around
+  if (n_sys > (int64_t(1) << 40)) return kc::fail(KC_ERR_ARG, "%s: n_sys too large", fn);
   if (n_pl < 1 || n_pl > KC_MAX_PLANETS)
     return kc::fail(KC_ERR_ARG, "%s: n_pl = %d outside 1..%d", fn, n_pl, KC_MAX_PLANETS);
   if (n_obs < 0 || n_obs > KC_MAX_OBS)

@@ -431,7 +431,7 @@ cudaError_t ragged_prep(const RaggedDev &d, int mode, const double *t, const dou
                         double *t_ref, cudaStream_t st) {
   const int64_t warps = d.n_sys;
   int64_t blocks = (warps * 32 + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
   if (blocks < 1) blocks = 1;
   if (mode == KC_MIXED)
     prep_obs_mixed<<<(int)blocks, 256, 0, st>>>(d, t, v, sigma, jitter2, (float4 *)obs_a,
@@ -445,7 +445,7 @@ cudaError_t launch_predict_ragged(const double *params, const int64_t *par_off,
                                   const int32_t *n_pl, const double *t, const int64_t *obs_off,
                                   int64_t n_sys, double t0, double *v_out, cudaStream_t st) {
   int64_t blocks = (n_sys * 32 + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
   predict_ragged_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, 0, st>>>(
       params, par_off, n_pl, t, obs_off, n_sys, t0, v_out);
   return cudaGetLastError();

@@ -81,6 +81,10 @@ def test_bad_arguments_rejected_on_host(lib):
                                     p, None) == 1
     assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 1, None, None, None, None) == 1
     assert lib.kc_measure_pipe_rate(0, None, None) == 1
+    # the allocation-free call refuses sizes whose scratch size would wrap
+    assert lib.kc_chi2_eval_mixed_noalloc(p, p, p, p, (1 << 62) + 1, 8, 16, 0.0, 0.0, p, None,
+                                          None) == 1
+    assert b"too large" in lib.kc_last_error()
     # DE-MC step: the partner range must be inside the population, hold two
     # chains and not overlap the updated chains (states, n_chains = 16,
     # n_pl = 1, ..., first = 0, count = 8, partner_first, partner_count)
