@@ -316,7 +316,8 @@ void kc_plan_destroy(kc_plan *plan);
 /* Launch shape of the uniform-batch kernels: each system is handled by
  * threads_per_system consecutive threads (1..block and a divisor of block;
  * a power of two except for the mixed chi2 kernel; at most 32 for the
- * gradient kernel), `block` threads per CTA (32..256, a multiple of 32).  split (mixed chi2 only) selects a
+ * gradient kernel), `block` threads per CTA (32..256, a multiple of 32;
+ * up to 1024 for split = 3).  split (mixed chi2 only) selects a
  * two-pass variant for small batches: a preparation pass first writes every
  * per-(system, planet) constant and the converted observations to
  * stream-ordered scratch from a library memory pool, then the main kernel
@@ -325,7 +326,13 @@ void kc_plan_destroy(kc_plan *plan);
  * threads_per_system = 32 x chunks (32..1024), any block; the last warp of a
  * system merges the chunks' partial sums in chunk order.  While the stream is
  * being captured into a CUDA graph the split variants are replaced by the
- * fused kernel (no allocation inside a graph). */
+ * fused kernel (no allocation inside a graph).
+ * split = 3 (mixed chi2 only): the warp-per-system kernel,
+ * threads_per_system = 8, 16 or 32 lanes per system, block a multiple of 32
+ * up to 1024; one CTA per block * threads_per_system / 32 systems.
+ * Allocates nothing, so it also runs under stream capture.  With no tuned
+ * entry the mixed chi2 (and the mixed DE-MC step) uses this variant with
+ * the block that spreads the CTAs most evenly over the SMs. */
 typedef struct kc_tile {
     int32_t threads_per_system;
     int32_t block;

@@ -218,6 +218,7 @@ Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
       return t;
     }
   }
+  if (kind == Kind::Chi2Mixed) return warp_tile(n_sys, n_pl, n_obs);
   return default_tile(kind, n_sys, n_pl, n_obs);
 }
 
@@ -535,6 +536,7 @@ kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
 
 bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
   const int G = t.threads_per_system, B = t.block;
+  if (t.split == 3) return kernel == KC_KERNEL_CHI2 && mode == KC_MIXED && kc::warp_tile_ok(G, B);
   if (B < 32 || B > 256 || (B & 31)) return false;
   if (t.split < 0 || t.split > 2) return false;
   if (t.split != 0 && (kernel != KC_KERNEL_CHI2 || mode != KC_MIXED)) return false;
@@ -639,13 +641,22 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
         for (int G : {8, 16, 32}) cands.push_back(kc_tile{G, B, split});
     }
   }
+  // the warp-per-system kernel: 8, 16 or 32 lanes per system, 4..32 warps
+  // per CTA
+  for (int G : {8, 16, 32})
+    for (int W = 4; W <= 32; ++W) cands.push_back(kc_tile{G, 32 * W, 3});
   for (const kc_tile &cand : cands) {
     const int G = cand.threads_per_system, B = cand.block, split = cand.split;
     if (!tile_ok(kernel, mode, cand)) continue;
-    if (n_obs > 0 && G > n_obs) continue;
+    if (n_obs > 0 && G > n_obs && split != 3) continue;
     if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
+    if (split == 3 && G > kc::warp_lanes_for(n_obs)) continue;  // >= 4 obs per lane
     Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
     err = launch(tile);                       // warm-up (and smem attribute)
+    if (err == cudaErrorInvalidConfiguration && split == 3) {
+      err = cudaSuccess;                      // does not fit on an SM: nothing launched
+      continue;
+    }
     if (err != cudaSuccess) break;
     float tmin = 1e30f;
     for (int rep = 0; rep < 5 && err == cudaSuccess; ++rep) {

@@ -1,0 +1,420 @@
+// kc_chi2_warp.cu -- the mixed-precision chi-square of a uniform batch with
+// G = 8, 16 or 32 lanes per system (one warp per system at G = 32), sized
+// by the host so that the CTAs spread evenly over the SMs.
+//
+// Same arithmetic as the fused kernel of kc_fwd.cu (double-single phase,
+// Sec. 5; Kepler's equation in single precision, Sec. 4.3; Eq. 3 velocity;
+// Kahan sums of the planet velocities and of chi2, Sec. 4.4), laid out for
+// the SMs rather than for a tile:
+//
+//  - A CTA of W warps evaluates W * 32 / G systems (one round).  The host
+//    picks W so that the CTAs of the first wave land evenly on the SMs (for
+//    4096 systems, 27 warps per CTA: one CTA and 27 systems on every SM,
+//    where tiles of 16 systems leave some SMs with 32 and others with 16).  Larger batches run many waves; the hardware then overlaps one
+//    CTA's prologue with the work of the others on its SM.
+//  - Prologue: every global load (the reference time, this thread's
+//    observation and its planet's parameters) is issued before any of them
+//    is used, so the CTA waits for memory once.
+//  - The observations (shared by every system, Sec. 4.1) are converted to
+//    float pairs and staged in shared memory, padded with zero-weight
+//    entries to whole chunks, so the inner loops have no tail.
+//  - Each lane holds a chunk of kChunk observations (their phases and their
+//    compensated velocity sums) in registers and streams the planets over
+//    it: a planet's constants (phase, velocity and the hoisted part of
+//    Mikkola's start, computed once per (system, planet)) are read from
+//    shared memory once per chunk, and the chunk's kChunk Kepler solves are
+//    independent chains for the scheduler to interleave.
+//  - The lanes of a system combine their compensated sums with TwoSum
+//    shuffles; no shared-memory reduction, no atomics, no scratch memory.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "kc_demc.cuh"
+#include "kc_device.cuh"
+#include "kc_internal.h"
+
+namespace kc {
+
+namespace {
+
+constexpr int kChunk = 4;           // observations per lane in registers
+constexpr int kObsTileMax = 1024;   // observations staged per CTA at a time
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+// x rounded up to a multiple of the power of two m (no division)
+__device__ __forceinline__ int round_up_pow2(int x, int m) { return (x + m - 1) & -m; }
+
+// Planet constants of the kernel: phase and velocity (PlanetF) and the
+// hoisted part of Mikkola's start (StartF); 48 bytes, three 16-byte loads.
+struct PlanetW {
+  PlanetF f;
+  StartF m;
+};
+
+struct WarpLayout {
+  size_t pl, gam, obs, w, total;
+  __host__ __device__ WarpLayout(int spr, int J, int tile) {
+    pl = 0;
+    gam = pl + sizeof(PlanetW) * spr * J;
+    obs = align16(gam + sizeof(float) * spr);
+    w = obs + sizeof(float4) * tile;
+    total = align16(w + sizeof(float) * tile);
+  }
+};
+
+// Observations held per CTA: all of them (padded to whole chunks of every
+// lane of a system) when they fit, else tiles of kObsTileMax.
+__host__ __device__ inline int warp_obs_tile(int n_obs, int G) {
+  return n_obs <= kObsTileMax ? round_up(n_obs > 0 ? n_obs : 1, G * kChunk) : kObsTileMax;
+}
+
+// Setup of one item of the CTA's round: items 0 .. spr*J - 1 are the
+// (system, planet) constants, items spr*J .. spr*(J+1) - 1 the systems'
+// gamma.  p holds the item's parameters (five, or gamma in p[0]); an
+// invalid planet carries e = NaN, which poisons its system.
+template <int J>
+__device__ __forceinline__ void setup_item(int i, int spr, int64_t sys0, int64_t n_sys,
+                                           const double (&p)[5], double t_ref, double t0,
+                                           PlanetW *pl_s, float *gam_s) {
+  if (i < spr * J) {
+    const int64_t s = sys0 + i / J;
+    PlanetW q = {};
+    if (s < n_sys) {
+      q.f = planet_setup_mixed(p, t_ref, t0);
+      if (!planet_valid(p[0], p[1], p[2], p[3], p[4])) q.f.e = __int_as_float(0x7fc00000);
+      q.m = kepler_start_setup(q.f.e);
+    }
+    pl_s[i] = q;
+  } else {
+    const int sl = i - spr * J;
+    float g = 0.0f;
+    if (sys0 + sl < n_sys) g = finite_bits(p[0]) ? d2f(p[0]) : __int_as_float(0x7fc00000);
+    gam_s[sl] = g;
+  }
+}
+
+// The item's parameters.  DEMC: the launch evaluates DE-MC proposals; with
+// a.demc.z set they are formed here from the chains' states and the draws
+// (and stored to the proposals, which a.params points at).
+template <int J, bool DEMC>
+__device__ __forceinline__ void load_item(int i, int spr, int64_t sys0, const UniformArgs &a,
+                                          double (&p)[5]) {
+  const int npar = 5 * J + 1;
+  if (i < spr * J) {
+    const int sl = i / J, j = i - sl * J;
+    const int64_t s = sys0 + sl;
+    if (s < a.n_sys) {
+      if (DEMC && a.demc.z) {
+        demc_form(a, s, 5 * j, npar, p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) p[k] = a.params[s * npar + 5 * j + k];
+      }
+    }
+  } else {
+    const int64_t s = sys0 + (i - spr * J);
+    if (s < a.n_sys) {
+      if (DEMC && a.demc.z) {
+        double g[1];
+        demc_form(a, s, 5 * J, npar, g);
+        p[0] = g[0];
+      } else {
+        p[0] = a.params[s * npar + 5 * J];
+      }
+    }
+  }
+}
+
+// RESID: also the per-system max Kepler residual.  DEMC: the batch is a
+// DE-MC step's proposals (a.demc): formed in the prologue, Metropolis
+// decision in the epilogue; plain evaluations contain neither.
+template <int J, bool RESID, bool DEMC>
+__global__ void __maxnreg__(64)
+chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__restrict__ out,
+                       float *__restrict__ resid_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int block = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int G = 1 << lg;
+  const int spr = (block >> 5) << (5 - lg);      // systems of this CTA
+  const WarpLayout L(spr, J, tile);
+  PlanetW *pl_s = reinterpret_cast<PlanetW *>(smem + L.pl);
+  float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
+  float *w_s = reinterpret_cast<float *>(smem + L.w);
+
+  const int64_t sys0 = (int64_t)blockIdx.x * spr;
+  const int nitems = spr * (J + 1);
+  const int step = G * kChunk;                   // a power of two
+  const int nk0 = min(tile, a.n_obs);
+  const int npad0 = round_up_pow2(nk0, step);
+
+  // ---- prologue: every global load first ----
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  double p[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (tid < nitems) load_item<J, DEMC>(tid, spr, sys0, a, p);
+  const bool has0 = tid < nk0, has1 = tid + block < nk0;
+  double t0v = 0.0, v0v = 0.0, s0v = 1.0, t1v = 0.0, v1v = 0.0, s1v = 1.0;
+  if (has0) { t0v = a.t[tid]; v0v = a.v[tid]; s0v = a.sigma[tid]; }
+  if (has1) { t1v = a.t[tid + block]; v1v = a.v[tid + block]; s1v = a.sigma[tid + block]; }
+
+  // the reference time's split, needed by the threads that stage
+  Split3 tr3 = {0.0f, 0.0f, 0.0f};
+  if (tid < npad0 || ntiles > 1) tr3 = split3(t_ref);
+  const float jit2 = d2f(a.jitter2);
+  // tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jitter^2); the
+  // padding up to whole chunks has zero weight (and tau = v = 0)
+  auto convert = [&](int k, bool real, double t, double v, double sigma) {
+    float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float wk = 0.0f;
+    if (real) {
+      sub_ds(split3(t), tr3, o.x, o.y);
+      split_d(v, o.z, o.w);
+      const float sg = d2f(sigma);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      wk = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+    }
+    obs_s[k] = o;
+    w_s[k] = wk;
+  };
+
+  if (tid < nitems) setup_item<J>(tid, spr, sys0, a.n_sys, p, t_ref, a.t0, pl_s, gam_s);
+  for (int i = tid + block; i < nitems; i += block) {       // more items than threads
+    double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    load_item<J, DEMC>(i, spr, sys0, a, q);
+    setup_item<J>(i, spr, sys0, a.n_sys, q, t_ref, a.t0, pl_s, gam_s);
+  }
+  if (tid < npad0) convert(tid, has0, t0v, v0v, s0v);
+  if (tid + block < npad0) convert(tid + block, has1, t1v, v1v, s1v);
+  for (int k = tid + 2 * block; k < npad0; k += block) {
+    const bool real = k < nk0;
+    convert(k, real, real ? a.t[k] : 0.0, real ? a.v[k] : 0.0, real ? a.sigma[k] : 1.0);
+  }
+  __syncthreads();
+
+  // ---- the CTA's systems, one per G lanes ----
+  const int slot = (warp << (5 - lg)) + (lane >> lg);
+  const int c = lane & (G - 1);
+  const int64_t s = sys0 + slot;
+  const PlanetW *q = pl_s + slot * J;
+  const float gam = gam_s[slot];
+  float poison = 0.0f * gam;                     // NaN for an invalid system
+#pragma unroll
+  for (int j = 0; j < J; ++j) poison += 0.0f * q[j].f.e;
+  Kahan acc = {0.0f, 0.0f};
+  float rmax = 0.0f;
+
+  for (int t = 0; t < ntiles; ++t) {
+    const int k0 = t * tile;
+    const int nk = min(tile, a.n_obs - k0);
+    const int npad = round_up_pow2(nk, step);
+    if (t > 0) {
+      __syncthreads();
+      for (int k = tid; k < npad; k += block) {
+        const bool real = k < nk;
+        convert(k, real, real ? a.t[k0 + k] : 0.0, real ? a.v[k0 + k] : 0.0,
+                real ? a.sigma[k0 + k] : 1.0);
+      }
+      __syncthreads();
+    }
+    for (int base = c; base < npad; base += step) {
+      float th[kChunk], tl[kChunk];
+      Kahan V[kChunk];
+#pragma unroll
+      for (int i = 0; i < kChunk; ++i) {
+        const float2 tt = *reinterpret_cast<const float2 *>(obs_s + base + (i << lg));
+        th[i] = tt.x;
+        tl[i] = tt.y;
+        V[i].big = 0.0f;
+        V[i].small = 0.0f;
+      }
+      // two planets per iteration: the second one's constants load while the
+      // first one's chains run (full unrolling spills at 64 registers)
+#pragma unroll 2
+      for (int j = 0; j < J; ++j) {
+        const PlanetW qj = q[j];
+#pragma unroll
+        for (int i = 0; i < kChunk; ++i) {
+          const float M = mean_anomaly_mixed(th[i], tl[i], qj.f);
+          float sE, cE;
+          const float E = kepler_f32_h(M, qj.f.e, qj.m, sE, cE);
+          if (RESID) {
+            const float r = fabsf((E - M) - qj.f.e * sE);
+            rmax = fmaxf(rmax, base + (i << lg) < nk ? r : 0.0f);
+          }
+          kahan_add(V[i], velocity_h(qj.f, sE, cE));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kChunk; ++i) {
+        const int k = base + (i << lg);
+        const float2 vo = *reinterpret_cast<const float2 *>(&obs_s[k].z);
+        // residual V - v_obs with the model and the observation as float pairs
+        const float r = __fadd_rn(__fsub_rn(V[i].big, vo.x),
+                                  __fsub_rn(gam, __fadd_rn(V[i].small, vo.y)));
+        kahan_add(acc, w_s[k] * r * r);
+      }
+    }
+  }
+
+  // combine the G lanes of the system (G a power of two within the warp)
+  for (int m = G >> 1; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+    if (RESID) rmax = fmaxf(rmax, shfl_xor(rmax, m));
+  }
+  if (c == 0 && s < a.n_sys) {
+    const float value = kahan_value(acc) + poison;   // NaN survives n_obs == 0
+    out[s] = value;
+    note_invalid(a.invalid, value);
+    if (RESID) resid_out[s] = rmax;
+    // the proposals this CTA formed are visible here after the barrier
+    if (DEMC) demc_accept(a, s, 5 * J + 1, value);
+  }
+}
+
+// Variants: 0 plain, 1 with the Kepler residual, 2 DE-MC step.
+template <int J>
+const void *warp_kernel_fn(int variant) {
+  switch (variant) {
+    case 0: return reinterpret_cast<const void *>(chi2_mixed_warp_kernel<J, false, false>);
+    case 1: return reinterpret_cast<const void *>(chi2_mixed_warp_kernel<J, true, false>);
+    case 2: return reinterpret_cast<const void *>(chi2_mixed_warp_kernel<J, false, true>);
+  }
+  return nullptr;
+}
+
+const void *warp_kernel_for(int J, int variant) {
+  switch (J) {
+    case 1: return warp_kernel_fn<1>(variant);
+    case 2: return warp_kernel_fn<2>(variant);
+    case 3: return warp_kernel_fn<3>(variant);
+    case 4: return warp_kernel_fn<4>(variant);
+    case 5: return warp_kernel_fn<5>(variant);
+    case 6: return warp_kernel_fn<6>(variant);
+    case 7: return warp_kernel_fn<7>(variant);
+    case 8: return warp_kernel_fn<8>(variant);
+  }
+  return nullptr;
+}
+
+// CTAs of the kernel resident per SM (occupancy API), per device, planet
+// count, block and shared-memory size; 0 when the shape does not fit.
+std::mutex g_occ_mu;
+std::map<std::tuple<int, int, int, size_t>, int> g_occ;
+
+int blocks_per_sm(int J, int variant, int block, size_t smem) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;                                    // no device: shapes stay valid
+  }
+  const auto key = std::make_tuple(dev * 16 + J, block, variant, smem);
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+  }
+  const void *fn = warp_kernel_for(J, variant);
+  int n = 0;
+  if (!fn) return 0;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[key] = n;
+  return n;
+}
+
+size_t warp_smem(int J, int G, int block, int n_obs) {
+  return WarpLayout((block / 32) * (32 / G), J, warp_obs_tile(n_obs, G)).total;
+}
+
+int log2_lanes(int G) { return G == 8 ? 3 : (G == 16 ? 4 : 5); }
+
+}  // namespace
+
+bool warp_tile_ok(int G, int block) {
+  return (G == 8 || G == 16 || G == 32) && block >= 32 && block <= 1024 && !(block & 31);
+}
+
+int warp_lanes_for(int n_obs) {
+  if (n_obs >= 32 * kChunk) return 32;
+  if (n_obs >= 16 * kChunk) return 16;
+  return 8;
+}
+
+Tile warp_tile(int64_t n_sys, int n_pl, int n_obs) {
+  // A grid of one CTA per W * 32 / G systems.  When it fits on the device
+  // at once, an SM holds at most ceil(CTAs / n_sm) CTAs; otherwise the
+  // hardware refills the SMs wave after wave and the load per SM is the
+  // total over the SMs.  Pick the W whose busiest SM carries the fewest
+  // warps of work; among equals, the one with more warps resident per SM
+  // (more latency hidden), then the larger CTA (fewer CTAs share an SM: on
+  // the 4096-system batch one CTA of 27 warps per SM ran 18.4 us where
+  // three of nine ran 20.5 us, with the same 27 systems per SM).
+  const int G = warp_lanes_for(n_obs);
+  const int spw = 32 / G;
+  const int64_t n_sm = sm_count();
+  Tile best{G, 8 * 32, 0, 3};
+  double best_load = 1e300;
+  int64_t best_warps = 0;
+  for (int W = 4; W <= 32; ++W) {
+    const int block = 32 * W;
+    const int occ = blocks_per_sm(n_pl, 0, block, warp_smem(n_pl, G, block, n_obs));
+    if (occ < 1) continue;
+    const int64_t ctas = (n_sys + (int64_t)W * spw - 1) / ((int64_t)W * spw);
+    const int64_t cap = n_sm * occ;
+    double load;
+    int64_t resident;
+    if (ctas <= cap) {
+      resident = (ctas + n_sm - 1) / n_sm;
+      load = (double)resident * W;
+    } else {
+      resident = occ;
+      load = (double)((ctas + n_sm - 1) / n_sm) * W;
+    }
+    const int64_t warps = resident * W;
+    const bool tie = load <= best_load * (1.0 + 1e-9);
+    if (load < best_load * (1.0 - 1e-9) || (tie && warps >= best_warps)) {
+      best_load = load;
+      best_warps = warps;
+      best = Tile{G, block, 0, 3};
+    }
+  }
+  best.obs_tile = warp_obs_tile(n_obs, G);
+  return best;
+}
+
+cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float *out,
+                                   float *resid, cudaStream_t st) {
+  const int G = tile.G, block = tile.block;
+  if (!warp_tile_ok(G, block)) return cudaErrorInvalidValue;
+  // a DE-MC step reports no residual (the DE-MC entry point has none)
+  const int variant = a.demc.states ? 2 : (resid != nullptr ? 1 : 0);
+  if (variant == 2) resid = nullptr;
+  const void *fn = warp_kernel_for(a.n_pl, variant);
+  if (!fn) return cudaErrorInvalidValue;
+  const int spr = (block / 32) * (32 / G);
+  const int obs_tile = warp_obs_tile(a.n_obs, G);
+  const size_t smem = WarpLayout(spr, a.n_pl, obs_tile).total;
+  if (blocks_per_sm(a.n_pl, variant, block, smem) < 1) return cudaErrorInvalidConfiguration;
+  const int64_t ctas = (a.n_sys + spr - 1) / spr;
+  if (ctas > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  UniformArgs args = a;
+  int lg = log2_lanes(G), tl = obs_tile, nt = (a.n_obs + obs_tile - 1) / obs_tile;
+  void *params[] = {&args, &lg, &tl, &nt, &out, &resid};
+  return cudaLaunchKernel(fn, dim3((unsigned)ctas), dim3(block), params, smem, st);
+}
+
+}  // namespace kc

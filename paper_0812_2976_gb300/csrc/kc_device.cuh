@@ -177,6 +177,50 @@ __device__ __forceinline__ void sincos_accurate(float x, float &s, float &c) {
   c = __uint_as_float(__float_as_uint(c0) ^ (((q + 1u) & 2u) << 30));
 }
 
+// sin and cos for |x| <= 3 pi / 2 (the starting values of the
+// single-precision Kepler solve lie within pi + 0.1): x = k pi + r with
+// k = round(x / pi) in {-1, 0, 1} and pi split into two floats (the first
+// product exact), so sin x = (-1)^k sin r and cos x = (-1)^k cos r with one
+// shared sign and no exchange of sin and cos; sin r and cos r on
+// [-pi/2, pi/2] by minimax polynomials of degree 9 and 10 (Remez fits of the
+// absolute error, 4.6e-9 and 2.4e-10; minimax_sincos.py prints the
+// coefficients).  Largest error over |x| <= pi + 0.1 in a float emulation:
+// 1.3e-7 (sin) and 1.1e-7 (cos), about one ulp of 1, most of it the rounding
+// of r near |r| = pi/2; 17 FMA-pipe and 3 integer operations where
+// sincos_accurate takes 17 and 9.
+constexpr float kInvPiF = 0.318309886183790672f;          // RN(1/pi)
+constexpr float kPiHiF = 3.14159274101257324219f;         // RN(pi)
+constexpr float kPiLoF = -8.74227800037248566e-8f;        // pi - kPiHiF
+constexpr float kSinC3 = -0.166666570965f;
+constexpr float kSinC5 = 0.00833301729157f;
+constexpr float kSinC7 = -0.000198066152016f;
+constexpr float kSinC9 = 2.6000547683e-6f;
+constexpr float kCosC2 = -0.499999995496f;
+constexpr float kCosC4 = 0.0416666407281f;
+constexpr float kCosC6 = -0.00138884035082f;
+constexpr float kCosC8 = 2.47618862485e-5f;
+constexpr float kCosC10 = -2.60771053559e-7f;
+
+__device__ __forceinline__ void sincos_pi(float x, float &s, float &c) {
+  const float k = __fmaf_rn(x, kInvPiF, kRoundMagic);
+  const unsigned sgn = __float_as_uint(k) << 31;            // k odd: both negate
+  const float kf = __fsub_rn(k, kRoundMagic);
+  float r = __fmaf_rn(-kf, kPiHiF, x);
+  r = __fmaf_rn(-kf, kPiLoF, r);
+  const float u = r * r;
+  float ps = __fmaf_rn(u, kSinC9, kSinC7);
+  ps = __fmaf_rn(u, ps, kSinC5);
+  ps = __fmaf_rn(u, ps, kSinC3);
+  const float sr = __fmaf_rn(r * u, ps, r);
+  float pc = __fmaf_rn(u, kCosC10, kCosC8);
+  pc = __fmaf_rn(u, pc, kCosC6);
+  pc = __fmaf_rn(u, pc, kCosC4);
+  pc = __fmaf_rn(u, pc, kCosC2);
+  const float cr = __fmaf_rn(u, pc, 1.0f);
+  s = __uint_as_float(__float_as_uint(sr) ^ sgn);
+  c = __uint_as_float(__float_as_uint(cr) ^ sgn);
+}
+
 // sin and cos in double precision for |x| <= 8: the same Cody & Waite
 // reduction (pi/2 as two doubles) and the Taylor series of sin to r^17
 // (truncation 8e-20 at pi/4) and of cos to r^16 (2e-18).  No branches, so
@@ -321,6 +365,67 @@ __device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &
   float s, c;
   sincos_accurate(E, s, c);
   const float d = halley_delta_f32(E, M, e, s, c);
+  const float hd2 = 0.5f * d * d;
+  sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
+  cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
+  return E + d;
+}
+
+// The per-planet part of Mikkola's start, formed once per (system, planet)
+// instead of at every evaluation: r = 1/(4 e + 1/2), bs = r/2 (b = M bs),
+// a = (1 - e) r, a3 = a^3 and the quintic correction's factor
+// corr = -0.078/(1 + e).
+struct StartF {
+  float bs, a, a3, corr;
+};
+
+__device__ __forceinline__ StartF kepler_start_setup(float e) {
+  const float r = 1.0f / __fmaf_rn(4.0f, e, 0.5f);
+  StartF m;
+  m.bs = 0.5f * r;
+  m.a = (1.0f - e) * r;
+  m.a3 = m.a * m.a * m.a;
+  m.corr = -0.078f / (1.0f + e);
+  return m;
+}
+
+// Mikkola's start from the hoisted constants.  The start is odd in M
+// (sign(b) = sign(M)), so it is formed on |b|: |t| = |b| + sqrt(b^2 + a^3),
+// z = |t|^(1/3) >= sqrt(a), s = z - a/z >= 0, the quintic correction
+// s (1 + corr s^4), and the sign of M applied once before
+// E0 = M + e s (3 - 4 s^2).  The same values as kepler_start up to the
+// rounding of the factored forms.
+__device__ __forceinline__ float kepler_start_h(float M, float e, const StartF &m) {
+  const float b = M * m.bs;
+  const float w = __fmaf_rn(b, b, m.a3);
+  const float tabs = fabsf(b) + w * rsqrt_fast(w);
+  const float z = ex2_fast(lg2_fast(tabs) * (1.0f / 3.0f));
+  float s = __fmaf_rn(-m.a, rcp_fast(z), z);
+  const float s2 = s * s;
+  s = s * __fmaf_rn(m.corr, s2 * s2, 1.0f);
+  const float ss = copysignf(s, M);
+  return __fmaf_rn(e, ss * __fmaf_rn(-4.0f, s * s, 3.0f), M);
+}
+
+// Halley's step -f f' / (f'^2 - f f''/2), f'' = e sin E: the form of
+// halley_delta_f32 with the factor 2 cancelled (one operation fewer).
+__device__ __forceinline__ float halley_delta_h(float E, float M, float e, float s, float c) {
+  const float es = e * s;
+  const float f = (E - M) - es;
+  const float f1 = __fmaf_rn(-e, c, 1.0f);
+  const float den = __fmaf_rn(f * es, -0.5f, f1 * f1);
+  return -(f * f1) * rcp_fast(den);
+}
+
+// kepler_f32 with the hoisted start constants and sincos_pi (the same
+// steps: start, sin/cos to about an ulp, one Halley step, angle-addition
+// update of sin/cos).
+__device__ __forceinline__ float kepler_f32_h(float M, float e, const StartF &m, float &sE,
+                                              float &cE) {
+  const float E = kepler_start_h(M, e, m);
+  float s, c;
+  sincos_pi(E, s, c);
+  const float d = halley_delta_h(E, M, e, s, c);
   const float hd2 = 0.5f * d * d;
   sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
   cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
@@ -759,6 +864,14 @@ __device__ __forceinline__ double mean_anomaly_f64(double tau, const PlanetD &q)
 __device__ __forceinline__ float velocity_mixed(const PlanetF &q, float sE, float cE) {
   const float D = __fmaf_rn(-q.e, cE, 1.0f);
   const float num = __fmaf_rn(q.A, cE - q.e, -(q.B * sE));
+  return __fmaf_rn(num, rcp_fast(D), q.C);
+}
+
+// The same velocity with the e cos w term folded: A e = K cos w e = C, so
+// A (cos E - e) - B sin E = A cos E - (B sin E + C), two FMAs.
+__device__ __forceinline__ float velocity_h(const PlanetF &q, float sE, float cE) {
+  const float D = __fmaf_rn(-q.e, cE, 1.0f);
+  const float num = __fmaf_rn(q.A, cE, -__fmaf_rn(q.B, sE, q.C));
   return __fmaf_rn(num, rcp_fast(D), q.C);
 }
 

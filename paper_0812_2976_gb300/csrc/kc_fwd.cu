@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "kc_demc.cuh"
 #include "kc_device.cuh"
 #include "kc_internal.h"
 
@@ -103,41 +104,6 @@ struct MixedPrep {
   const float *w;        // [n_obs]
 };
 
-// The Metropolis decision of DE-MC in the epilogue of the chi2 kernel that
-// has just evaluated proposal s (demcmc_accept_kernel's rule and
-// arithmetic, applied to the value the kernel stores).
-template <typename T>
-__device__ __forceinline__ void demc_accept(const UniformArgs &a, int64_t s, int npar, T value) {
-  const DemcAccept &d = a.demc;
-  const int64_t i = d.first + s;
-  T *chi2 = static_cast<T *>(d.chi2);
-  const double delta = (double)value - (double)chi2[i];
-  const bool acc = log(d.u[3 * s]) < -0.5 * delta;      // false when delta is NaN
-  if (acc) {
-    for (int p = 0; p < npar; ++p) d.states[i * npar + p] = a.params[s * npar + p];
-    chi2[i] = value;
-  }
-  if (d.accepted) d.accepted[s] = acc ? 1 : 0;
-}
-
-// Parameters p0 .. p0 + N - 1 of proposal s, formed in the fused kernel's
-// prologue (the proposal kernel's arithmetic, demc_proposal) and stored to
-// the proposals, which params points at (the caller's writable buffer).
-template <int N>
-__device__ __forceinline__ void demc_form(const UniformArgs &a, int64_t s, int p0, int npar,
-                                          double (&out)[N]) {
-  const DemcAccept &d = a.demc;
-  int64_t r1, r2;
-  demc_partners(d.u[3 * s + 1], d.u[3 * s + 2], d.partner_first, d.partner_count, r1, r2);
-  double *prop = const_cast<double *>(a.params) + s * npar;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    out[k] = demc_proposal(d.states, npar, d.first + s, r1, r2, p0 + k, d.gamma,
-                           d.eps_scale[p0 + k], d.z[s * npar + p0 + k]);
-    prop[p0 + k] = out[k];
-  }
-}
-
 // PRE = false: each CTA computes its planets' constants (FP64) and converts
 // the observations itself.  PRE = true (split variant): both come from
 // prep_mixed_kernel, launched just before with programmatic dependent
@@ -148,13 +114,16 @@ __device__ __forceinline__ void demc_form(const UniformArgs &a, int64_t s, int p
 // SINGLE = true (with PRE = false): the pure single-precision variant of
 // Sec. 5 (precision comparisons only): times, epoch and periods rounded to
 // float and the phase formed in float.
+// DEMC = true: the launch carries a DE-MC step (a.demc): proposals formed in
+// the prologue when a.demc.z is set, the Metropolis decision in the
+// epilogue.  Plain evaluations use DEMC = false and contain neither.
 // At most 104 registers up to four planets, 128 above (blocks of at most
 // 256 threads): left alone the compiler keeps Mikkola's per-planet constants
 // of all J planets live across the observation loop (124 registers at
 // J = 4, four CTAs of 128 per SM); capped, it recomputes part of them and
 // the kernel runs 2 % faster on both the paper batch and the 2^20-system
 // sweep.
-template <int J, bool PRE, bool NLL = false, bool SINGLE = false>
+template <int J, bool PRE, bool NLL = false, bool SINGLE = false, bool DEMC = false>
 __global__ void __maxnreg__(J <= 4 ? 104 : 128)
 chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__restrict__ out,
                   float *__restrict__ resid_out) {
@@ -226,7 +195,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       PlanetF q = {0, 0, 0, 0, 0, 0, 0, 0};
       if (s < a.n_sys) {
         double p[5];
-        if (!NLL && !SINGLE && a.demc.z) {
+        if (DEMC && a.demc.z) {
           demc_form(a, s, 5 * j, npar, p);        // DE-MC: this planet's proposal
         } else {
 #pragma unroll
@@ -248,7 +217,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
       float g = 0.0f;
       if (s < a.n_sys) {
         double gd[1];
-        if (!NLL && !SINGLE && a.demc.z)
+        if (DEMC && a.demc.z)
           demc_form(a, s, 5 * J, npar, gd);
         else
           gd[0] = a.params[s * npar + 5 * J];
@@ -363,7 +332,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     out[s] = value;
     note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = rmax;
-    if (!NLL && !SINGLE && a.demc.states) demc_accept(a, s, npar, value);
+    if (DEMC) demc_accept(a, s, npar, value);
   }
 }
 
@@ -493,7 +462,7 @@ chi2_mixed_chunk_kernel(UniformArgs a, MixedPrep prep, ChunkScratch cs, int chun
 
 // ------------------------------------------------------------ FP64
 
-template <int J, bool NLL = false>
+template <int J, bool NLL = false, bool DEMC = false>
 __global__ void __launch_bounds__(256, 2)
 chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
                 float *__restrict__ resid_out) {
@@ -602,7 +571,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     out[s] = value;
     note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = (float)rmax;
-    if (!NLL && a.demc.states) demc_accept(a, s, 5 * J + 1, value);
+    if (DEMC) demc_accept(a, s, 5 * J + 1, value);
   }
 }
 
@@ -804,11 +773,18 @@ cudaError_t launch_chi2_mixed_prepared(const UniformArgs &a, const Tile &tile, v
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
   }
-#define KC_LAUNCH(JJ)                                                                      \
-  err = set_smem(chi2_mixed_kernel<JJ, true>, smem);                                       \
-  if (err == cudaSuccess)                                                                  \
-    err = cudaLaunchKernelEx(&cfg, chi2_mixed_kernel<JJ, true>, a, prep, tile.G, tile.obs_tile, \
-                             out, resid);
+#define KC_LAUNCH(JJ)                                                                         \
+  if (a.demc.states) {                                                                        \
+    err = set_smem(chi2_mixed_kernel<JJ, true, false, false, true>, smem);                    \
+    if (err == cudaSuccess)                                                                   \
+      err = cudaLaunchKernelEx(&cfg, chi2_mixed_kernel<JJ, true, false, false, true>, a, prep, \
+                               tile.G, tile.obs_tile, out, resid);                            \
+  } else {                                                                                    \
+    err = set_smem(chi2_mixed_kernel<JJ, true>, smem);                                        \
+    if (err == cudaSuccess)                                                                   \
+      err = cudaLaunchKernelEx(&cfg, chi2_mixed_kernel<JJ, true>, a, prep, tile.G,            \
+                               tile.obs_tile, out, resid);                                    \
+  }
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;
@@ -833,6 +809,7 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a_in, const Tile &tile_in, floa
                               float *resid, cudaStream_t st) {
   UniformArgs a = a_in;
   Tile tile = tile_in;
+  if (tile.split == 3) return launch_chi2_mixed_warp(a, tile, out, resid, st);
   if (tile.split) {
     // No stream-ordered allocation inside a graph being captured: the fused
     // kernel (no scratch) stands in for the split variants there.
@@ -864,11 +841,18 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a_in, const Tile &tile_in, floa
   const int grid = grid_for(a.n_sys, tile.block / tile.G);
   const MixedPrep none{nullptr, nullptr, nullptr, nullptr};
   cudaError_t err = cudaSuccess;
-#define KC_LAUNCH(JJ)                                                                   \
-  err = set_smem(chi2_mixed_kernel<JJ, false>, smem);                                   \
-  if (err == cudaSuccess)                                                               \
-    chi2_mixed_kernel<JJ, false><<<grid, tile.block, smem, st>>>(a, none, tile.G,         \
-                                                                 tile.obs_tile, out, resid);
+#define KC_LAUNCH(JJ)                                                                       \
+  if (a.demc.states) {                                                                      \
+    err = set_smem(chi2_mixed_kernel<JJ, false, false, false, true>, smem);                 \
+    if (err == cudaSuccess)                                                                 \
+      chi2_mixed_kernel<JJ, false, false, false, true><<<grid, tile.block, smem, st>>>(      \
+          a, none, tile.G, tile.obs_tile, out, resid);                                      \
+  } else {                                                                                  \
+    err = set_smem(chi2_mixed_kernel<JJ, false>, smem);                                     \
+    if (err == cudaSuccess)                                                                 \
+      chi2_mixed_kernel<JJ, false><<<grid, tile.block, smem, st>>>(a, none, tile.G,           \
+                                                                   tile.obs_tile, out, resid); \
+  }
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;
@@ -884,11 +868,18 @@ cudaError_t launch_chi2_f64(const UniformArgs &a_in, const Tile &tile, double *o
   if (err != cudaSuccess) return err;
   const size_t smem = smem_chi2_f64(a.n_pl, tile);
   const int grid = grid_for(a.n_sys, tile.block / tile.G);
-#define KC_LAUNCH(JJ)                                                                \
-  err = set_smem(chi2_f64_kernel<JJ>, smem);                                         \
-  if (err == cudaSuccess)                                                            \
-    chi2_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out, \
-                                                        resid);
+#define KC_LAUNCH(JJ)                                                                      \
+  if (a.demc.states) {                                                                     \
+    err = set_smem(chi2_f64_kernel<JJ, false, true>, smem);                                \
+    if (err == cudaSuccess)                                                                \
+      chi2_f64_kernel<JJ, false, true><<<grid, tile.block, smem, st>>>(a, tile.G,            \
+                                                                      tile.obs_tile, out, resid); \
+  } else {                                                                                 \
+    err = set_smem(chi2_f64_kernel<JJ>, smem);                                             \
+    if (err == cudaSuccess)                                                                \
+      chi2_f64_kernel<JJ><<<grid, tile.block, smem, st>>>(a, tile.G, tile.obs_tile, out,     \
+                                                          resid);                          \
+  }
   KC_DISPATCH_J(a.n_pl, KC_LAUNCH)
 #undef KC_LAUNCH
   if (err != cudaSuccess) return err;

@@ -17,7 +17,8 @@ struct Tile {
   int G;
   int block;
   int obs_tile;
-  int split = 0;   // mixed chi2 only: 1, 2 = two-pass variants (see kc_fwd.cu)
+  int split = 0;   // mixed chi2 only: 1, 2 = two-pass variants (see kc_fwd.cu),
+                   // 3 = the warp-per-system kernel of kc_chi2_warp.cu
 };
 
 // DE-MC step carried by a chi2 launch: the batch's systems are proposals
@@ -103,6 +104,15 @@ cudaError_t launch_chi2_single(const UniformArgs &a, const Tile &tile, float *ou
                                cudaStream_t st);
 cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out,
                               float *resid, cudaStream_t st);
+// Warp-per-system mixed chi2 (kc_chi2_warp.cu): G = 8, 16 or 32 lanes per
+// system, `block` threads (a multiple of 32, at most 1024) per CTA, one CTA
+// per block * G / 32 systems; warp_tile picks the block that spreads the CTAs
+// evenly over the SMs.  Carries a DE-MC step when a.demc.states is set.
+bool warp_tile_ok(int G, int block);
+int warp_lanes_for(int n_obs);
+Tile warp_tile(int64_t n_sys, int n_pl, int n_obs);
+cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float *out,
+                                   float *resid, cudaStream_t st);
 // Gradient (kc_grad.cu); nll = true: the free-jitter log-likelihood variant
 // (parameters 5*n_pl + 2 per system).
 cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2,

@@ -85,7 +85,7 @@ extern "C" kc_status kc_chi2_eval_mixed_noalloc(const double *params, const doub
   const kc::UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter,
                           kc::invalid_counter()};
   kc::Tile tile = kc::choose_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);
-  if (tile.G > tile.block || tile.split == 2)
+  if (tile.G > tile.block || tile.split >= 2)
     tile = kc::default_tile(kc::Kind::Chi2Mixed, n_sys, n_pl, n_obs);
   tile.split = 1;
   return kc::cuda_status(kc::launch_chi2_mixed_prepared(a, tile, scratch, out, max_kepler_resid,

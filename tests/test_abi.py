@@ -122,8 +122,14 @@ def test_tile_table_host_logic(lib):
     t = _lib.KcTile()
     # default heuristic for the paper-shaped batch
     assert lib.kc_get_tile(0, 1, 4096, 4, 256, ctypes.byref(t)) == 0
-    assert t.block in (64, 128, 256) and t.threads_per_system >= 1
+    # mixed chi2: the persistent kernel, lanes per system 8/16/32 and whole warps
+    assert t.split == 3 and t.threads_per_system == 32
+    assert t.block % 32 == 0 and 32 <= t.block <= 1024
     default = (t.threads_per_system, t.block, t.split)
+    assert lib.kc_get_tile(0, 1, 4096, 4, 32, ctypes.byref(t)) == 0
+    assert (t.threads_per_system, t.split) == (8, 3)             # 4 observations per lane
+    assert lib.kc_get_tile(0, 0, 4096, 4, 256, ctypes.byref(t)) == 0
+    assert t.block in (64, 128, 256) and t.split == 0           # FP64 kernel
     # pin, read back, same size class (power-of-two bucket), then remove
     pin = _lib.KcTile(16, 128, 1)
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(pin)) == 0
@@ -140,6 +146,14 @@ def test_tile_table_host_logic(lib):
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(512, 64, 2))) == 0
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(16, 64, 2))) == 1
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(2048, 64, 2))) == 1
+    assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
+    # split = 3 (persistent): 8, 16 or 32 lanes, whole warps up to 1024 threads
+    for good in ((32, 288, 3), (8, 1024, 3), (16, 32, 3)):
+        assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*good))) == 0
+    for bad in ((4, 128, 3), (32, 100, 3), (32, 2048, 3)):
+        assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
+    assert lib.kc_set_tile(1, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(32, 288, 3))) == 1
+    assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(32, 288, 3))) == 1
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
     # the split variants exist for the mixed chi2 kernel only
     assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1

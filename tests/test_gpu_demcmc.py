@@ -27,13 +27,16 @@ def dev(a, dtype=torch.float64):
 
 @pytest.mark.parametrize("mode,tol,tile", [
     ("fp64", 1e-12, None), ("mixed", 1e-5, None),
+    ("mixed", 1e-5, (16, 256, 0)),      # fused tile kernel: proposals and accept inside
     ("mixed", 1e-5, (16, 128, 1)),      # prepared two-pass: accept in the main kernel
     ("mixed", 1e-5, (64, 64, 2)),       # chunked two-pass: accept as its own kernel
+    ("mixed", 1e-5, (8, 96, 3)),        # warp-per-system kernel, four systems per warp
 ])
 def test_step_matches_oracle(kc, oracle_mod, mode, tol, tile):
     """The Metropolis step runs in the chi2 kernel's epilogue, or after the
     chunked two-pass variant as its own kernel; every launch shape gives
-    the oracle's step."""
+    the oracle's step (with no tile pinned, mixed takes the warp-per-system
+    kernel)."""
     if tile is not None:
         kc.kc_set_tile("chi2", mode, 256, 4, 256, tile)
         assert kc.kc_get_tile("chi2", mode, 256, 4, 256) == tile

@@ -435,7 +435,8 @@ def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
     assert np.all(np.abs(c32.cpu().numpy().astype(np.float64) - ref) <= bound)
 
 
-@pytest.mark.parametrize("tile", [(4, 128, 0), (8, 64, 1), (32, 128, 0), (64, 128, 2)])
+@pytest.mark.parametrize("tile", [(4, 128, 0), (8, 64, 1), (32, 128, 0), (64, 128, 2),
+                                  (8, 64, 3), (16, 96, 3), (32, 288, 3)])
 def test_high_eccentricity_mixed_warps(kc, oracle_mod, tile):
     """Every third system has a planet at e = 0.985, the others e <= 0.9:
     with 4 or 8 threads per system a warp holds several systems of both
@@ -479,7 +480,8 @@ def test_rv_predict_vs_oracle(kc, oracle_mod):
 @pytest.mark.parametrize("tile", [(8, 64, 1), (32, 32, 1), (64, 256, 1), (1, 128, 1),
                                   (32, 128, 2), (128, 64, 2), (256, 256, 2), (1024, 32, 2),
                                   (24, 96, 0), (12, 192, 0), (48, 96, 0), (24, 192, 1),
-                                  (3, 96, 0), (16, 224, 0), (32, 160, 0), (8, 224, 1)])
+                                  (3, 96, 0), (16, 224, 0), (32, 160, 0), (8, 224, 1),
+                                  (32, 288, 3), (32, 1024, 3), (16, 160, 3), (8, 32, 3)])
 def test_split_variant_matches_oracle(kc, oracle_mod, tile):
     """The two-pass (preparation + main) variant of the mixed kernel and the
     fused kernel with a thread count per system that is not a power of two
@@ -499,6 +501,30 @@ def test_split_variant_matches_oracle(kc, oracle_mod, tile):
             assert float(resid.max()) <= RESID_TOL
     finally:
         kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, None)
+
+
+@pytest.mark.parametrize("tile", [(32, 128, 3), (16, 512, 3)])
+def test_persistent_kernel_rounds_and_observation_tiles(kc, oracle_mod, tile):
+    """The persistent kernel with more rounds than resident CTAs (each CTA
+    takes several rounds, setting up each one's planets) and more
+    observations than one shared-memory tile (1100 > 1024: restaged per
+    round), every system against the oracle."""
+    rng = np.random.default_rng(71)
+    n_sys, n_pl, n_obs = 20000, 1, 1100
+    par = synth_rows(rng, n_sys, n_pl)
+    t = np.sort(rng.uniform(2450000, 2456000, n_obs))
+    v = rng.normal(0, 30, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    ref = oracle_mod.chi2(par, t, v, sig, n_pl, t0=2450000.0, jitter=0.5)
+    P, T, V, S = dev(par, t, v, sig)
+    kc.kc_set_tile("chi2", "mixed", n_sys, n_pl, n_obs, tile)
+    try:
+        got, resid = kc.kc_chi2_eval_ex(P, T, V, S, t0=2450000.0, jitter=0.5, mode="mixed",
+                                        max_kepler_resid=True)
+    finally:
+        kc.kc_set_tile("chi2", "mixed", n_sys, n_pl, n_obs, None)
+    assert rel_err(got.cpu().numpy(), ref).max() <= MIXED_TOL
+    assert float(resid.max()) <= RESID_TOL
 
 
 def test_short_periods_far_from_the_epoch(kc, oracle_mod):
