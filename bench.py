@@ -45,15 +45,24 @@ FALLBACK_SM_MHZ = 2070.0
 # select operations not counted), from the algorithm as implemented:
 #   double-single mean anomaly 17, Mikkola's starting value 19 (its
 #   per-planet constants and the MUFU square root, logarithm, exponential
-#   and reciprocals not counted), one accurate sin/cos (Cody-Waite + Taylor)
-#   27, the Halley step 12, sin/cos update of the step 10, velocity 8,
-#   planet Kahan sum 4, and per observation the residual + weighted square +
-#   chi2 Kahan sum 10 (shared by n_pl planets).
+#   and reciprocals not counted), one accurate sin/cos 27, the Halley step
+#   (12 in the tile kernels, 11 in the warp-per-system kernel, whose form
+#   cancels the factor 2), sin/cos update of the step 10, velocity 8, planet
+#   Kahan sum 4, and per observation the residual + weighted square + chi2
+#   Kahan sum 10 (shared by n_pl planets).  The per-(system, planet) setup
+#   is not counted.
 KEPLER_MIXED_FLOPS = 19 + 27 + 12 + 10
 
 
-def mixed_flops_per_eval(n_pl: int) -> float:
-    return 17 + KEPLER_MIXED_FLOPS + 8 + 4 + 10.0 / n_pl
+def mixed_flops_per_eval(n_pl: int, warp: bool = False) -> float:
+    """FLOPs per evaluation of the tile kernels, or (warp=True) of the
+    warp-per-system kernel (tile split 3)."""
+    return 17 + KEPLER_MIXED_FLOPS - (1 if warp else 0) + 8 + 4 + 10.0 / n_pl
+
+
+def mixed_kernel_name(n_pl: int, tile) -> str:
+    return (f"chi2_mixed_warp_kernel<{n_pl}>" if tile[2] == 3 else
+            f"chi2_mixed_kernel<{n_pl}>")
 
 
 # The adjoint adds, per planet and observation: the velocity partials 26
@@ -94,11 +103,11 @@ F64_FLOPS_PER_EVAL = 10 + 20 + 13 + 8 + 11
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the mixed chi2 kernel in its current form, from an ncu capture of this
-# benchmark's own default workload (autotuned tile 16,256,0): the batch reads
-# its 688 KB of parameters and 6 KB of observations once (the rest is sector
-# granularity of the 168-byte parameter rows).  Keyed by (config, n_sys
-# override); other workloads report null.
-DRAM_BYTES_PER_LAUNCH = {(1, None): 765440}
+# benchmark's own default workload (tile 32,864,3, the warp-per-system
+# kernel): the batch reads its 688 KB of parameters and 6 KB of observations
+# once (the rest is sector granularity of the 168-byte parameter rows).
+# Keyed by (config, n_sys override, tile); other launches report null.
+DRAM_BYTES_PER_LAUNCH = {(1, None, (32, 864, 3)): 760832}
 
 
 def sm_count() -> int:
@@ -151,6 +160,26 @@ def kepler_throughput(kc, dev, stream, n=1 << 24):
     return out
 
 
+def oracle_subset(w, n_sub, grad=False):
+    """The FP64 oracle on n_sub evenly spaced systems of a uniform workload,
+    on the host cores (OpenMP over systems); planet-obs evals/s of chi2 (and
+    its gradient with grad).  Its observations are formed by the oracle
+    from the same seeded draws."""
+    import oracle
+    oracle.build()
+    v = oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
+    idx = np.unique(np.linspace(0, w.n_sys - 1, n_sub).astype(np.int64))
+    par = np.ascontiguousarray(w.params[idx])
+    oracle.chi2(par[:16], w.t, v, w.sigma, w.n_pl, w.t0, grad=grad)          # warm
+    t_start = time.perf_counter()
+    oracle.chi2(par, w.t, v, w.sigma, w.n_pl, w.t0, grad=grad)
+    el = time.perf_counter() - t_start
+    return {"value": idx.size * w.n_pl * w.n_obs / el, "unit": "planet-obs evals/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{idx.size} evenly spaced systems of {w.n_sys}, chi2"
+                      f"{' + gradient' if grad else ''}, {el:.2f} s wall"}
+
+
 def grid_sweep_throughput(kc, synth, dev, stream, args):
     """Mixed chi2 on the 2^20-system sweep (config 2), autotuned."""
     import torch
@@ -176,10 +205,19 @@ def grid_sweep_throughput(kc, synth, dev, stream, args):
     sec = a.elapsed_time(b) / 1e3 / steps
     evals = w.n_sys * w.n_pl * w.n_obs
     val = evals / sec
+    tile = kc.kc_get_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs)
+    fpe = mixed_flops_per_eval(w.n_pl, warp=tile[2] == 3)
     peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
-    return {"value": val, "unit": "planet-obs evals/s", "ms_per_step": 1e3 * sec,
-            "n_sys": w.n_sys, "roofline_frac": val * mixed_flops_per_eval(w.n_pl) / 1e12 / peak,
-            "inputs": "176 MB of parameters > L2"}
+    out = {"value": val, "unit": "planet-obs evals/s", "ms_per_step": 1e3 * sec,
+           "n_sys": w.n_sys, "roofline_frac": val * fpe / 1e12 / peak,
+           "roofline": {"bound": "alu", "achieved": val * fpe / 1e12, "peak": peak,
+                        "unit": "TFLOP/s", "frac": val * fpe / 1e12 / peak,
+                        "flops_per_eval": fpe, "kernel": mixed_kernel_name(w.n_pl, tile)},
+           "tile": {"threads_per_system": tile[0], "block": tile[1], "split": tile[2]},
+           "inputs": "176 MB of parameters > L2"}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_subset(w, 16384)
+    return out
 
 
 def gradient_throughput(kc, synth, dev, stream, args):
@@ -219,6 +257,8 @@ def gradient_throughput(kc, synth, dev, stream, args):
         torch.cuda.synchronize(dev)
         out[name] = evals * reps / (a.elapsed_time(b) / 1e3)
     peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_subset(w, 16384, grad=True)
     out["roofline_alu"] = {
         "peak": peak, "unit": "TFLOP/s",
         "chi2_grad_frac": out["chi2_grad"] * grad_flops_per_eval(w.n_pl) / 1e12 / peak,
@@ -270,6 +310,8 @@ def parse_args():
                     help="config 4: time the forward plan only")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 / grid-sweep side measurements")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the ragged-batch side measurement of the default run")
     return ap.parse_args()
 
 
@@ -553,6 +595,24 @@ def run_kc(args):
     e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the same steps on the host's clock: back-to-back calls through the
+    # binding and the C ABI (ctypes, argument checks, launch) with their
+    # copies, one synchronise at the end; no GPU hold, no L2 flush
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    wall_s = time.perf_counter() - wall0
+    if world > 1:
+        from paper_0812_2976_gb300 import dist as kdist
+        wall_s = kdist.max_over_ranks(wall_s, device=dev)
+    e2e_wall = {"value": evals * args.steps * world / wall_s, "unit": "planet-obs evals/s",
+                "ms_per_step": 1e3 * wall_s / args.steps,
+                "how": "time.perf_counter around the timed steps of the e2e leg issued back "
+                       "to back (H2D copy, kc_chi2_eval_mixed, D2H copy), final synchronise "
+                       "included"}
+
     extras = {}
     if not args.no_extras:
         # FP64 path on the same batch ("mixed vs FP64")
@@ -590,19 +650,23 @@ def run_kc(args):
         extras["grid_sweep"] = grid_sweep_throughput(kc, synth, dev, stream, args)
         extras["gradient"] = gradient_throughput(kc, synth, dev, stream, args)
         extras["demcmc"] = demcmc_throughput(kc, w, P, T, V, S, dev)
+        if world == 1 and not args.no_ragged:
+            extras["ragged"] = ragged_measure(kc, synth, dev, stream, flush, args, compact=True)
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", FALLBACK_SM_MHZ)
     peak_tflops = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz * 1e6 / 1e12
-    flops = mixed_flops_per_eval(w.n_pl) * evals
+    warp = tile[2] == 3
+    flops = mixed_flops_per_eval(w.n_pl, warp) * evals
     achieved = flops / (t_sum / args.steps) / 1e12          # one GPU's launch
-    traffic = DRAM_BYTES_PER_LAUNCH.get((args.config, args.n_sys)) if world == 1 else None
+    traffic = (DRAM_BYTES_PER_LAUNCH.get((args.config, args.n_sys, tuple(tile)))
+               if world == 1 else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": f"chi2_mixed_kernel<{w.n_pl}>",
+                "kernel": mixed_kernel_name(w.n_pl, tile),
                 "peak_basis": f"FP32 FMA pipe: {sm_count()} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP "
                               f"x {sm_mhz:.0f} MHz ({pk_kind} max SM clock)",
-                "flops_per_eval": mixed_flops_per_eval(w.n_pl)}
+                "flops_per_eval": mixed_flops_per_eval(w.n_pl, warp)}
 
     if rank != 0:
         return
@@ -618,6 +682,7 @@ def run_kc(args):
                             "split": tile[2], "how": tile_kind}},
         "roofline": roofline,
         "e2e": e2e,
+        "e2e_wall": e2e_wall,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -665,9 +730,9 @@ def time_steps(fn, steps, stream, flush):
 
 
 def run_kc_ragged(args):
-    """Config 4: 200000 systems with their own n_obs ~ U[16,1024] and
-    n_pl ~ U{1..6}; one step = forward chi2 + gradient of every system in
-    one persistent, graph-replayed launch (kc_plan_run)."""
+    """Config 4 as the headline: 200000 systems with their own n_obs ~
+    U[16,1024] and n_pl ~ U{1..6}; one step = forward chi2 + gradient of
+    every system in one persistent, graph-replayed launch (kc_plan_run)."""
     import torch
     world, rank, local = dist_setup(args)
     if world > 1:
@@ -680,9 +745,39 @@ def run_kc_ragged(args):
     from paper_0812_2976_gb300 import build, synth
     build.build()
     kc._lib.load()
-    w = synth.ragged(n_sys=args.n_sys or synth.RAGGED_N_SYS,
-                     seed=None if rank == 0 else synth.SEED_BASE + 4 + 1000 * rank)
     stream = torch.cuda.current_stream(dev)
+    flush = L2Flush(dev)
+    r = ragged_measure(kc, synth, dev, stream, flush, args, world=world, rank=rank)
+    if rank != 0:
+        return
+    want_grad = not args.no_grad
+    line = {
+        "metric": ("planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)"
+                   if want_grad else "planet-obs evals/s (chi2, ragged n_pl 1-6, n_obs 16-1024)"),
+        "value": r["value"], "unit": "planet-obs evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+ds (mixed)", "data": "synthetic", "config": r["config"],
+        "e2e": r["e2e"], "gpu_launches": args.steps, "clocks": r["clocks"],
+        "roofline": r["roofline"]}
+    for k in ("forward_only", "padded_baseline", "cpu_baseline"):
+        if k in r:
+            line[k] = r[k]
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ragged_measure(kc, synth, dev, stream, flush, args, world=1, rank=0, compact=False):
+    """The ragged workload (config 4) through a RaggedPlan: chi2 + gradient
+    of every system per step (chi2 only with --no-grad), with the forward-
+    only plan, the padded uniform-size baseline, the ALU roofline of the
+    persistent kernel, end to end from pinned host memory and the oracle on
+    a sample of at least 16384 systems.  compact: the dictionary kept as an
+    extra of the default run."""
+    import torch
+    w = synth.ragged(n_sys=args.n_sys if args.config == 4 and args.n_sys else synth.RAGGED_N_SYS,
+                     seed=None if rank == 0 else synth.SEED_BASE + 4 + 1000 * rank)
     T = torch.tensor(w.t, device=dev)
     S = torch.tensor(w.sigma, device=dev)
     V = kc.kc_rv_predict_ragged(torch.tensor(w.truth, device=dev), torch.tensor(w.par_off),
@@ -690,18 +785,17 @@ def run_kc_ragged(args):
     V += torch.tensor(w.noise, device=dev)
     P = torch.tensor(w.params, device=dev)
     evals = w.evals()
-    flush = L2Flush(dev)
+    want_grad = not args.no_grad
 
-    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=not args.no_grad)
+    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed", want_grad=want_grad)
     plan.set_observations(T, V, S)
     shape = plan.autotune(P) if not args.no_tune else None
-    want_grad = not args.no_grad
     res = plan.run(P)
     chi, grad = res if want_grad else (res, None)
     for _ in range(max(args.warmup, 3)):
         plan.run(P, chi, grad)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local) if rank == 0 else None
+    sampler = ClockSampler(dev.index) if rank == 0 and not compact else None
     if world > 1:
         torch.distributed.barrier()
     if sampler:
@@ -713,11 +807,27 @@ def run_kc_ragged(args):
     if world > 1:
         from paper_0812_2976_gb300 import dist as kdist
         t_sum = kdist.max_over_ranks(t_sum, device=dev)
-    value = evals * args.steps * world / t_sum
+    out = {"value": evals * args.steps * world / t_sum, "unit": "planet-obs evals/s",
+           "ms_per_step": 1e3 * t_sum / args.steps, "clocks": clocks,
+           "what": "chi2 + gradient" if want_grad else "chi2",
+           "config": {"workload": "ragged", "n_sys": w.n_sys, "evals": evals,
+                      "n_obs_total": int(w.obs_off[-1]),
+                      "l2": "flushed between steps (write 256 MiB, then read 256 MiB)",
+                      "launch": {"block": shape[0], "ctas_per_sm": shape[1], "how": "autotuned"}
+                      if shape else "default"}}
+    # ALU roofline of the persistent kernel: every system at its own n_pl
+    n_obs_s = np.diff(np.asarray(w.obs_off)).astype(np.float64)
+    npl_s = np.asarray(w.n_pl).astype(np.float64)
+    per_planet = (grad_flops_per_eval(1) - 12.0) if want_grad else (mixed_flops_per_eval(1) - 10.0)
+    per_obs = 12.0 if want_grad else 10.0
+    flops_step = float(np.sum(n_obs_s * (npl_s * per_planet + per_obs)))
+    peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
+    achieved = flops_step / (t_sum / args.steps) / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": f"ragged_mixed_kernel<{'GRAD' if want_grad else 'FWD'}>",
+                       "flops_per_step": flops_step}
 
-    extras = {}
-    if not args.no_extras:
-        extras = ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev)
     # end to end: host parameters in, host chi2 + gradient out (the plan
     # writes both into views of one device buffer, returned with one copy)
     hP = torch.tensor(w.params).pin_memory()
@@ -736,38 +846,12 @@ def run_kc_ragged(args):
     for _ in range(2):
         e2e_step()
     e2e_s = time_steps(e2e_step, args.steps, stream, flush)
-    if rank != 0:
-        return
-    line = {
-        "metric": ("planet-obs evals/s (chi2 + gradient, ragged n_pl 1-6, n_obs 16-1024)"
-                   if want_grad else "planet-obs evals/s (chi2, ragged n_pl 1-6, n_obs 16-1024)"),
-        "value": value, "unit": "planet-obs evals/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_sum / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+ds (mixed)", "data": "synthetic",
-        "config": {"workload": "ragged", "n_sys": w.n_sys, "evals": evals,
-                   "n_obs_total": int(w.obs_off[-1]), "l2": "flushed between steps (write 256 MiB, then read 256 MiB)",
-                   "launch": {"block": shape[0], "ctas_per_sm": shape[1], "how": "autotuned"}
-                   if shape else "default"},
-        "e2e": {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
-                "h2d_bytes_per_step": hP.numel() * 8,
-                "d2h_bytes_per_step": hout.numel() * 4},
-        "gpu_launches": args.steps,
-        "clocks": clocks,
-    }
-    # ALU roofline of the persistent kernel: every system at its own n_pl
-    n_obs_s = np.diff(np.asarray(w.obs_off)).astype(np.float64)
-    npl_s = np.asarray(w.n_pl).astype(np.float64)
-    per_planet = (grad_flops_per_eval(1) - 12.0) if want_grad else (mixed_flops_per_eval(1) - 10.0)
-    per_obs = 12.0 if want_grad else 10.0
-    flops_step = float(np.sum(n_obs_s * (npl_s * per_planet + per_obs)))
-    peak = 2 * FP32_LANES_PER_SM * sm_count() * sm_mhz_for_peaks() * 1e6 / 1e12
-    achieved = flops_step / (t_sum / args.steps) / 1e12
-    line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "kernel": f"ragged_mixed_kernel<{'GRAD' if want_grad else 'FWD'}>",
-                        "flops_per_step": flops_step}
-    line.update(extras)
+    out["e2e"] = {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
+                  "h2d_bytes_per_step": hP.numel() * 8, "d2h_bytes_per_step": hout.numel() * 4}
+    del plan, dP, dout, hP, hout, chi, grad
+
+    if not args.no_extras or compact:
+        out.update(ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev))
     if not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()
@@ -779,12 +863,16 @@ def run_kc_ragged(args):
         oracle.chi2_ragged(sub.params, sub.par_off, sub.n_pl, sub.t, vsub, sub.sigma,
                            sub.obs_off, grad=want_grad)
         el = time.perf_counter() - t0c
-        line["cpu_baseline"] = {"value": sub.evals() / el, "unit": "planet-obs evals/s",
-                                "cores": oracle.max_threads(), "kind": "oracle",
-                                "sample": f"{idx.size} systems (every {idx[1] - idx[0]}th), "
-                                          f"chi2{' + gradient' if want_grad else ''}, "
-                                          f"{el:.1f} s wall"}
-    print(json.dumps(line), flush=True)
+        out["cpu_baseline"] = {"value": sub.evals() / el, "unit": "planet-obs evals/s",
+                               "cores": oracle.max_threads(), "kind": "oracle",
+                               "sample": f"{idx.size} systems (every {idx[1] - idx[0]}th), "
+                                         f"chi2{' + gradient' if want_grad else ''}, "
+                                         f"{el:.1f} s wall"}
+    del P, T, V, S
+    torch.cuda.empty_cache()
+    if compact:
+        out.pop("clocks", None)
+    return out
 
 
 def ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev):
