@@ -296,8 +296,10 @@ kc_status kc_plan_set_observations(kc_plan *plan, const double *t,
  * kernel into a CUDA graph (on a stream private to the plan); every run
  * launches that graph on `stream`, retargeted to the given pointers.  When
  * `stream` is itself being captured the two operations are recorded into
- * the caller's graph instead.  Runs of one plan must not overlap on the
- * device (they share the work queue). */
+ * the caller's graph instead.  Every stream a plan runs on gets its own work
+ * queue and graph (up to 64 streams per plan, kept until kc_plan_destroy;
+ * KC_ERR_UNSUPPORTED beyond), so runs on different streams may overlap on
+ * the device; runs on one stream are ordered by it. */
 kc_status kc_plan_run(kc_plan *plan, const double *params, void *chi2_out,
                       void *grad_out, kc_stream stream);
 
@@ -390,6 +392,19 @@ kc_status kc_last_device_error(int64_t *n_invalid);
  * allocates and frees its own scratch.  KC_ERR_ARG for another pipe or a
  * NULL result pointer. */
 kc_status kc_measure_pipe_rate(int32_t pipe, double *ops_per_sm_clock, kc_stream stream);
+
+/* First failed device index check of a KC_DEBUG build of the library
+ * (compiled with -DKC_DEBUG; the paper has no counterpart: it stands in for
+ * a memory checker).  Such a build checks, in its kernels, every index that
+ * reaches memory through caller data or launch arithmetic (parameter and
+ * observation indices, shared-memory slots, a ragged plan's queue entries,
+ * planet counts and offsets); a failed check skips its access or substitutes
+ * an index known to be in range, so nothing traps or faults.  *word
+ * receives the first failure since the previous call on the current device
+ * (bit 63 set, site in bits 48-55, the low 48 bits of the index; zero if
+ * none) and the word is reset.  Synchronises the device.  A normal build
+ * returns KC_ERR_UNSUPPORTED with *word = 0.  KC_ERR_ARG for NULL. */
+kc_status kc_debug_word(uint64_t *word);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int32_t kc_version(void);

@@ -10,7 +10,11 @@ import ctypes
 import os
 import threading
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkc.so")
+# KC_LIBRARY selects another build of the same library (the KC_DEBUG build,
+# libkc_debug.so, in its test); by default the in-tree libkc.so.  Either
+# way a missing file raises.
+LIB_PATH = (os.environ.get("KC_LIBRARY") or
+            os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkc.so"))
 
 KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_NOMEM, KC_ERR_UNSUPPORTED = range(5)
 KC_FP64, KC_MIXED, KC_FP32 = 0, 1, 2
@@ -71,6 +75,7 @@ SIGNATURES = {
     "kc_last_device_error": (_i32, [ctypes.POINTER(_i64)]),
     "kc_measure_pipe_rate": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), _st]),
     "kc_last_error": (ctypes.c_char_p, []),
+    "kc_debug_word": (_i32, [ctypes.POINTER(ctypes.c_uint64)]),
     "kc_version": (_i32, []),
 }
 

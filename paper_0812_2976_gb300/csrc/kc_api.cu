@@ -75,9 +75,10 @@ cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st) {
 }
 
 namespace {
-// Systems whose result came out NaN (invalid parameters or observations),
-// summed over every launch on the device since the last read.
-__device__ unsigned long long g_invalid_systems = 0ull;
+// [0]: systems whose result came out NaN (invalid parameters or
+// observations), summed over every launch on the device since the last
+// read; [1]: the first failed index check of a KC_DEBUG build (zero if none).
+__device__ unsigned long long g_invalid_systems[2] = {0ull, 0ull};
 std::mutex g_inv_mu;
 std::map<int, unsigned long long *> g_inv_addr;
 }  // namespace
@@ -286,6 +287,24 @@ kc_status kc_last_device_error(int64_t *n_invalid) {
   if (e != cudaSuccess) return cuda_status(e, "kc_last_device_error: counter");
   *n_invalid = (int64_t)n;
   return ok();
+}
+
+kc_status kc_debug_word(uint64_t *word) {
+  if (!word) return fail(KC_ERR_ARG, "kc_debug_word: NULL pointer");
+  *word = 0;
+#ifndef KC_DEBUG
+  return fail(KC_ERR_UNSUPPORTED, "kc_debug_word: library built without KC_DEBUG");
+#else
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e, "kc_debug_word: device");
+  unsigned long long w = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&w, kc::g_invalid_systems, sizeof(w), sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = cudaMemcpyToSymbol(kc::g_invalid_systems, &zero, sizeof(zero), sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_status(e, "kc_debug_word: word");
+  *word = w;
+  return ok();
+#endif
 }
 
 int32_t kc_version(void) { return 100; }

@@ -78,7 +78,8 @@ __host__ __device__ inline int warp_obs_tile(int n_obs, int G) {
 template <int J>
 __device__ __forceinline__ void setup_item(int i, int spr, int64_t sys0, int64_t n_sys,
                                            const double (&p)[5], double t_ref, double t0,
-                                           PlanetW *pl_s, float *gam_s) {
+                                           PlanetW *pl_s, float *gam_s, unsigned long long *dbg) {
+  if (!dbg_ok(dbg, i < spr * (J + 1), kDbgSmem, i)) return;
   if (i < spr * J) {
     const int64_t s = sys0 + i / J;
     PlanetW q = {};
@@ -106,17 +107,19 @@ __device__ __forceinline__ void load_item(int i, int spr, int64_t sys0, const Un
   if (i < spr * J) {
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
-    if (s < a.n_sys) {
+    const int64_t at = s * npar + 5 * j;
+    if (s < a.n_sys && dbg_ok(a.invalid, at + 4 < a.n_sys * npar, kDbgParam, at)) {
       if (DEMC && a.demc.z) {
         demc_form(a, s, 5 * j, npar, p);
       } else {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) p[k] = a.params[s * npar + 5 * j + k];
+        for (int k = 0; k < 5; ++k) p[k] = a.params[at + k];
       }
     }
   } else {
     const int64_t s = sys0 + (i - spr * J);
-    if (s < a.n_sys) {
+    if (s < a.n_sys && dbg_ok(a.invalid, s * npar + 5 * J < a.n_sys * npar, kDbgParam,
+                              s * npar + 5 * J)) {
       if (DEMC && a.demc.z) {
         double g[1];
         demc_form(a, s, 5 * J, npar, g);
@@ -156,7 +159,9 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
   const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
   double p[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (tid < nitems) load_item<J, DEMC>(tid, spr, sys0, a, p);
-  const bool has0 = tid < nk0, has1 = tid + block < nk0;
+  const bool has0 = tid < nk0 && dbg_ok(a.invalid, tid < a.n_obs, kDbgObs, tid);
+  const bool has1 = tid + block < nk0 && dbg_ok(a.invalid, tid + block < a.n_obs, kDbgObs,
+                                                tid + block);
   double t0v = 0.0, v0v = 0.0, s0v = 1.0, t1v = 0.0, v1v = 0.0, s1v = 1.0;
   if (has0) { t0v = a.t[tid]; v0v = a.v[tid]; s0v = a.sigma[tid]; }
   if (has1) { t1v = a.t[tid + block]; v1v = a.v[tid + block]; s1v = a.sigma[tid + block]; }
@@ -168,6 +173,7 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
   // tau = t - t_ref and v as float pairs, w = 1/(sigma^2 + jitter^2); the
   // padding up to whole chunks has zero weight (and tau = v = 0)
   auto convert = [&](int k, bool real, double t, double v, double sigma) {
+    if (!dbg_ok(a.invalid, k < tile, kDbgSmem, k)) return;
     float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float wk = 0.0f;
     if (real) {
@@ -181,22 +187,23 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
     w_s[k] = wk;
   };
 
-  if (tid < nitems) setup_item<J>(tid, spr, sys0, a.n_sys, p, t_ref, a.t0, pl_s, gam_s);
+  if (tid < nitems) setup_item<J>(tid, spr, sys0, a.n_sys, p, t_ref, a.t0, pl_s, gam_s, a.invalid);
   for (int i = tid + block; i < nitems; i += block) {       // more items than threads
     double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     load_item<J, DEMC>(i, spr, sys0, a, q);
-    setup_item<J>(i, spr, sys0, a.n_sys, q, t_ref, a.t0, pl_s, gam_s);
+    setup_item<J>(i, spr, sys0, a.n_sys, q, t_ref, a.t0, pl_s, gam_s, a.invalid);
   }
   if (tid < npad0) convert(tid, has0, t0v, v0v, s0v);
   if (tid + block < npad0) convert(tid + block, has1, t1v, v1v, s1v);
   for (int k = tid + 2 * block; k < npad0; k += block) {
-    const bool real = k < nk0;
+    const bool real = k < nk0 && dbg_ok(a.invalid, k < a.n_obs, kDbgObs, k);
     convert(k, real, real ? a.t[k] : 0.0, real ? a.v[k] : 0.0, real ? a.sigma[k] : 1.0);
   }
   __syncthreads();
 
   // ---- the CTA's systems, one per G lanes ----
-  const int slot = (warp << (5 - lg)) + (lane >> lg);
+  int slot = (warp << (5 - lg)) + (lane >> lg);
+  if (!dbg_ok(a.invalid, slot < spr, kDbgSmem, slot)) slot = 0;
   const int c = lane & (G - 1);
   const int64_t s = sys0 + slot;
   const PlanetW *q = pl_s + slot * J;
@@ -214,13 +221,14 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
     if (t > 0) {
       __syncthreads();
       for (int k = tid; k < npad; k += block) {
-        const bool real = k < nk;
+        const bool real = k < nk && dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k);
         convert(k, real, real ? a.t[k0 + k] : 0.0, real ? a.v[k0 + k] : 0.0,
                 real ? a.sigma[k0 + k] : 1.0);
       }
       __syncthreads();
     }
     for (int base = c; base < npad; base += step) {
+      if (!dbg_ok(a.invalid, base + ((kChunk - 1) << lg) < tile, kDbgSmem, base)) break;
       float th[kChunk], tl[kChunk];
       Kahan V[kChunk];
 #pragma unroll

@@ -197,9 +197,13 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
         double p[5];
         if (DEMC && a.demc.z) {
           demc_form(a, s, 5 * j, npar, p);        // DE-MC: this planet's proposal
-        } else {
+        } else if (dbg_ok(a.invalid, s * npar + 5 * j + 4 < a.n_sys * npar, kDbgParam,
+                          s * npar + 5 * j)) {
 #pragma unroll
           for (int k = 0; k < 5; ++k) p[k] = a.params[s * npar + 5 * j + k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) p[k] = 0.0;
         }
         q = planet_setup_mixed(p, t_ref, a.t0);
         if (SINGLE) {     // 1/P and M0/(2 pi) in float, the phase taken from t - t0
@@ -252,6 +256,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     if (k0 > 0) {
       __syncthreads();
       for (int k = tid; k < nk; k += block) {
+        if (!dbg_ok(a.invalid, k0 + k < a.n_obs && k < obs_tile, kDbgObs, k0 + k)) continue;
         if (PRE) {
           obs_s[k] = prep.obs[k0 + k];
           w_s[k] = prep.w[k0 + k];
@@ -489,7 +494,9 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
     PlanetD q = {};
-    if (s < a.n_sys) q = planet_setup_f64(a.params + s * npar + 5 * j, dref);
+    if (s < a.n_sys && dbg_ok(a.invalid, s * npar + 5 * j + 4 < a.n_sys * npar, kDbgParam,
+                              s * npar + 5 * j))
+      q = planet_setup_f64(a.params + s * npar + 5 * j, dref);
     pl_s[i] = q;
   }
   for (int i = tid; i < ST; i += block) {
@@ -506,6 +513,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     const int nk = min(obs_tile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs && k < obs_tile, kDbgObs, k0 + k)) continue;
       ObsD o;
       o.tau = a.t[k0 + k] - t_ref;
       o.v = a.v[k0 + k];

@@ -173,7 +173,8 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
     GradPlanetF q = {};
-    if (s < a.n_sys) q = grad_setup_mixed(a.params + s * NP + 5 * j, t_ref, a.t0);
+    if (s < a.n_sys && dbg_ok(a.invalid, s * NP + 5 * j + 4 < a.n_sys * NP, kDbgParam, s * NP))
+      q = grad_setup_mixed(a.params + s * NP + 5 * j, t_ref, a.t0);
     pl_s[i] = q;
   }
   for (int i = tid; i < ST; i += block) {
@@ -198,6 +199,7 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
     const int nk = min(obs_tile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k)) continue;
       float th, tl, vh, vl;
       sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
       split_d(a.v[k0 + k], vh, vl);
@@ -307,7 +309,8 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
     const int sl = i / J, j = i - sl * J;
     const int64_t s = sys0 + sl;
     GradPlanetD q = {};
-    if (s < a.n_sys) q = grad_setup_f64(a.params + s * NP + 5 * j, dref);
+    if (s < a.n_sys && dbg_ok(a.invalid, s * NP + 5 * j + 4 < a.n_sys * NP, kDbgParam, s * NP))
+      q = grad_setup_f64(a.params + s * NP + 5 * j, dref);
     pl_s[i] = q;
   }
   for (int i = tid; i < ST; i += block) {
@@ -327,6 +330,7 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
     const int nk = min(obs_tile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k)) continue;
       ObsGD o;
       const double tk = a.t[k0 + k];
       o.tau = tk - t_ref;
@@ -508,7 +512,9 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
   for (int i = tid; i < kGnWarps * J; i += block) {
     const int64_t si = sys0 + i / J;
     GradPlanetF q = {};
-    if (si < a.n_sys) q = grad_setup_mixed(a.params + si * NP + 5 * (i % J), t_ref, a.t0);
+    if (si < a.n_sys &&
+        dbg_ok(a.invalid, si * NP + 5 * (i % J) + 4 < a.n_sys * NP, kDbgParam, si * NP))
+      q = grad_setup_mixed(a.params + si * NP + 5 * (i % J), t_ref, a.t0);
     pl_s[i] = q;
   }
   for (int i = tid; i < kGnWarps; i += block)
@@ -542,6 +548,7 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
     const int nk = min(kGnObsTile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k)) continue;
       float th, tl, vh, vl;
       sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
       split_d(a.v[k0 + k], vh, vl);
@@ -700,7 +707,9 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
   for (int i = tid; i < kGnWarpsD * J; i += block) {
     const int64_t si = sys0 + i / J;
     GradPlanetD q = {};
-    if (si < a.n_sys) q = grad_setup_f64(a.params + si * NP + 5 * (i % J), dref);
+    if (si < a.n_sys &&
+        dbg_ok(a.invalid, si * NP + 5 * (i % J) + 4 < a.n_sys * NP, kDbgParam, si * NP))
+      q = grad_setup_f64(a.params + si * NP + 5 * (i % J), dref);
     pl_s[i] = q;
   }
   for (int i = tid; i < kGnWarpsD; i += block)
@@ -721,6 +730,7 @@ gn_f64_kernel(UniformArgs a, double *__restrict__ chi2_out, double *__restrict__
     const int nk = min(kGnObsTile, a.n_obs - k0);
     __syncthreads();
     for (int k = tid; k < nk; k += block) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k)) continue;
       ObsGD o;
       const double tk = a.t[k0 + k];
       o.tau = tk - t_ref;

@@ -63,14 +63,50 @@ struct UniformArgs {
 // tile table), which still gives valid launch shapes.
 int sm_count();
 
-// The library's per-device invalid-system counter (kc_api.cu); NULL if its
-// address cannot be obtained.
+// The library's per-device words (kc_api.cu): [0] the invalid-system
+// counter, [1] the first failed index check of a KC_DEBUG build.  Kernels
+// receive the address of [0]; NULL if it cannot be obtained.
 unsigned long long *invalid_counter();
 
 // Counts a NaN result (one atomic per invalid system).
 template <typename T>
 __device__ __forceinline__ void note_invalid(unsigned long long *ctr, T value) {
   if (ctr != nullptr && value != value) atomicAdd(ctr, 1ull);
+}
+
+// Index checks of a KC_DEBUG build (the library compiled with -DKC_DEBUG).
+// A failed check records its site and the offending index in the debug word
+// (the first failure wins; kc_debug_word reads it) and returns false; the
+// caller then carries on with a safe substitute (the access skipped, or an
+// index known to be in range), so a failed check neither traps, faults nor
+// leaves a barrier waiting.  In a normal build every check is true and
+// compiles to nothing.  words: the address kernels receive as their
+// invalid-system counter.
+enum DebugSite : unsigned {
+  kDbgParam = 1,       // parameter index of a uniform batch
+  kDbgObs = 2,         // observation index of a uniform batch
+  kDbgSmem = 3,        // shared-memory slot (setup item, staged observation, system)
+  kDbgOrder = 4,       // ragged: queue entry outside 0 .. n_sys - 1
+  kDbgPlanets = 5,     // ragged: planet count outside 1 .. KC_MAX_PLANETS
+  kDbgObsOff = 6,      // ragged: observation range outside the plan's observations
+  kDbgParOff = 7,      // ragged: parameter range outside the packed parameters
+};
+
+template <typename I>
+__device__ __forceinline__ bool dbg_ok(unsigned long long *words, bool ok, DebugSite site,
+                                       I index) {
+#ifdef KC_DEBUG
+  if (!ok && words != nullptr)
+    atomicCAS(words + 1, 0ull,
+              (1ull << 63) | ((unsigned long long)site << 48) |
+                  ((unsigned long long)(long long)index & 0xffffffffffffull));
+  return ok;
+#else
+  (void)words;
+  (void)site;
+  (void)index;
+  return true;
+#endif
 }
 
 // Stream-ordered scratch from the library's per-device memory pool

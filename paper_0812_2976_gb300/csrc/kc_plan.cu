@@ -17,6 +17,29 @@ using kc::cuda_status;
 using kc::fail;
 using kc::ok;
 
+// Streams a plan can run on, each with its own work queue and graph.
+constexpr int kPlanMaxStreams = 64;
+
+// What one stream needs to run the plan: its work-queue counter (so that
+// runs on different streams do not take each other's systems) and the graph
+// captured with that counter, pointed at the last run's arrays.
+struct PlanStream {
+  cudaStream_t stream = nullptr;
+  unsigned long long *queue = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t kernel_node = nullptr;
+  const double *g_params = nullptr;
+  void *g_chi2 = nullptr, *g_grad = nullptr;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    kernel_node = nullptr;
+  }
+};
+
 struct kc_plan {
   int device = 0;
   int mode = KC_MIXED;
@@ -27,28 +50,30 @@ struct kc_plan {
   int32_t *d_n_pl = nullptr;
   double *d_t_ref = nullptr;
   void *d_obs_a = nullptr, *d_obs_b = nullptr;
-  unsigned long long *d_queue = nullptr;
+  unsigned long long *d_queue = nullptr;  // kPlanMaxStreams counters
   bool obs_ready = false;
   int grid = 0, block = 256;
-  // graph state
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t kernel_node = nullptr;
-  cudaStream_t cap_stream = nullptr;      // private stream the graph is captured on
-  const double *g_params = nullptr;
-  void *g_chi2 = nullptr, *g_grad = nullptr;
+  std::vector<PlanStream> streams;       // the streams the plan has run on
+  cudaStream_t cap_stream = nullptr;      // private stream graphs are captured on
   std::mutex mu;
 
   kc::RaggedDev dev() const {
     return kc::RaggedDev{d_obs_off, d_par_off, d_n_pl, d_order, d_t_ref, n_sys, t0,
-                         kc::invalid_counter()};
+                         kc::invalid_counter(), n_obs, n_par};
   }
   void drop_graph() {
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
-    exec = nullptr;
-    graph = nullptr;
-    kernel_node = nullptr;
+    for (PlanStream &ps : streams) ps.drop_graph();
+  }
+  // The entry of stream st (created on first use, with the next free
+  // counter); NULL when kPlanMaxStreams streams already have one.
+  PlanStream *stream_for(cudaStream_t st) {
+    for (PlanStream &ps : streams)
+      if (ps.stream == st) return &ps;
+    if ((int)streams.size() >= kPlanMaxStreams) return nullptr;
+    streams.emplace_back();
+    streams.back().stream = st;
+    streams.back().queue = d_queue + streams.size() - 1;
+    return &streams.back();
   }
   void release() {
     drop_graph();
@@ -62,26 +87,31 @@ struct kc_plan {
 
 namespace {
 
-kc_status launch_direct(kc_plan *p, const double *params, void *chi2, void *grad,
+kc_status too_many_streams() {
+  return fail(KC_ERR_UNSUPPORTED, "kc_plan_run: the plan has run on %d streams already",
+              kPlanMaxStreams);
+}
+
+kc_status launch_direct(kc_plan *p, PlanStream *ps, const double *params, void *chi2, void *grad,
                         cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), st);
+  cudaError_t e = cudaMemsetAsync(ps->queue, 0, sizeof(unsigned long long), st);
   if (e == cudaSuccess)
     e = kc::ragged_launch(p->dev(), p->mode, p->grad, p->d_obs_a, p->d_obs_b, params, chi2, grad,
-                          p->d_queue, p->grid, p->block, st);
+                          ps->queue, p->grid, p->block, st);
   return cuda_status(e, "kc_plan_run");
 }
 
 // Records the queue reset and the kernel into a graph on the plan's private
 // stream (the caller's stream may be the legacy default stream, which cannot
 // be captured); the graph is then launched on whatever stream runs the plan.
-kc_status capture(kc_plan *p, const double *params, void *chi2, void *grad) {
-  p->drop_graph();
+kc_status capture(kc_plan *p, PlanStream *ps, const double *params, void *chi2, void *grad) {
+  ps->drop_graph();
   cudaStream_t st = p->cap_stream;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: begin capture");
-  cudaError_t e1 = cudaMemsetAsync(p->d_queue, 0, sizeof(unsigned long long), st);
+  cudaError_t e1 = cudaMemsetAsync(ps->queue, 0, sizeof(unsigned long long), st);
   cudaError_t e2 = kc::ragged_launch(p->dev(), p->mode, p->grad, p->d_obs_a, p->d_obs_b, params,
-                                     chi2, grad, p->d_queue, p->grid, p->block, st);
+                                     chi2, grad, ps->queue, p->grid, p->block, st);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(st, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
@@ -105,32 +135,32 @@ kc_status capture(kc_plan *p, const double *params, void *chi2, void *grad) {
     cudaGraphDestroy(g);
     return cuda_status(e != cudaSuccess ? e : cudaErrorUnknown, "kc_plan_run: instantiate");
   }
-  p->graph = g;
-  p->exec = ex;
-  p->kernel_node = kn;
-  p->g_params = params;
-  p->g_chi2 = chi2;
-  p->g_grad = grad;
+  ps->graph = g;
+  ps->exec = ex;
+  ps->kernel_node = kn;
+  ps->g_params = params;
+  ps->g_chi2 = chi2;
+  ps->g_grad = grad;
   return ok();
 }
 
 // Point the captured kernel at new parameter / output arrays.
-kc_status retarget(kc_plan *p, const double *params, void *chi2, void *grad) {
+kc_status retarget(kc_plan *p, PlanStream *ps, const double *params, void *chi2, void *grad) {
   cudaKernelNodeParams kp;
-  cudaError_t e = cudaGraphKernelNodeGetParams(p->kernel_node, &kp);
+  cudaError_t e = cudaGraphKernelNodeGetParams(ps->kernel_node, &kp);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: node params");
   kc::RaggedDev d = p->dev();
   const void *oa = p->d_obs_a, *ob = p->d_obs_b;
-  unsigned long long *q = p->d_queue;
+  unsigned long long *q = ps->queue;
   void *args_mixed[] = {&d, (void *)&oa, (void *)&ob, (void *)&params, &chi2, &grad, &q};
   void *args_f64[] = {&d, (void *)&oa, (void *)&params, &chi2, &grad, &q};
   kp.kernelParams = p->mode == KC_MIXED ? args_mixed : args_f64;
   kp.extra = nullptr;
-  e = cudaGraphExecKernelNodeSetParams(p->exec, p->kernel_node, &kp);
+  e = cudaGraphExecKernelNodeSetParams(ps->exec, ps->kernel_node, &kp);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: update node");
-  p->g_params = params;
-  p->g_chi2 = chi2;
-  p->g_grad = grad;
+  ps->g_params = params;
+  ps->g_chi2 = chi2;
+  ps->g_grad = grad;
   return ok();
 }
 
@@ -151,6 +181,7 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
   *plan = nullptr;
   if (n_sys < 1 || !obs_off || !n_pl)
     return fail(KC_ERR_ARG, "kc_plan_create_ragged: need n_sys >= 1, obs_off and n_pl");
+  if (n_sys > (int64_t(1) << 40)) return fail(KC_ERR_ARG, "kc_plan_create_ragged: n_sys too large");
   if (mode != KC_FP64 && mode != KC_MIXED)
     return fail(KC_ERR_ARG, "kc_plan_create_ragged: bad mode");
   if (!std::isfinite(t0) || !std::isfinite(jitter))
@@ -159,8 +190,12 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
   std::vector<int64_t> par_off(n_sys + 1, 0);
   std::vector<int64_t> work(n_sys);
   for (int64_t s = 0; s < n_sys; ++s) {
+    // ordered first, so that the difference cannot overflow
+    if (obs_off[s + 1] < obs_off[s])
+      return fail(KC_ERR_ARG, "kc_plan_create_ragged: obs_off decreases at system %lld",
+                  (long long)s);
     const int64_t n = obs_off[s + 1] - obs_off[s];
-    if (n < 0 || n > KC_MAX_OBS)
+    if (n > KC_MAX_OBS)
       return fail(KC_ERR_ARG, "kc_plan_create_ragged: system %lld has %lld observations",
                   (long long)s, (long long)n);
     if (n_pl[s] < 1 || n_pl[s] > KC_MAX_PLANETS)
@@ -180,6 +215,8 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
     return work[a] > work[b];
   });
 
+  if (obs_off[n_sys] > (int64_t(1) << 40))
+    return fail(KC_ERR_ARG, "kc_plan_create_ragged: more than 2^40 observations");
   kc_plan *p = new kc_plan();
   cudaGetDevice(&p->device);
   p->mode = mode;
@@ -202,7 +239,7 @@ kc_status kc_plan_create_ragged(kc_plan **plan, const int64_t *obs_off, const in
   alloc((void **)&p->d_t_ref, sizeof(double) * n_sys);
   alloc(&p->d_obs_a, obs_bytes_a);
   alloc(&p->d_obs_b, obs_bytes_b);
-  alloc((void **)&p->d_queue, sizeof(unsigned long long));
+  alloc((void **)&p->d_queue, sizeof(unsigned long long) * kPlanMaxStreams);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -266,18 +303,21 @@ kc_status kc_plan_run(kc_plan *plan, const double *params, void *chi2_out, void 
   if (!plan->obs_ready)
     return fail(KC_ERR_ARG, "kc_plan_run: kc_plan_set_observations has not been called");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  PlanStream *ps = plan->stream_for(st);
+  if (!ps) return too_many_streams();
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(st, &cap);
   if (e != cudaSuccess) return cuda_status(e, "kc_plan_run: stream");
-  if (cap != cudaStreamCaptureStatusNone) return launch_direct(plan, params, chi2_out, grad_out, st);
-  if (!plan->exec) {
-    kc_status s = capture(plan, params, chi2_out, grad_out);
+  if (cap != cudaStreamCaptureStatusNone)
+    return launch_direct(plan, ps, params, chi2_out, grad_out, st);
+  if (!ps->exec) {
+    kc_status s = capture(plan, ps, params, chi2_out, grad_out);
     if (s != KC_OK) return s;
-  } else if (plan->g_params != params || plan->g_chi2 != chi2_out || plan->g_grad != grad_out) {
-    kc_status s = retarget(plan, params, chi2_out, grad_out);
+  } else if (ps->g_params != params || ps->g_chi2 != chi2_out || ps->g_grad != grad_out) {
+    kc_status s = retarget(plan, ps, params, chi2_out, grad_out);
     if (s != KC_OK) return s;
   }
-  return cuda_status(cudaGraphLaunch(plan->exec, st), "kc_plan_run: graph launch");
+  return cuda_status(cudaGraphLaunch(ps->exec, st), "kc_plan_run: graph launch");
 }
 
 kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out, void *grad_out,
@@ -289,6 +329,8 @@ kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out, 
   if (!plan->obs_ready)
     return fail(KC_ERR_ARG, "kc_plan_autotune: kc_plan_set_observations has not been called");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  PlanStream *ps = plan->stream_for(st);
+  if (!ps) return too_many_streams();
   const int sms = sm_count(plan->device);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -303,11 +345,11 @@ kc_status kc_plan_autotune(kc_plan *plan, const double *params, void *chi2_out, 
     for (int k = 1; k <= kmax && status == KC_OK; ++k) {
       plan->block = b;
       plan->grid = sms * k;
-      status = launch_direct(plan, params, chi2_out, grad_out, st);   // warm-up
+      status = launch_direct(plan, ps, params, chi2_out, grad_out, st);   // warm-up
       float tmin = 1e30f;
       for (int rep = 0; rep < 2 && status == KC_OK; ++rep) {
         cudaEventRecord(e0, st);
-        status = launch_direct(plan, params, chi2_out, grad_out, st);
+        status = launch_direct(plan, ps, params, chi2_out, grad_out, st);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.0f;

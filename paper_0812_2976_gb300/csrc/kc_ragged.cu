@@ -33,6 +33,22 @@ namespace {
 
 __device__ inline double nan_r() { return __longlong_as_double(0x7ff8000000000000ll); }
 
+// KC_DEBUG checks of a ragged system's descriptors (always true in a normal
+// build): its observation range inside the plan's observations, its planet
+// count, its parameter range inside the packed parameters.
+__device__ __forceinline__ bool ragged_obs_ok(const RaggedDev &d, int64_t s, int64_t o0,
+                                              int64_t o1) {
+  return dbg_ok(d.invalid, 0 <= o0 && o0 <= o1 && o1 <= d.n_obs_total, kDbgObsOff, s);
+}
+
+__device__ __forceinline__ bool ragged_system_ok(const RaggedDev &d, int64_t s, int J,
+                                                 int64_t o0, int64_t o1) {
+  if (!dbg_ok(d.invalid, J >= 1 && J <= KC_MAX_PLANETS, kDbgPlanets, s)) return false;
+  if (!ragged_obs_ok(d, s, o0, o1)) return false;
+  const int64_t p0 = d.par_off[s];
+  return dbg_ok(d.invalid, 0 <= p0 && p0 + 5 * J + 1 <= d.n_par_total, kDbgParOff, s);
+}
+
 __device__ inline double system_gamma_r(const double *p, int J) {
   bool ok = finite_bits(p[5 * J]);
   for (int j = 0; j < J; ++j)
@@ -53,6 +69,7 @@ __global__ void prep_obs_mixed(RaggedDev d, const double *__restrict__ t,
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = warp; s < d.n_sys; s += nwarp) {
     const int64_t o0 = d.obs_off[s], o1 = d.obs_off[s + 1];
+    if (!ragged_obs_ok(d, s, o0, o1)) continue;
     const double tr = o1 > o0 ? t[o0] : d.t0;
     if (lane == 0) t_ref[s] = tr;
     // no FP64 instruction: differences from exact three-float splits
@@ -81,6 +98,7 @@ __global__ void prep_obs_f64(RaggedDev d, const double *__restrict__ t,
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = warp; s < d.n_sys; s += nwarp) {
     const int64_t o0 = d.obs_off[s], o1 = d.obs_off[s + 1];
+    if (!ragged_obs_ok(d, s, o0, o1)) continue;
     const double tr = o1 > o0 ? t[o0] : d.t0;
     if (lane == 0) t_ref[s] = tr;
     for (int64_t k = o0 + lane; k < o1; k += 32) {
@@ -96,7 +114,8 @@ __global__ void predict_ragged_kernel(const double *__restrict__ params,
                                       const int32_t *__restrict__ n_pl,
                                       const double *__restrict__ t,
                                       const int64_t *__restrict__ obs_off, int64_t n_sys,
-                                      double t0, double *__restrict__ v_out) {
+                                      double t0, double *__restrict__ v_out,
+                                      unsigned long long *words) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -104,6 +123,11 @@ __global__ void predict_ragged_kernel(const double *__restrict__ params,
     const int64_t o0 = obs_off[s], o1 = obs_off[s + 1];
     if (o1 <= o0) continue;
     const int J = n_pl[s];
+    // the caller's arrays (no totals known here): ordered offsets, a planet
+    // count in range
+    if (!dbg_ok(words, o0 >= 0 && par_off[s] >= 0, kDbgObsOff, s) ||
+        !dbg_ok(words, J >= 1 && J <= KC_MAX_PLANETS, kDbgPlanets, s))
+      continue;
     const double *p = params + par_off[s];
     const double tr = t[o0];
     const double gam = system_gamma_r(p, J);
@@ -370,8 +394,10 @@ ragged_mixed_kernel(RaggedDev d, const float4 *__restrict__ oa, const float2 *__
     idx = __shfl_sync(0xffffffffu, idx, 0);
     if (idx >= (unsigned long long)d.n_sys) break;
     const int64_t s = d.order[idx];
+    if (!dbg_ok(d.invalid, 0 <= s && s < d.n_sys, kDbgOrder, (int64_t)idx)) continue;
     const int J = d.n_pl[s];
     const int64_t o0 = d.obs_off[s];
+    if (!ragged_system_ok(d, s, J, o0, d.obs_off[s + 1])) continue;
     const int n = (int)(d.obs_off[s + 1] - o0);
     const double *p = params + d.par_off[s];
     if (lane < J) pl[lane] = rsetup_mixed(p + 5 * lane, d.t_ref[s], d.t0, GRAD);
@@ -400,8 +426,10 @@ ragged_f64_kernel(RaggedDev d, const ObsR64 *__restrict__ od, const double *__re
     idx = __shfl_sync(0xffffffffu, idx, 0);
     if (idx >= (unsigned long long)d.n_sys) break;
     const int64_t s = d.order[idx];
+    if (!dbg_ok(d.invalid, 0 <= s && s < d.n_sys, kDbgOrder, (int64_t)idx)) continue;
     const int J = d.n_pl[s];
     const int64_t o0 = d.obs_off[s];
+    if (!ragged_system_ok(d, s, J, o0, d.obs_off[s + 1])) continue;
     const int n = (int)(d.obs_off[s + 1] - o0);
     const double *p = params + d.par_off[s];
     const double dref = d.t_ref[s] - d.t0;
@@ -447,7 +475,7 @@ cudaError_t launch_predict_ragged(const double *params, const int64_t *par_off,
   int64_t blocks = (n_sys * 32 + 255) / 256;
   if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
   predict_ragged_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, 0, st>>>(
-      params, par_off, n_pl, t, obs_off, n_sys, t0, v_out);
+      params, par_off, n_pl, t, obs_off, n_sys, t0, v_out, invalid_counter());
   return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct RaggedDev {
   int64_t n_sys;
   double t0;
   unsigned long long *invalid;   // NaN-result counter (kc_last_device_error) or NULL
+  int64_t n_obs_total;           // observations of the plan (obs_off[n_sys])
+  int64_t n_par_total;           // packed parameters of the plan (par_off[n_sys])
 };
 
 // Converts t, v, sigma (device, [obs_off[n_sys]]) to the kernel's form:

@@ -81,6 +81,10 @@ def test_bad_arguments_rejected_on_host(lib):
                                     p, None) == 1
     assert lib.kc_chi2_gauss_newton(p, p, p, p, 4, 2, 8, 0.0, 0.0, 1, None, None, None, None) == 1
     assert lib.kc_measure_pipe_rate(0, None, None) == 1
+    # KC_DEBUG index word: a normal build has none
+    w = ctypes.c_uint64(7)
+    assert lib.kc_debug_word(ctypes.byref(w)) == 4 and w.value == 0
+    assert lib.kc_debug_word(None) == 1
     # the allocation-free call refuses sizes whose scratch size would wrap
     assert lib.kc_chi2_eval_mixed_noalloc(p, p, p, p, (1 << 62) + 1, 8, 16, 0.0, 0.0, p, None,
                                           None) == 1
@@ -98,6 +102,30 @@ def test_bad_arguments_rejected_on_host(lib):
         assert lib.kc_demcmc_step(p, p, 16, 1, p, p, p, 8, t0, jit, 1, 0, 8, 8, 8, g,
                                   p, p, p, p, p, None, None) == 1
         assert msg in lib.kc_last_error()
+
+
+def test_ragged_plan_offsets_checked_on_host(lib):
+    """Offsets that decrease, overflow or exceed the observation limits are
+    refused before any device memory is touched; so are bad planet counts."""
+    plan = ctypes.c_void_p()
+
+    def create(off, npl):
+        off = (ctypes.c_int64 * len(off))(*off)
+        npl = (ctypes.c_int32 * len(npl))(*npl)
+        return lib.kc_plan_create_ragged(ctypes.byref(plan), off, npl, len(npl), 0.0, 0.0, 1, 0)
+    i64max, i64min = 2 ** 63 - 1, -2 ** 63
+    for off, npl, msg in (([1, 5], [1], b"obs_off[0]"),
+                          ([0, 5, 3], [1, 1], b"decreases"),
+                          ([0, 16, i64min], [1, 1], b"decreases"),        # would wrap
+                          ([0, 16, i64max], [1, 1], b"observations"),
+                          ([0, (1 << 24) + 1], [1], b"observations"),
+                          ([0, 4], [0], b"n_pl"), ([0, 4], [9], b"n_pl")):
+        assert create(off, npl) == 1, (off, npl)
+        assert msg in lib.kc_last_error(), (msg, lib.kc_last_error())
+        assert not plan.value
+    assert lib.kc_plan_create_ragged(ctypes.byref(plan), ctypes.c_void_p(64), ctypes.c_void_p(64),
+                                     (1 << 40) + 1, 0.0, 0.0, 1, 0) == 1
+    assert b"too large" in lib.kc_last_error()
 
 
 def test_empty_batches_are_no_ops(lib):

@@ -243,3 +243,31 @@ def test_rv_predict_ragged_vs_oracle(kc, oracle_mod, small):
                                   torch.tensor(w.n_pl), dev(w.t), torch.tensor(w.obs_off),
                                   t0=2450000.0).cpu().numpy()
     assert np.max(np.abs(got - ref)) <= 1e-9
+
+
+def test_runs_on_two_streams_may_overlap(kc, oracle_mod):
+    """One plan run on two streams with nothing ordering the runs: each
+    stream has its own work queue, so both streams' results are the
+    oracle's (a queue shared by the two kernels would split the systems
+    between them)."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.ragged(20000, seed=91)
+    v = observed(oracle_mod, w)
+    ref1 = oracle_mod.chi2_ragged(w.params, w.par_off, w.n_pl, w.t, v, w.sigma, w.obs_off)
+    ref2 = oracle_mod.chi2_ragged(w.truth, w.par_off, w.n_pl, w.t, v, w.sigma, w.obs_off)
+    plan = kc.RaggedPlan(w.obs_off, w.n_pl, mode="mixed")
+    plan.set_observations(dev(w.t), dev(v), dev(w.sigma))
+    P1, P2 = dev(w.params), dev(w.truth)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for _ in range(3):
+        with torch.cuda.stream(s1):
+            a = plan.run(P1)
+        with torch.cuda.stream(s2):
+            b = plan.run(P2)
+        outs.append((a, b))
+    torch.cuda.synchronize()
+    for a, b in outs:
+        assert rel_err(a.cpu().numpy(), ref1).max() <= MIXED_TOL
+        assert rel_err(b.cpu().numpy(), ref2).max() <= MIXED_TOL
