@@ -63,3 +63,44 @@ def test_ragged_rows_of_different_lengths():
     got = ref.copy()
     got[-1] = np.inf
     assert grad_excess_ragged(got, ref, gabs, off, 1e-3, U32) > 1.0
+
+
+def test_derived_terms_only_where_the_terms_cancel():
+    """Non-cancelling components keep the survey's bound; cancelling ones add
+    (KAPPA_FORM + accumulation) u sum|c| and the residual term."""
+    from tolerance import KAPPA_FORM, Arith, grad_bound
+    ref = np.array([[1.0, 1e-4, 1e-4, 2.0]])
+    gabs = np.array([[5.0, 100.0, 100.0, 2.0]])       # columns 1, 2 cancel
+    comp = np.array([False, True, False, False])       # column 1 compensated
+    resid = np.array([[7.0, 3e-9, 5e-9, 11.0]])
+    ar = Arith(lanes=32, n_obs=512, compensated=comp, resid=resid)
+    core = grad_bound(ref, gabs, 1e-3, U32)
+    b = grad_bound(ref, gabs, 1e-3, U32, ar)
+    assert b[0, 0] == core[0, 0] and b[0, 3] == core[0, 3]
+    assert np.isclose(b[0, 1], core[0, 1] + (KAPPA_FORM + 2) * U32 * 100.0 + 3e-9)
+    assert np.isclose(b[0, 2], core[0, 2] + (KAPPA_FORM + 16 + 5) * U32 * 100.0 + 5e-9)
+    # a planted error just above a cancelling component's bound fails
+    got = ref.copy()
+    got[0, 2] += 1.01 * b[0, 2]
+    assert grad_excess(got, ref, gabs, 1e-3, U32, ar) > 1.0
+    got[0, 2] = ref[0, 2] + 0.99 * b[0, 2]
+    assert grad_excess(got, ref, gabs, 1e-3, U32, ar) <= 1.0
+
+
+def test_residual_error_grows_towards_pericentre(oracle_mod):
+    """eps_k of the residual bound: circular orbits give the constant part;
+    an eccentric orbit's largest value sits at pericentre (D = 1 - e)."""
+    from tolerance import residual_error
+    t = np.linspace(0.0, 10.0, 2001)
+    circ = np.array([[10.0, 5.0, 0.0, 0.3, 0.0, 0.0]])
+    ecc = np.array([[10.0, 5.0, 0.9, 0.3, 0.0, 0.0]])
+    v = np.zeros_like(t)
+    e0 = residual_error(oracle_mod, circ, t, v, 1, 0.0, U32)[0]
+    e9 = residual_error(oracle_mod, ecc, t, v, 1, 0.0, U32)[0]
+    assert np.allclose(e0, U32 * (5.0 * (np.pi + 3 + 18) + 3 * np.abs(
+        oracle_mod.predict(circ, t, 1)[0])), rtol=1e-12)
+    k = int(np.argmax(e9))
+    M = oracle_mod.mean_anomaly(t[k], 0.0, 10.0, 0.0)
+    assert abs(np.remainder(M + np.pi, 2 * np.pi) - np.pi) < 0.05     # at pericentre
+    # K ((pi + 3) / D^2 + 18 / D) at D = 1 - e = 0.1, plus 3 |V| (< 1 % here)
+    assert np.isclose(e9.max(), U32 * 5.0 * ((np.pi + 3) / 0.1 ** 2 + 18 / 0.1), rtol=0.01)
