@@ -245,7 +245,11 @@ def gradient_throughput(kc, synth, dev, stream, args):
                      ("nll_grad", lambda: kc.kc_nll_grad(PJ, T, V, S, t0=w.t0, mode="mixed",
                                                          stream=stream)),
                      ("chi2_grad_fp64", lambda: kc.kc_chi2_grad(P, T, V, S, t0=w.t0,
-                                                                mode="fp64", stream=stream))):
+                                                                mode="fp64", stream=stream)),
+                     ) + tuple(
+                         (f"gauss_newton_split{split}",
+                          lambda split=split: gn_with_split(kc, split, P, T, V, S, w, stream))
+                         for split in GN_SPLITS):
         fn()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 2 if name.endswith("fp64") else 5
@@ -267,7 +271,28 @@ def gradient_throughput(kc, synth, dev, stream, args):
         "flops_per_eval": {"grad": grad_flops_per_eval(w.n_pl), "gauss_newton": gn_flops_per_eval(w.n_pl)},
         "gauss_newton_tensor_tflops": out["gauss_newton"] / w.n_pl
                                       * gn_tensor_flops_per_obs(w.n_pl) / 1e12}
+    # the two ways of adding U^T U, side by side
+    out["gauss_newton_variants"] = {
+        name: out.pop(f"gauss_newton_split{split}")
+        for split, name in zip(GN_SPLITS, ("mma_sync", "tcgen05"))}
+    out["gauss_newton_default_split"] = kc.kc_get_tile("gn", "mixed", w.n_sys, w.n_pl,
+                                                       w.n_obs)[2]
     return out
+
+
+# Gauss-Newton tile splits: 0 = mma.sync, 4 = tcgen05
+GN_SPLITS = (0, 4)
+
+
+def gn_with_split(kc, split, P, T, V, S, w, stream):
+    """One Gauss-Newton launch with the given U^T U variant pinned for the
+    workload's size class, the previous table entry restored after."""
+    prev = kc.kc_get_tile("gn", "mixed", w.n_sys, w.n_pl, w.n_obs)
+    kc.kc_set_tile("gn", "mixed", w.n_sys, w.n_pl, w.n_obs, (32, 128, split))
+    try:
+        return kc.kc_chi2_gauss_newton(P, T, V, S, t0=w.t0, mode="mixed", stream=stream)
+    finally:
+        kc.kc_set_tile("gn", "mixed", w.n_sys, w.n_pl, w.n_obs, prev)
 
 
 def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):

@@ -135,8 +135,10 @@ kc_status kc_chi2_grad(const double *params, const double *t,
  * row by row (H[0][0..n-1], H[1][1..n-1], ...); float for KC_MIXED, double
  * for KC_FP64.  KC_MIXED forms the per-batch update H += U^T U (U: 32
  * observations x n, rows sqrt(w_k) J_k) on the tensor cores with TF32
- * inputs split in two (error about 1e-6 of sqrt(H_pp H_qq)).  Invalid
- * systems give NaN in all their outputs.  Errors as kc_chi2_grad. */
+ * inputs split in two (error about 1e-6 of sqrt(H_pp H_qq)), by warp-level
+ * mma.sync or by tcgen05 MMAs with the accumulator in tensor memory, as
+ * the tile table's KC_KERNEL_GN entry says.  Invalid systems give NaN in
+ * all their outputs.  Errors as kc_chi2_grad. */
 kc_status kc_chi2_gauss_newton(const double *params, const double *t,
                                const double *v_obs, const double *sigma,
                                int64_t n_sys, int32_t n_pl, int32_t n_obs,
@@ -341,7 +343,19 @@ typedef struct kc_tile {
     int32_t split;
 } kc_tile;
 
-typedef enum kc_kernel { KC_KERNEL_CHI2 = 0, KC_KERNEL_GRAD = 1 } kc_kernel;
+/* KC_KERNEL_GN (KC_MIXED only): the Gauss-Newton kernel of
+ * kc_chi2_gauss_newton, one warp per system and four per CTA
+ * (threads_per_system = 32, block = 128); split chooses how it adds U^T U:
+ * 0 = warp-level mma.sync (TF32), 32 observations per batch; 4 = tcgen05
+ * MMAs for the CTA's four systems stacked in one M = 64, N = 64 tile (one
+ * issuing thread, accumulator in 64 TMEM columns per CTA), 64 observations
+ * per batch, n_pl <= 3 only.  Without a tuned entry split 4 is used for
+ * n_pl <= 3 and split 0 above. */
+typedef enum kc_kernel {
+    KC_KERNEL_CHI2 = 0,
+    KC_KERNEL_GRAD = 1,
+    KC_KERNEL_GN = 2
+} kc_kernel;
 
 /* Tiles are looked up by (kernel, mode, n_pl, power-of-two bucket of n_sys,
  * power-of-two bucket of n_obs) in a process-wide table; a missing entry
@@ -353,7 +367,8 @@ kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys,
                       int32_t n_pl, int32_t n_obs, kc_tile *tile);
 
 /* Autotuner: times every admissible tile on the given problem (device
- * arrays as for kc_chi2_eval_ex / kc_chi2_grad; t0 = 0, no jitter), stores
+ * arrays as for kc_chi2_eval_ex / kc_chi2_grad / kc_chi2_gauss_newton;
+ * t0 = 0, no jitter), stores
  * the fastest in the table and returns it in *best (and its time in
  * *best_ms, may be NULL).  Blocking: synchronises `stream`; must not be
  * called while the stream is being captured.  Allocates and frees its own

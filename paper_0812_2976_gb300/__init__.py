@@ -346,7 +346,9 @@ def _kernel(kernel) -> int:
         return _lib.KC_KERNEL_CHI2
     if kernel in (_lib.KC_KERNEL_GRAD, "grad"):
         return _lib.KC_KERNEL_GRAD
-    raise ValueError(f"unknown kernel {kernel!r}: use 'chi2' or 'grad'")
+    if kernel in (_lib.KC_KERNEL_GN, "gn"):
+        return _lib.KC_KERNEL_GN
+    raise ValueError(f"unknown kernel {kernel!r}: use 'chi2', 'grad' or 'gn'")
 
 
 def kc_autotune(params, t, v_obs, sigma, kernel="chi2", mode="mixed", stream=None):

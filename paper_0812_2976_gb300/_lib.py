@@ -29,7 +29,7 @@ _i32 = ctypes.c_int32
 _f64 = ctypes.c_double
 _st = ctypes.c_void_p         # kc_stream (cudaStream_t)
 
-KC_KERNEL_CHI2, KC_KERNEL_GRAD = 0, 1
+KC_KERNEL_CHI2, KC_KERNEL_GRAD, KC_KERNEL_GN = 0, 1, 2
 
 
 class KcTile(ctypes.Structure):

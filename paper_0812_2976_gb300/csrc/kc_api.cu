@@ -220,6 +220,7 @@ Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
     }
   }
   if (kind == Kind::Chi2Mixed) return warp_tile(n_sys, n_pl, n_obs);
+  if (kind == Kind::GnMixed) return Tile{32, 128, 0, gn_default_variant(n_pl)};
   return default_tile(kind, n_sys, n_pl, n_obs);
 }
 
@@ -404,8 +405,13 @@ kc_status kc_chi2_gauss_newton(const double *params, const double *t, const doub
   if (n_sys == 0) return ok();
   UniformArgs a{params, t, v_obs, sigma, n_sys, n_pl, n_obs, t0, jitter * jitter,
                 kc::invalid_counter()};
+  int variant = 0;
+  if (mode == KC_MIXED) {
+    variant = kc::choose_tile(Kind::GnMixed, n_sys, n_pl, n_obs).split;
+    if (!kc::gn_variant_ok(variant, n_pl)) variant = 0;
+  }
   return cuda_status(kc::launch_gauss_newton(a, mode == KC_FP64, chi2_out, grad_out, jtj_out,
-                                             reinterpret_cast<cudaStream_t>(stream)),
+                                             reinterpret_cast<cudaStream_t>(stream), variant),
                      fn);
 }
 
@@ -550,11 +556,21 @@ namespace {
 
 kc::Kind kind_of(kc_kernel kernel, kc_mode mode) {
   if (kernel == KC_KERNEL_CHI2) return mode == KC_FP64 ? kc::Kind::Chi2F64 : kc::Kind::Chi2Mixed;
+  if (kernel == KC_KERNEL_GN) return kc::Kind::GnMixed;
   return mode == KC_FP64 ? kc::Kind::GradF64 : kc::Kind::GradMixed;
+}
+
+// Tiled kernels: chi2 and gradient in both modes, Gauss-Newton mixed only.
+bool kernel_ok(kc_kernel kernel, kc_mode mode) {
+  if (mode != KC_FP64 && mode != KC_MIXED) return false;
+  if (kernel == KC_KERNEL_GN) return mode == KC_MIXED;
+  return kernel == KC_KERNEL_CHI2 || kernel == KC_KERNEL_GRAD;
 }
 
 bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
   const int G = t.threads_per_system, B = t.block;
+  if (kernel == KC_KERNEL_GN)     // one warp per system, four per CTA; the variant in split
+    return mode == KC_MIXED && G == 32 && B == 128 && (t.split == 0 || t.split == 4);
   if (t.split == 3) return kernel == KC_KERNEL_CHI2 && mode == KC_MIXED && kc::warp_tile_ok(G, B);
   if (B < 32 || B > 256 || (B & 31)) return false;
   if (t.split < 0 || t.split > 2) return false;
@@ -573,9 +589,7 @@ bool tile_ok(kc_kernel kernel, kc_mode mode, const kc_tile &t) {
 
 kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_pl, int32_t n_obs,
                       const kc_tile *tile) {
-  if ((kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
-      (mode != KC_FP64 && mode != KC_MIXED) || n_sys < 0 || n_obs < 0 || n_pl < 1 ||
-      n_pl > KC_MAX_PLANETS)
+  if (!kernel_ok(kernel, mode) || n_sys < 0 || n_obs < 0 || n_pl < 1 || n_pl > KC_MAX_PLANETS)
     return fail(KC_ERR_ARG, "kc_set_tile: bad kernel, mode or sizes");
   const kc::TileKey key = kc::key_of(kind_of(kernel, mode), n_sys, n_pl, n_obs);
   std::lock_guard<std::mutex> lk(kc::g_tile_mu);
@@ -584,14 +598,15 @@ kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_p
     return ok();
   }
   if (!tile_ok(kernel, mode, *tile)) return fail(KC_ERR_ARG, "kc_set_tile: inadmissible tile");
+  if (kernel == KC_KERNEL_GN && !kc::gn_variant_ok(tile->split, n_pl))
+    return fail(KC_ERR_ARG, "kc_set_tile: the tcgen05 Gauss-Newton variant needs n_pl <= 3");
   kc::g_tiles[key] = Tile{tile->threads_per_system, tile->block, 0, tile->split};
   return ok();
 }
 
 kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys, int32_t n_pl, int32_t n_obs,
                       kc_tile *tile) {
-  if (!tile || (kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
-      (mode != KC_FP64 && mode != KC_MIXED) || n_sys < 0 || n_obs < 0 || n_pl < 1 ||
+  if (!tile || !kernel_ok(kernel, mode) || n_sys < 0 || n_obs < 0 || n_pl < 1 ||
       n_pl > KC_MAX_PLANETS)
     return fail(KC_ERR_ARG, "kc_get_tile: bad arguments");
   const Tile t = kc::choose_tile(kind_of(kernel, mode), n_sys, n_pl, n_obs);
@@ -608,19 +623,21 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   kc_status st = check_uniform(params, t, v_obs, sigma, n_sys, n_pl, n_obs, params,
                                "kc_autotune");
   if (st != KC_OK) return st;
-  if ((kernel != KC_KERNEL_CHI2 && kernel != KC_KERNEL_GRAD) ||
-      (mode != KC_FP64 && mode != KC_MIXED))
-    return fail(KC_ERR_ARG, "kc_autotune: bad kernel or mode");
+  if (!kernel_ok(kernel, mode)) return fail(KC_ERR_ARG, "kc_autotune: bad kernel or mode");
   if (n_sys == 0) return fail(KC_ERR_ARG, "kc_autotune: empty problem");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const kc::Kind kind = kind_of(kernel, mode);
   const size_t elem = mode == KC_FP64 ? sizeof(double) : sizeof(float);
   const size_t npar = 5 * (size_t)n_pl + 1;
-  void *chi = nullptr, *grad = nullptr;
+  void *chi = nullptr, *grad = nullptr, *jtj = nullptr;
   cudaError_t e = cudaMallocAsync(&chi, elem * n_sys, s);
-  if (e == cudaSuccess && kernel == KC_KERNEL_GRAD) e = cudaMallocAsync(&grad, elem * n_sys * npar, s);
+  if (e == cudaSuccess && kernel != KC_KERNEL_CHI2)
+    e = cudaMallocAsync(&grad, elem * n_sys * npar, s);
+  if (e == cudaSuccess && kernel == KC_KERNEL_GN)
+    e = cudaMallocAsync(&jtj, elem * n_sys * (npar * (npar + 1) / 2), s);
   if (e != cudaSuccess) {
     if (chi) cudaFreeAsync(chi, s);
+    if (grad) cudaFreeAsync(grad, s);
     return fail(KC_ERR_NOMEM, "kc_autotune: cannot allocate timing buffers: %s",
                 cudaGetErrorString(e));
   }
@@ -635,11 +652,14 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
       case kc::Kind::GradF64: return kc::launch_grad_f64(a, tile, (double *)chi, (double *)grad, s);
       case kc::Kind::GradMixed:
         return kc::launch_grad_mixed(a, tile, (float *)chi, (float *)grad, s);
+      case kc::Kind::GnMixed:
+        return kc::launch_gauss_newton(a, false, chi, grad, jtj, s, tile.split);
     }
     return cudaErrorInvalidValue;
   };
   float best_t = 1e30f;
-  Tile best_tile = kc::default_tile(kind, n_sys, n_pl, n_obs);
+  Tile best_tile = kernel == KC_KERNEL_GN ? Tile{32, 128, 0, 0}
+                                          : kc::default_tile(kind, n_sys, n_pl, n_obs);
   const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
   const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
@@ -650,7 +670,11 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   // two per SM on 141 of its SMs, where 256 CTAs of 256 threads leave 48
   // SMs with one)
   std::vector<kc_tile> cands;
-  for (int split = 0; split <= 2; ++split) {
+  // Gauss-Newton: the U^T U update by mma.sync or by tcgen05
+  if (kernel == KC_KERNEL_GN)
+    for (int split : {0, 4})
+      if (kc::gn_variant_ok(split, n_pl)) cands.push_back(kc_tile{32, 128, split});
+  for (int split = 0; split <= 2 && kernel != KC_KERNEL_GN; ++split) {
     for (int B : {32, 64, 128, 256})
       for (int G = 1; G <= (split == 2 ? 1024 : B); G <<= 1) cands.push_back(kc_tile{G, B, split});
     if (split < 2) {
@@ -663,16 +687,16 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   // the warp-per-system kernel: 8, 16 or 32 lanes per system, 4..32 warps
   // per CTA
   for (int G : {8, 16, 32})
-    for (int W = 4; W <= 32; ++W) cands.push_back(kc_tile{G, 32 * W, 3});
+    for (int W = 4; W <= 32 && kernel == KC_KERNEL_CHI2; ++W) cands.push_back(kc_tile{G, 32 * W, 3});
   for (const kc_tile &cand : cands) {
     const int G = cand.threads_per_system, B = cand.block, split = cand.split;
     if (!tile_ok(kernel, mode, cand)) continue;
-    if (n_obs > 0 && G > n_obs && split != 3) continue;
+    if (n_obs > 0 && G > n_obs && split != 3 && kernel != KC_KERNEL_GN) continue;
     if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
     if (split == 3 && G > kc::warp_lanes_for(n_obs)) continue;  // >= 4 obs per lane
     Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
     err = launch(tile);                       // warm-up (and smem attribute)
-    if (err == cudaErrorInvalidConfiguration && split == 3) {
+    if (err == cudaErrorInvalidConfiguration && split >= 3) {
       err = cudaSuccess;                      // does not fit on an SM: nothing launched
       continue;
     }
@@ -698,6 +722,7 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
   }
   cudaFreeAsync(chi, s);
   if (grad) cudaFreeAsync(grad, s);
+  if (jtj) cudaFreeAsync(jtj, s);
   cudaStreamSynchronize(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -24,6 +24,7 @@
 
 #include "kc_device.cuh"
 #include "kc_internal.h"
+#include "kc_tcgen05.cuh"
 
 namespace kc {
 
@@ -414,7 +415,8 @@ grad_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ chi2_ou
 // observation of a batch of 32 and writes u_k = sqrt(w_k) J_k as a row of a
 // 32 x n matrix U in shared memory; the warp then adds U^T U to its
 // accumulators.  Mixed path: that update is a rank-32 dense contraction per
-// batch on the tensor cores (mma.sync m16n8k8, TF32 inputs in the three-
+// batch on the tensor cores (mma.sync m16n8k8 here; the tcgen05 form
+// follows), TF32 inputs in the three-
 // product split hi*hi + hi*lo + lo*hi, FP32 accumulation), only the tiles
 // on or above the diagonal.  Each element of U is split into its (hi, lo)
 // pair once, when its row is written; since B = U and A = U^T cover the
@@ -474,6 +476,49 @@ __device__ __forceinline__ float2 tf32_pair(float x) {
   const float hi = __uint_as_float(__float_as_uint(x) & kTf32Mask);
   const float lo = __uint_as_float(__float_as_uint(__fsub_rn(x, hi)) & kTf32Mask);
   return make_float2(hi, lo);
+}
+
+// One observation of the Gauss-Newton pass for the lane: its chi2 and
+// gradient terms are added to acc, gP, g, and its row u = sqrt(w) J written
+// to urow.  A lane past the batch's end evaluates a valid observation with
+// weight 0, so all lanes run the same instructions.
+template <int J>
+__device__ __forceinline__ void gn_obs(const float4 &o, const float4 &wt, bool live, float gam,
+                                       const GradPlanetF (&qr)[J], Kahan &acc, Kahan (&gP)[J],
+                                       float (&g)[5 * J + 1], float (&urow)[5 * J + 1]) {
+  float sEj[J], cEj[J];
+  Kahan V = {0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const PlanetF &p = qr[j].base;
+    const float M = mean_anomaly_mixed(o.x, o.y, p);
+    kepler_f32(M, p.e, sEj[j], cEj[j]);
+    kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
+  }
+  const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
+  const float wk = live ? wt.x : 0.0f, wr = wk * r, a2 = 2.0f * wr;
+  kahan_add(acc, wr * r);
+  const float sw = live ? wt.z : 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const GradPlanetF &qj = qr[j];
+    Partials<float> d;
+    const float invD = rcp_fast(__fmaf_rn(-qj.base.e, cEj[j], 1.0f));
+    velocity_partials(qj.base.e, qj.K, qj.cw, qj.sw, qj.beta, qj.ibeta, sEj[j], cEj[j], invD, d);
+    d.dP = d.dM * (-kTwoPiF * wt.y * qj.n2);
+    kahan_add(gP[j], a2 * d.dP);
+    g[5 * j + 1] = fmaf(a2, d.dK, g[5 * j + 1]);
+    g[5 * j + 2] = fmaf(a2, d.de, g[5 * j + 2]);
+    g[5 * j + 3] = fmaf(a2, d.dw, g[5 * j + 3]);
+    g[5 * j + 4] = fmaf(a2, d.dM, g[5 * j + 4]);
+    urow[5 * j + 0] = sw * d.dP;
+    urow[5 * j + 1] = sw * d.dK;
+    urow[5 * j + 2] = sw * d.de;
+    urow[5 * j + 3] = sw * d.dw;
+    urow[5 * j + 4] = sw * d.dM;
+  }
+  g[5 * J] += a2;
+  urow[5 * J] = sw;
 }
 
 // D = A B + D for one 16 x 8 tile, A 16 x 8 (row), B 8 x 8 (col), TF32.
@@ -681,6 +726,245 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         if (row < NP && col < NP && col >= row) H[tri_index(NP, row, col)] = C[mt][nt][i] + poison;
       }
     }
+}
+
+// ---------------------------------------------- Gauss-Newton on tcgen05
+//
+// The same pass with the U^T U update on the fifth-generation tensor cores:
+// the operands come from shared memory through matrix descriptors, the
+// accumulator stays in tensor memory (TMEM) for the whole launch, and one
+// thread issues each batch's MMAs, so the warps evaluating observations
+// spend no issue slots or shared-memory loads on the contraction.  The
+// smallest tcgen05 tile is M = 64 rows, four times one system's 16 (n_pl
+// <= 3: 5 n_pl + 1 <= 16 parameters; rows beyond them never reach a kept
+// entry), so the CTA's four warps write their systems' U^T rows into one
+// 64-row tile (rows 16 w .. 16 w + 15 for warp w; TF32 (hi, lo) pairs as in
+// gn_mixed_kernel, in two tiles, K-major, 128-byte swizzle), and thread 0
+// issues D += U^T_tile U_tile (M = 64, N = 64, three MMAs per K = 8 step:
+// lo hi, hi lo, hi hi); the four diagonal 16 x 16 blocks are kept and 3/4
+// of the products are cross-system terms that are thrown away.  A batch is
+// 64 observations, two per lane, evaluated side by side (two independent
+// chains per planet for the scheduler); its tile is two 64 x 32 halves.
+// One tile suffices: a warp rewrites it only after evaluating the next 64
+// observations, by which time the MMAs that read it have long completed
+// (its lane 0 still waits on the mbarrier their commit arrives on).  A CTA
+// barrier per batch hands the written tile to the issuing thread (on a
+// GB300 this ran 822 us on 65536 x 3 x 512 against 891 us with a "full"
+// mbarrier that let the other warps run a batch ahead of warp 0).  With
+// M = 64 the accumulator's row r sits in TMEM lane 32 (r / 16) + r % 16, so
+// warp w reads its system's block from its own lanes 32 w .. 32 w + 15,
+// columns 16 w .. 16 w + 15.  Every wait is bounded; a wait that gives up
+// makes the CTA's results NaN (counted by the invalid-system counter) and
+// the TMEM is still freed.
+
+constexpr int kTcHalfBytes = 64 * 32 * 4;       // 64 rows x 32 observations, TF32
+constexpr int kTcBatch = 64;                    // observations per batch
+constexpr int kTcObsTile = 512;                 // observations staged at a time
+constexpr int kTcCols = 64;                     // TMEM columns per CTA
+constexpr uint64_t kTcWaitLimit = 20000000;     // ns an mbarrier wait may take (20 ms)
+
+struct GnTcLayout {
+  size_t u, pl, gam, obs, w, bar, slot, total;
+  __host__ __device__ GnTcLayout(int J) {
+    u = 0;                                       // hi halves, then lo halves: 1024-aligned
+    pl = u + 4 * kTcHalfBytes;
+    gam = pl + sizeof(GradPlanetF) * kGnWarps * J;
+    obs = align_up(gam + sizeof(float) * kGnWarps, 16);
+    w = obs + sizeof(float4) * kTcObsTile;
+    bar = align_up(w + sizeof(float4) * kTcObsTile, 8);
+    slot = bar + sizeof(uint64_t);
+    total = align_up(slot + 16, 16) + 1024;     // 1024 bytes to align the base
+  }
+};
+
+// Lane 0 waits; the warp learns the outcome (and is ordered after it).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t limit, int lane) {
+  bool ok = true;
+  if (lane == 0) ok = tc::mbar_wait(bar, parity, limit);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// Writes one row of U^T (the lane's observation in K-half `half`) as TF32
+// (hi, lo) pairs: element (row 16 warp + p, column c) of a half sits in
+// 8-row group 2 warp + p / 8 (1024 bytes each), row p % 8 (128 bytes),
+// 16-byte chunk (c / 4) ^ (p % 8), word c % 4.
+template <int NP>
+__device__ __forceinline__ void gn_tc_store(unsigned char *rows, uint32_t lane_q,
+                                            const float (&urow)[NP]) {
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const float2 pr = tf32_pair(urow[p]);
+    const uint32_t off = (p >> 3) * 1024 + (p & 7) * 128 + ((lane_q ^ (p & 7)) << 4);
+    *reinterpret_cast<float *>(rows + off) = pr.x;
+    *reinterpret_cast<float *>(rows + 2 * kTcHalfBytes + off) = pr.y;
+  }
+}
+
+template <int J>
+__global__ void __launch_bounds__(kGnWarps * 32, 4)
+gn_mixed_tc_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__ grad_out,
+                   float *__restrict__ jtj_out) {
+  constexpr int NP = gn_np(J);
+  constexpr int NTRI = NP * (NP + 1) / 2;
+  static_assert(NP <= 16, "one system's U^T fits 16 rows of the M = 64 tile");
+  static_assert(kGnWarps == 4, "four systems per M = 64 tile");
+  constexpr uint32_t IDESC = tc::idesc_tf32(64, 64);
+  constexpr int kThreads = kGnWarps * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  const GnTcLayout L(J);
+  GradPlanetF *pl_s = reinterpret_cast<GradPlanetF *>(smem + L.pl);
+  float *gam_s = reinterpret_cast<float *>(smem + L.gam);
+  float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
+  float4 *wt_s = reinterpret_cast<float4 *>(smem + L.w);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);   // commits of the MMAs
+  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + L.slot);
+  unsigned char *tiles = smem + L.u;
+  const uint32_t tiles_a = tc::smem_u32(tiles), bar_a = tc::smem_u32(bar);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t sys0 = (int64_t)blockIdx.x * kGnWarps;
+  const int64_t s = sys0 + warp;
+
+  if (warp == 0) tc::tmem_alloc(tc::smem_u32(slot), kTcCols);
+  if (tid == 0) {
+    tc::mbar_init(bar_a, 1);                   // one commit per batch
+    tc::mbar_init_fence();
+  }
+  const double t_ref = a.n_obs > 0 ? a.t[0] : a.t0;
+  const Split3 tr3 = split3(t_ref), te3 = split3(a.t0);
+  const float dref_f = (tr3.x0 - te3.x0) + (tr3.x1 - te3.x1);     // t_ref - t0
+  const float jit2 = d2f(a.jitter2);
+  for (int i = tid; i < kGnWarps * J; i += kThreads) {
+    const int64_t si = sys0 + i / J;
+    GradPlanetF q = {};
+    if (si < a.n_sys &&
+        dbg_ok(a.invalid, si * NP + 5 * (i % J) + 4 < a.n_sys * NP, kDbgParam, si * NP))
+      q = grad_setup_mixed(a.params + si * NP + 5 * (i % J), t_ref, a.t0);
+    pl_s[i] = q;
+  }
+  for (int i = tid; i < kGnWarps; i += kThreads)
+    gam_s[i] = sys0 + i < a.n_sys ? d2f(system_gamma_g(a.params + (sys0 + i) * NP, J)) : 0.0f;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *slot;
+
+  GradPlanetF qr[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) qr[j] = pl_s[warp * J + j];
+  const float gam = gam_s[warp];
+  const uint32_t lane_q = (uint32_t)lane >> 2;
+  unsigned char *my_rows = tiles + 2048 * warp + 4 * (lane & 3);
+  Kahan acc = {0.0f, 0.0f};
+  Kahan gP[J];
+  float g[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < J; ++j) gP[j] = Kahan{0.0f, 0.0f};
+  uint32_t nb = 0;                                   // batches (commits) so far
+  bool ok = true;
+
+  for (int k0 = 0; k0 < a.n_obs; k0 += kTcObsTile) {
+    const int nk = min(kTcObsTile, a.n_obs - k0);
+    __syncthreads();
+    for (int k = tid; k < nk; k += kThreads) {
+      if (!dbg_ok(a.invalid, k0 + k < a.n_obs, kDbgObs, k0 + k)) continue;
+      float th, tl, vh, vl;
+      sub_ds(split3(a.t[k0 + k]), tr3, th, tl);
+      split_d(a.v[k0 + k], vh, vl);
+      obs_s[k] = make_float4(th, tl, vh, vl);
+      const float sg = d2f(a.sigma[k0 + k]);
+      const float var = __fmaf_rn(sg, sg, jit2);
+      const float wk = var > 0.0f ? 1.0f / var : __int_as_float(0x7fc00000);
+      wt_s[k] = make_float4(wk, th + dref_f, sqrtf(wk), 0.0f);
+    }
+    __syncthreads();
+    for (int kb = 0; kb < nk; kb += kTcBatch) {
+      const int ka = kb + lane, kbb = kb + 32 + lane;
+      const int ia = min(ka, nk - 1), ib = min(kbb, nk - 1);
+      float ua[NP], ub[NP];
+      gn_obs<J>(obs_s[ia], wt_s[ia], ka < nk, gam, qr, acc, gP, g, ua);
+      gn_obs<J>(obs_s[ib], wt_s[ib], kbb < nk, gam, qr, acc, gP, g, ub);
+      if (nb > 0 && ok)                  // the MMAs that read the tile before
+        ok = warp_wait(bar_a, (nb - 1) & 1u, kTcWaitLimit, lane);
+      gn_tc_store<NP>(my_rows, lane_q, ua);
+      gn_tc_store<NP>(my_rows + kTcHalfBytes, lane_q, ub);
+      tc::fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+          // K step ks: observations 8 ks .. 8 ks + 7 of the batch, in half ks / 4
+          const uint32_t hi = tiles_a + (ks >> 2) * kTcHalfBytes + 32u * (ks & 3);
+          const uint32_t lo = hi + 2 * kTcHalfBytes;
+          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(lo), tc::desc_kmajor_sw128(hi), IDESC,
+                       (nb | ks) != 0);
+          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(hi), tc::desc_kmajor_sw128(lo), IDESC, 1u);
+          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(hi), tc::desc_kmajor_sw128(hi), IDESC, 1u);
+        }
+        tc::commit(bar_a);
+      }
+      ++nb;
+    }
+  }
+
+  // Every MMA is complete once the last commit's phase is; a longer wait if
+  // a wait gave up before.
+  float h[16];
+  if (nb > 0) {
+    const bool last_ok = warp_wait(bar_a, (nb - 1) & 1u, ok ? kTcWaitLimit : 4 * kTcWaitLimit,
+                                   lane);
+    ok = ok && last_ok;
+    tc::fence_after_sync();
+    tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + 16u * warp, h);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) h[i] = 0.0f;
+  }
+
+  for (int m = 16; m >= 1; m >>= 1) {
+    Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
+    kahan_merge(acc, o);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      Kahan op = {shfl_xor(gP[j].big, m), shfl_xor(gP[j].small, m)};
+      kahan_merge(gP[j], op);
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) g[i] += shfl_xor(g[i], m);
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) g[5 * j] = kahan_value(gP[j]);
+  if (s < a.n_sys) {
+    // NaN for an invalid system, or where a wait on the tensor cores gave up
+    const float poison = ok ? 0.0f * gam : __int_as_float(0x7fc00000);
+    if (lane == 0) {
+      const float value = kahan_value(acc) + poison;
+      if (chi2_out) chi2_out[s] = value;
+      note_invalid(a.invalid, value);
+    }
+    if (grad_out) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        if (lane == (i & 31)) grad_out[s * NP + i] = g[i] + poison;
+    }
+    float *H = jtj_out + s * NTRI;
+    if (lane < NP) {
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c >= lane) H[tri_index(NP, lane, c)] = h[c] + poison;
+    }
+  }
+
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(taddr, kTcCols);
+  }
 }
 
 template <int J>
@@ -909,9 +1193,48 @@ cudaError_t launch_grad_f64(const UniformArgs &a, const Tile &tile, double *chi2
   return cudaGetLastError();
 }
 
+// The tcgen05 variant (split 4): n_pl <= 3.  Every resident CTA holds
+// kTcCols TMEM columns, so the launch is refused unless the SM's 512
+// columns cover all CTAs that can be resident at once (an allocation would
+// otherwise wait for another CTA to finish).
+template <int J>
+cudaError_t launch_gn_tc(const UniformArgs &a, void *chi2, void *grad, void *jtj,
+                         cudaStream_t st) {
+  const size_t smem = GnTcLayout(J).total;
+  cudaError_t err = set_smem(gn_mixed_tc_kernel<J>, smem);
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gn_mixed_tc_kernel<J>,
+                                                      kGnWarps * 32, smem);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1 || per_sm * kTcCols > 512) return cudaErrorInvalidConfiguration;
+  const int grid = (int)((a.n_sys + kGnWarps - 1) / kGnWarps);
+  gn_mixed_tc_kernel<J><<<grid, kGnWarps * 32, smem, st>>>(a, (float *)chi2, (float *)grad,
+                                                           (float *)jtj);
+  return cudaGetLastError();
+}
+
+// Without a tuned entry the mixed Gauss-Newton kernel updates U^T U on
+// tcgen05 where it can (n_pl <= 3): on a GB300, 65536 systems x 3 planets x
+// 512 observations took 822 us against 869 us with mma.sync (whose
+// registers do not leave room for two observations per lane: 958 us).
+int gn_default_variant(int n_pl) { return n_pl <= 3 ? 4 : 0; }
+
+bool gn_variant_ok(int variant, int n_pl) {
+  return variant == 0 || (variant == 4 && n_pl >= 1 && n_pl <= 3);
+}
+
 cudaError_t launch_gauss_newton(const UniformArgs &a, bool f64, void *chi2, void *grad,
-                                void *jtj, cudaStream_t st) {
+                                void *jtj, cudaStream_t st, int variant) {
   cudaError_t err = cudaSuccess;
+  if (!f64 && variant != 0) {
+    if (!gn_variant_ok(variant, a.n_pl)) return cudaErrorInvalidValue;
+    switch (a.n_pl) {
+      case 1: return launch_gn_tc<1>(a, chi2, grad, jtj, st);
+      case 2: return launch_gn_tc<2>(a, chi2, grad, jtj, st);
+      default: return launch_gn_tc<3>(a, chi2, grad, jtj, st);
+    }
+  }
   if (f64) {
     const int grid = (int)((a.n_sys + kGnWarpsD - 1) / kGnWarpsD);
 #define KC_LAUNCH(JJ)                                                                        \

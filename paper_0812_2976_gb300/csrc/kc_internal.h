@@ -124,9 +124,14 @@ cudaError_t launch_chi2_f64(const UniformArgs &a, const Tile &tile, double *out,
                             float *resid, cudaStream_t st);
 // Gauss-Newton matrix with chi2 and its gradient (kc_grad.cu): chi2 / grad
 // may be NULL; jtj is [n_sys][n (n + 1)/2], n = 5 n_pl + 1; float (mixed) or
-// double (f64).
+// double (f64).  variant (mixed only; the tile's split): 0 = U^T U by
+// mma.sync, 4 = by tcgen05 MMAs for four systems stacked in an M = 64 tile
+// (n_pl <= 3, gn_variant_ok).
 cudaError_t launch_gauss_newton(const UniformArgs &a, bool f64, void *chi2, void *grad,
-                                void *jtj, cudaStream_t st);
+                                void *jtj, cudaStream_t st, int variant);
+bool gn_variant_ok(int variant, int n_pl);
+// Built-in choice of variant for the mixed Gauss-Newton kernel.
+int gn_default_variant(int n_pl);
 
 // FMA-pipe throughput probe (kc_probe.cu): one CTA of 1024 threads per SM
 // (grid n_sm), eight FMA chains per thread, iters steps; writes each CTA's
@@ -172,7 +177,7 @@ size_t smem_chi2_mixed(int n_pl, const Tile &tile);
 size_t smem_grad(int n_pl, const Tile &tile, bool f64);
 
 // Launch shape for a problem (kc_api.cu): the tuned table, else a heuristic.
-enum class Kind { Chi2F64 = 0, Chi2Mixed = 1, GradF64 = 2, GradMixed = 3 };
+enum class Kind { Chi2F64 = 0, Chi2Mixed = 1, GradF64 = 2, GradMixed = 3, GnMixed = 4 };
 Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 int obs_tile_for(Kind kind, int n_obs);

@@ -187,3 +187,22 @@ def test_tile_table_host_logic(lib):
     assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
     assert lib.kc_set_tile(1, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(8, 64, 1))) == 1
     assert lib.kc_get_tile(0, 1, 4096, 0, 256, ctypes.byref(t)) == 1
+    # Gauss-Newton (kernel 2, mixed only): split 0 = mma.sync, 4 = tcgen05
+    # (n_pl <= 3); one warp per system, 128 threads
+    assert lib.kc_get_tile(2, 1, 65536, 3, 512, ctypes.byref(t)) == 0
+    assert (t.threads_per_system, t.block, t.split) == (32, 128, 4)     # default: tcgen05
+    assert lib.kc_get_tile(2, 1, 65536, 4, 512, ctypes.byref(t)) == 0
+    assert (t.threads_per_system, t.block, t.split) == (32, 128, 0)
+    assert lib.kc_get_tile(2, 0, 65536, 3, 512, ctypes.byref(t)) == 1
+    for split in (4, 0):
+        assert lib.kc_set_tile(2, 1, 65536, 3, 512, ctypes.byref(_lib.KcTile(32, 128, split))) == 0
+        assert lib.kc_get_tile(2, 1, 65536, 3, 512, ctypes.byref(t)) == 0
+        assert (t.threads_per_system, t.block, t.split) == (32, 128, split)
+    assert lib.kc_set_tile(2, 1, 65536, 4, 512, ctypes.byref(_lib.KcTile(32, 128, 4))) == 1
+    assert lib.kc_set_tile(2, 1, 65536, 4, 512, ctypes.byref(_lib.KcTile(32, 128, 0))) == 0
+    for bad in ((16, 128, 4), (32, 256, 4), (32, 128, 3), (32, 128, 1), (32, 128, 5)):
+        assert lib.kc_set_tile(2, 1, 65536, 3, 512, ctypes.byref(_lib.KcTile(*bad))) == 1
+    assert lib.kc_set_tile(2, 0, 65536, 3, 512, ctypes.byref(_lib.KcTile(32, 128, 0))) == 1
+    assert lib.kc_set_tile(3, 1, 65536, 3, 512, ctypes.byref(_lib.KcTile(32, 128, 0))) == 1
+    for n_pl in (3, 4):
+        assert lib.kc_set_tile(2, 1, 65536, n_pl, 512, None) == 0

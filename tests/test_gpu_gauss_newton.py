@@ -7,6 +7,8 @@ the mixed path forms J_k in FP32 (relative error ~1e-6, the period column
 ~1e-5 through (t - t0)/P^2) and the update on the tensor cores with the
 two-term TF32 split by truncation (< 3 * 2^-20 ~ 3e-6 per product), so 1e-4
 leaves an order of magnitude; FP64: 1e-10."""
+import contextlib
+
 import numpy as np
 import pytest
 import torch
@@ -43,6 +45,18 @@ def h_err(got, ref, n):
     return np.abs(G - R) / scale
 
 
+@contextlib.contextmanager
+def gn_variant(kc, split, n_sys, n_pl, n_obs):
+    """Runs the mixed Gauss-Newton kernel's U^T U update by mma.sync (split
+    0) or tcgen05 (4: four systems stacked in an M = 64 tile) for this size
+    class."""
+    kc.kc_set_tile("gn", "mixed", n_sys, n_pl, n_obs, (32, 128, split))
+    try:
+        yield
+    finally:
+        kc.kc_set_tile("gn", "mixed", n_sys, n_pl, n_obs, None)
+
+
 def rel(got, ref):
     return np.abs(np.asarray(got, np.float64) - ref) / np.maximum(np.abs(ref), 1.0)
 
@@ -54,9 +68,10 @@ def grad_err(got, ref, gabs, mode="mixed", arith=None):
     return grad_excess(got, ref, gabs, rel, u, arith)
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64"])
-def test_gradient_workload_sampled(kc, oracle_mod, mode):
-    """Config-3 shapes (n_pl 3, n_obs 512, t0 = 2450000) on 2048 systems."""
+@pytest.mark.parametrize("mode,split", [("mixed", 0), ("mixed", 4), ("fp64", 0)])
+def test_gradient_workload_sampled(kc, oracle_mod, mode, split):
+    """Config-3 shapes (n_pl 3, n_obs 512, t0 = 2450000) on 2048 systems;
+    mixed with each way of adding U^T U."""
     from paper_0812_2976_gb300 import synth
     w = synth.uniform(3, n_sys=2048)
     v = oracle_mod.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
@@ -64,7 +79,10 @@ def test_gradient_workload_sampled(kc, oracle_mod, mode):
                                             gabs=True)
     H_ref = oracle_mod.gauss_newton(w.params, w.t, w.sigma, w.n_pl, t0=w.t0)
     P, T, V, S = dev(w.params, w.t, v, w.sigma)
-    chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=w.t0, mode=mode)
+    ctx = gn_variant(kc, split, 2048, w.n_pl, w.t.size) if mode == "mixed" else \
+        contextlib.nullcontext()
+    with ctx:
+        chi, g, H = kc.kc_chi2_gauss_newton(P, T, V, S, t0=w.t0, mode=mode)
     tol = (CHI2_MIXED_TOL, GRAD_MIXED_TOL, H_MIXED_TOL) if mode == "mixed" else \
         (CHI2_F64_TOL, GRAD_F64_TOL, H_F64_TOL)
     assert rel(chi.cpu().numpy(), chi_ref).max() <= tol[0]
@@ -104,6 +122,59 @@ def test_planet_counts_ragged_tails_invalid(kc, oracle_mod, n_pl, n_obs):
         assert grad_err(g[ok], g_ref[ok], g_abs[ok], mode, ar) <= 1.0
         assert h_err(H[ok], H_ref[ok], 5 * n_pl + 1).max() <= tol[2]
         assert kc.kc_last_device_error() == 1
+
+
+@pytest.mark.parametrize("split", [4])
+@pytest.mark.parametrize("n_pl,n_obs,n_sys", [(1, 33, 37), (2, 300, 9), (3, 1000, 6),
+                                              (3, 1, 5), (3, 0, 3), (3, 97, 4097),
+                                              (3, 64, 8), (2, 513, 4)])
+def test_tcgen05_variants(kc, oracle_mod, split, n_pl, n_obs, n_sys):
+    """The tcgen05 form of the U^T U update against the oracle and against
+    the mma.sync form, element by element: partial last CTAs (n_sys not a
+    multiple of four), a partial last batch of 64 observations (one lane's
+    second observation only, or neither), exactly one batch, several
+    observation tiles of 512 and many batches through the one operand tile,
+    one observation, none (H = 0), and an invalid system beside valid ones
+    in one M = 64 tile (its NaN rows must not reach the others' blocks)."""
+    rng = np.random.default_rng(100 * n_pl + n_obs)
+    cols = []
+    for _ in range(n_pl):
+        cols += [np.exp(rng.uniform(0, np.log(3000), n_sys)), rng.uniform(1, 80, n_sys),
+                 rng.uniform(0, 0.85, n_sys), rng.uniform(0, 2 * np.pi, n_sys),
+                 rng.uniform(0, 2 * np.pi, n_sys)]
+    par = np.stack(cols + [rng.uniform(-10, 10, n_sys)], axis=1)
+    bad = [1] if n_sys > 1 else []
+    par[bad, 2] = 1.5                                    # e > 1: invalid
+    t = np.sort(rng.uniform(2450000, 2453000, n_obs))
+    v = rng.normal(0, 30, n_obs)
+    sig = rng.uniform(1, 5, n_obs)
+    t0 = 2450500.0
+    n = 5 * n_pl + 1
+    chi_ref, g_ref, g_abs = oracle_mod.chi2(par, t, v, sig, n_pl, t0=t0, gabs=True)
+    H_ref = oracle_mod.gauss_newton(par, t, sig, n_pl, t0=t0)
+    P, T, V, S = dev(par, t, v, sig)
+    ok = np.setdiff1d(np.arange(n_sys), bad)
+    with gn_variant(kc, 0, n_sys, n_pl, n_obs):
+        chi0, g0, H0 = [x.cpu().numpy() for x in kc.kc_chi2_gauss_newton(P, T, V, S, t0=t0,
+                                                                          mode="mixed")]
+    kc.kc_last_device_error()
+    with gn_variant(kc, split, n_sys, n_pl, n_obs):
+        chi, g, H = [x.cpu().numpy() for x in kc.kc_chi2_gauss_newton(P, T, V, S, t0=t0,
+                                                                       mode="mixed")]
+    assert kc.kc_last_device_error() == len(bad)
+    assert np.all(np.isnan(chi[bad])) and np.all(np.isnan(g[bad])) and np.all(np.isnan(H[bad]))
+    assert np.all(np.isfinite(H[ok]))
+    if n_obs == 0:
+        assert np.all(H[ok] == 0) and np.all(chi[ok] == 0) and np.all(g[ok] == 0)
+        return
+    assert rel(chi[ok], chi_ref[ok]).max() <= CHI2_MIXED_TOL
+    ar = uniform_arith(kc, oracle_mod, par[ok], t, v, sig, n_pl, t0, 0.0, "mixed", "gn")
+    assert grad_err(g[ok], g_ref[ok], g_abs[ok], "mixed", ar) <= 1.0
+    assert h_err(H[ok], H_ref[ok], n).max() <= H_MIXED_TOL
+    # the same split products as the mma.sync form: both within a few 2^-20
+    # of the exact matrix on the correlation scale
+    assert h_err(H[ok], H0[ok].astype(np.float64), n).max() <= 2e-5
+    np.testing.assert_array_equal(chi[ok], chi0[ok])
 
 
 def test_high_eccentricity(kc, oracle_mod):
