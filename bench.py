@@ -43,21 +43,23 @@ FALLBACK_SM_MHZ = 2070.0
 # Algorithmic FP32 work of one planet-observation evaluation of the mixed
 # path, in FLOPs (FMA = 2, add/mul = 1; MUFU sin/cos/rcp and integer or
 # select operations not counted), from the algorithm as implemented:
-#   double-single mean anomaly 17, Mikkola's starting value 19 (its
-#   per-planet constants and the MUFU square root, logarithm, exponential
-#   and reciprocals not counted), one accurate sin/cos 27, the Halley step
+#   double-single mean anomaly 18 (its low part formed already scaled by
+#   2 pi), Mikkola's starting value 18 (its per-planet constants and the
+#   MUFU square root, logarithm, exponential and reciprocals not counted),
+#   one accurate sin/cos 27, the Halley step
 #   (12 in the tile kernels, 11 in the warp-per-system kernel, whose form
 #   cancels the factor 2), sin/cos update of the step 10, velocity 8, planet
 #   Kahan sum 4, and per observation the residual + weighted square + chi2
 #   Kahan sum 10 (shared by n_pl planets).  The per-(system, planet) setup
 #   is not counted.
-KEPLER_MIXED_FLOPS = 19 + 27 + 12 + 10
+KEPLER_MIXED_FLOPS = 18 + 27 + 12 + 10
+MEAN_ANOMALY_FLOPS = 18
 
 
 def mixed_flops_per_eval(n_pl: int, warp: bool = False) -> float:
     """FLOPs per evaluation of the tile kernels, or (warp=True) of the
     warp-per-system kernel (tile split 3)."""
-    return 17 + KEPLER_MIXED_FLOPS - (1 if warp else 0) + 8 + 4 + 10.0 / n_pl
+    return MEAN_ANOMALY_FLOPS + KEPLER_MIXED_FLOPS - (1 if warp else 0) + 8 + 4 + 10.0 / n_pl
 
 
 def mixed_kernel_name(n_pl: int, tile) -> str:
@@ -70,7 +72,7 @@ def mixed_kernel_name(n_pl: int, tile) -> str:
 # compensated dP sum 5 and the four other accumulations 8; per observation
 # the weighted residual, chi2 sum and gamma term 12 (instead of 10).
 def grad_flops_per_eval(n_pl: int) -> float:
-    return 17 + KEPLER_MIXED_FLOPS + 8 + 4 + 44 + 12.0 / n_pl
+    return MEAN_ANOMALY_FLOPS + KEPLER_MIXED_FLOPS + 8 + 4 + 44 + 12.0 / n_pl
 
 
 # The Gauss-Newton pass adds the row u = sqrt(w) J of U (5 products per

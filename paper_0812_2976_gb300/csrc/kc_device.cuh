@@ -117,6 +117,12 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// One MUFU operation, where x * rsqrt(x) takes two (x > 0 here).
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float lg2_fast(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -335,7 +341,7 @@ __device__ __forceinline__ float kepler_start(float M, float e) {
   const float a = (1.0f - e) * r;
   const float b = M * (0.5f * r);
   const float w = __fmaf_rn(b, b, a * a * a);
-  const float t = b + copysignf(w * rsqrt_fast(w), b);
+  const float t = b + copysignf(sqrt_fast(w), b);      // w >= a^3 > 0
   const float z = copysignf(ex2_fast(lg2_fast(fabsf(t)) * (1.0f / 3.0f)), t);
   float s = __fmaf_rn(-a, rcp_fast(z), z);
   const float s2 = s * s;
@@ -398,7 +404,7 @@ __device__ __forceinline__ StartF kepler_start_setup(float e) {
 __device__ __forceinline__ float kepler_start_h(float M, float e, const StartF &m) {
   const float b = M * m.bs;
   const float w = __fmaf_rn(b, b, m.a3);
-  const float tabs = fabsf(b) + w * rsqrt_fast(w);
+  const float tabs = fabsf(b) + sqrt_fast(w);           // w >= a^3 > 0
   const float z = ex2_fast(lg2_fast(tabs) * (1.0f / 3.0f));
   float s = __fmaf_rn(-m.a, rcp_fast(z), z);
   const float s2 = s * s;
@@ -578,10 +584,11 @@ struct PlanetD {
 };
 
 // Single-precision constants of one planet for the mixed path: 1/P and the
-// phase offset as float pairs (the "pair of single" arithmetic of Sec. 5),
-// e and the velocity constants.
+// phase offset as float pairs (the "pair of single" arithmetic of Sec. 5;
+// the low parts stored times 2 pi, the scale the mean anomaly needs them
+// in), e and the velocity constants.
 struct PlanetF {
-  float n_hi, n_lo, c_hi, c_lo, e, A, B, C;
+  float n_hi, n_lo2pi, c_hi, c_lo2pi, e, A, B, C;
 };
 
 // Parameter checks on the bit patterns (integer pipe, no FP64 compares):
@@ -799,7 +806,10 @@ __device__ __forceinline__ void phase_setup_ds(double P, double M0, double t_ref
 __device__ __forceinline__ PlanetF planet_setup_mixed(const double *p, double t_ref, double t0) {
   const double P = p[0], K = p[1], e = p[2], w = p[3], M0 = p[4];
   PlanetF q;
-  phase_setup_ds(P, M0, t_ref, t0, q.n_hi, q.n_lo, q.c_hi, q.c_lo);
+  float n_lo, c_lo;
+  phase_setup_ds(P, M0, t_ref, t0, q.n_hi, n_lo, q.c_hi, c_lo);
+  q.n_lo2pi = n_lo * kTwoPiF;
+  q.c_lo2pi = c_lo * kTwoPiF;
   const float ef = d2f(e);
   q.e = ef;
   // sin/cos of w to single-precision rounding although w itself is double:
@@ -824,15 +834,19 @@ __device__ __forceinline__ PlanetF planet_setup_mixed(const double *p, double t_
 // Mixed path.  tau = tau_hi + tau_lo = t - t_ref as a float pair.  The
 // product tau * (n_hi + n_lo) keeps its exact FMA remainder, so its
 // fractional part is good to ~1e-11 cycles although tau/P reaches 1e4
-// (valid for |tau/P| < 2^22).  Result in [-pi, pi] up to rounding.
+// (valid for |tau/P| < 2^22).  The low part of the phase is formed already
+// scaled by 2 pi, 2 pi (pe + tau_lo n_hi) + tau_hi (2 pi n_lo) + 2 pi c_lo,
+// and enters the final FMA M = 2 pi u + lo, one rounding.  Result in
+// [-pi, pi] up to rounding.
 __device__ __forceinline__ float mean_anomaly_mixed(float tau_hi, float tau_lo, const PlanetF &q) {
   const float p = __fmul_rn(tau_hi, q.n_hi);  // kept apart from p - round(p)
   const float pe = __fmaf_rn(tau_hi, q.n_hi, -p);
-  const float lo = __fmaf_rn(tau_hi, q.n_lo, __fmaf_rn(tau_lo, q.n_hi, pe)) + q.c_lo;
+  const float lo = __fmaf_rn(__fmaf_rn(tau_lo, q.n_hi, pe), kTwoPiF,
+                             __fmaf_rn(tau_hi, q.n_lo2pi, q.c_lo2pi));
   const float fp = __fsub_rn(p, round_small(p));              // exact
   float u = __fadd_rn(fp, q.c_hi);
   u = __fsub_rn(u, round_small(u));                           // exact
-  return (u + lo) * kTwoPiF;
+  return __fmaf_rn(u, kTwoPiF, lo);
 }
 
 // Pure single precision (the paper's all-float variant, for comparisons):

@@ -208,9 +208,9 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
         q = planet_setup_mixed(p, t_ref, a.t0);
         if (SINGLE) {     // 1/P and M0/(2 pi) in float, the phase taken from t - t0
           q.n_hi = 1.0f / d2f(p[0]);
-          q.n_lo = 0.0f;
+          q.n_lo2pi = 0.0f;
           q.c_hi = d2f(p[4]) * (1.0f / kTwoPiF);
-          q.c_lo = 0.0f;
+          q.c_lo2pi = 0.0f;
         }
         if (!planet_valid(p[0], p[1], p[2], p[3], p[4])) q.e = __int_as_float(0x7fc00000);
       }

@@ -5,7 +5,7 @@ graph-replayed launch.  Same tolerances as the uniform path."""
 import numpy as np
 import pytest
 import torch
-from tolerance import U32, U64, grad_bound, grad_excess_ragged, ragged_ariths
+from tolerance import U32, U64, chi2_rounding_term, grad_bound, grad_excess_ragged, ragged_ariths
 
 pytestmark = pytest.mark.gpu
 
@@ -145,8 +145,18 @@ def test_graph_replay_new_pointers_and_streams(kc, oracle_mod, small):
     c = plan.run(P1, chi2_out=torch.empty_like(a))
     ref1 = oracle_mod.chi2_ragged(w.params, w.par_off, w.n_pl, w.t, v, w.sigma, w.obs_off)
     ref2 = oracle_mod.chi2_ragged(w.truth, w.par_off, w.n_pl, w.t, v, w.sigma, w.obs_off)
-    assert rel_err(a.cpu().numpy(), ref1).max() <= MIXED_TOL
-    assert rel_err(b.cpu().numpy(), ref2).max() <= MIXED_TOL
+    # 1e-5 relative plus the residuals' rounding carried into chi2 (at the
+    # truth, chi2 ~ n_obs: a 2-observation system with K ~ 50 m/s moves by
+    # ~1e-5 of its chi2 per 1e-7 rad of M)
+    for got, ref, par in ((a, ref1, w.params), (b, ref2, w.truth)):
+        got = got.cpu().numpy().astype(np.float64)
+        for s in range(w.n_sys):
+            o0, o1 = w.obs_off[s], w.obs_off[s + 1]
+            p0, p1 = w.par_off[s], w.par_off[s + 1]
+            extra = chi2_rounding_term(oracle_mod, par[p0:p1], w.t[o0:o1], v[o0:o1],
+                                       w.sigma[o0:o1], int(w.n_pl[s]), 0.0, 0.0, U32)[0] \
+                if o1 > o0 else 0.0
+            assert abs(got[s] - ref[s]) <= MIXED_TOL * max(ref[s], 1.0) + extra, (s, got[s], ref[s])
     assert torch.equal(a, c)
     s2 = torch.cuda.Stream()
     with torch.cuda.stream(s2):

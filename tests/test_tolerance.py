@@ -90,17 +90,62 @@ def test_derived_terms_only_where_the_terms_cancel():
 def test_residual_error_grows_towards_pericentre(oracle_mod):
     """eps_k of the residual bound: circular orbits give the constant part;
     an eccentric orbit's largest value sits at pericentre (D = 1 - e)."""
-    from tolerance import residual_error
+    from tolerance import KAPPA_M, residual_error
     t = np.linspace(0.0, 10.0, 2001)
     circ = np.array([[10.0, 5.0, 0.0, 0.3, 0.0, 0.0]])
     ecc = np.array([[10.0, 5.0, 0.9, 0.3, 0.0, 0.0]])
     v = np.zeros_like(t)
     e0 = residual_error(oracle_mod, circ, t, v, 1, 0.0, U32)[0]
     e9 = residual_error(oracle_mod, ecc, t, v, 1, 0.0, U32)[0]
-    assert np.allclose(e0, U32 * (5.0 * (np.pi + 3 + 18) + 3 * np.abs(
+    assert np.allclose(e0, U32 * (5.0 * (KAPPA_M + 3 + 18) + 3 * np.abs(
         oracle_mod.predict(circ, t, 1)[0])), rtol=1e-12)
     k = int(np.argmax(e9))
     M = oracle_mod.mean_anomaly(t[k], 0.0, 10.0, 0.0)
     assert abs(np.remainder(M + np.pi, 2 * np.pi) - np.pi) < 0.05     # at pericentre
-    # K ((pi + 3) / D^2 + 18 / D) at D = 1 - e = 0.1, plus 3 |V| (< 1 % here)
-    assert np.isclose(e9.max(), U32 * 5.0 * ((np.pi + 3) / 0.1 ** 2 + 18 / 0.1), rtol=0.01)
+    # K ((KAPPA_M + 3) / D^2 + 18 / D) at D = 1 - e = 0.1, plus 3 |V| (< 1 % here)
+    assert np.isclose(e9.max(), U32 * 5.0 * ((KAPPA_M + 3) / 0.1 ** 2 + 18 / 0.1), rtol=0.01)
+
+
+def test_mean_anomaly_float_error_bound():
+    """KAPPA_M: the mixed path's mean anomaly (phase frac(tau/P) + c from
+    float pairs, its low part formed already times 2 pi, one final FMA with
+    the float 2 pi) emulated in float32 on 10^6 random phases stays within
+    KAPPA_M u of the exact value, and the bound is not loose by more than
+    a factor of two (a dropped term would show)."""
+    from tolerance import KAPPA_M
+    rng = np.random.default_rng(3)
+    n = 1_000_000
+    f32 = np.float32
+
+    def fma(x, y, z):      # float32 FMA: the exact product of two floats fits a double
+        return (np.float64(1) * x * y + z).astype(f32)
+
+    magic = f32(1.5 * 2 ** 23)
+
+    def rnd(x):
+        return ((x + magic) - magic).astype(f32)
+
+    P = np.exp(rng.uniform(0, np.log(4000), n))
+    tau = rng.uniform(0, 6000, n)
+    c = rng.uniform(-0.5, 0.5, n)
+    inv = 1.0 / P
+    n_hi = inv.astype(f32)
+    n_lo = (inv - n_hi).astype(f32)
+    c_hi = c.astype(f32)
+    c_lo = (c - c_hi).astype(f32)
+    th = tau.astype(f32)
+    tl = (tau - th).astype(f32)
+    two_pi = np.full(n, f32(2 * np.pi))
+    p = (th * n_hi).astype(f32)
+    pe = fma(th, n_hi, -p)
+    lo = fma(fma(tl, n_hi, pe), two_pi, fma(th, (n_lo * two_pi).astype(f32),
+                                             (c_lo * two_pi).astype(f32)))
+    u = ((p - rnd(p)).astype(f32) + c_hi).astype(f32)
+    u = (u - rnd(u)).astype(f32)
+    M = fma(u, two_pi, lo).astype(np.float64)
+    exact = tau / P + c
+    exact = (exact - np.round(exact)) * 2 * np.pi
+    err = np.abs(M - exact)
+    err = np.minimum(err, np.abs(err - 2 * np.pi))
+    assert err.max() <= KAPPA_M * U32
+    assert err.max() > 0.5 * KAPPA_M * U32

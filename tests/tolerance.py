@@ -29,13 +29,26 @@ kernels' own operations rather than from measured errors:
   the residual's own error, sum_k 2 w_k |d_ik| eps_k <= 2 sqrt(H_ii)
     sqrt(sum_k w_k eps_k^2) (Cauchy-Schwarz; H = sum_k w_k d_k d_k^T, the
     oracle's Gauss-Newton matrix), with eps_k bounding the computed
-    residual's absolute error: M rounded to float moves v_j by at most
-    u pi K_j / D_jk^2 (|dv/dM| <= K/D^2), the Kepler solve's rounding of f
-    (3 u) moves E by 3 u / D and v by 3 u K / D^2, sin/cos and the velocity's
-    evaluation (products, the reciprocal) by at most 18 u K / D, and the
-    planet sum and the residual add 3 u (|V_k| + |v_k|):
-        eps_k = u [sum_j K_j ((pi + 3) / D_jk^2 + 18 / D_jk)
+    residual's absolute error: M's float error, KAPPA_M u (below), moves
+    v_j by at most KAPPA_M u K_j / D_jk^2 (|dv/dM| <= K/D^2), the Kepler
+    solve's rounding of f (3 u) moves E by 3 u / D and v by 3 u K / D^2,
+    sin/cos and the velocity's evaluation (products, the reciprocal) by at
+    most 18 u K / D, and the planet sum and the residual add
+    3 u (|V_k| + |v_k|):
+        eps_k = u [sum_j K_j ((KAPPA_M + 3) / D_jk^2 + 18 / D_jk)
                    + 3 (|V_k| + |v_k|)].
+  M's error, from the mixed path's operations: the phase sum
+    u = frac(tau/P) + c rounds once (|u| < 1: 2^-25 cycles, 2 pi 2^-25 =
+    pi u rad), the float 2 pi differs from 2 pi by 1.75e-7 (times
+    |u| <= 1/2: 1.47 u), the final FMA rounds once (|M| <= pi: 2 u), the
+    low part and the phase offset are exact to ~1e-14 cycles:
+    KAPPA_M = pi + 3.5.
+
+The same eps_k bounds the chi2 of the mixed path: |d chi2| <= 1e-5
+max(chi2, 1) (the survey's relative bound, which covers the weights and
+the compensated sums) + 2 sum_k w_k |r_k| eps_k, the second term mattering
+only where chi2 is small and the amplitudes large (a model at its truth,
+few observations).
 
 A component whose bound is zero (an all-zero oracle row, e.g. a system
 without observations) must match exactly, and a NaN on one side only (the
@@ -51,6 +64,7 @@ import numpy as np
 U32 = 2.0 ** -24
 U64 = 2.0 ** -53
 KAPPA_FORM = 34.0
+KAPPA_M = math.pi + 3.5
 CANCELLING = 10.0       # sum_k |c_ik| above this multiple of |g_i|: cancellation
 
 
@@ -148,8 +162,19 @@ def residual_error(oracle, params, t, v_obs, n_pl, t0, u):
                                 np.broadcast_to(M0, (n_sys, t.size)))
         E = oracle.kepler_E(M, np.broadcast_to(e, M.shape))
         D = 1.0 - e * np.cos(E)
-        scale += np.abs(K) * ((math.pi + 3.0) / D ** 2 + 18.0 / D)
+        scale += np.abs(K) * ((KAPPA_M + 3.0) / D ** 2 + 18.0 / D)
     return u * (scale + 3.0 * (np.abs(V) + np.abs(np.asarray(v_obs, np.float64))[None, :]))
+
+
+def chi2_rounding_term(oracle, params, t, v_obs, sigma, n_pl, t0, jitter, u):
+    """[n_sys] 2 sum_k w_k |r_k| eps_k: the computed residuals' error carried
+    into chi2 (first order), r_k from the oracle's model."""
+    params = np.atleast_2d(np.asarray(params, np.float64))
+    v_obs = np.asarray(v_obs, np.float64)
+    w = 1.0 / (np.asarray(sigma, np.float64) ** 2 + jitter ** 2)
+    eps = residual_error(oracle, params, t, v_obs, n_pl, t0, u)
+    r = np.abs(oracle.predict(params[:, :5 * n_pl + 1], t, n_pl, t0) - v_obs[None, :])
+    return 2.0 * np.sum(w[None, :] * r * eps, axis=1)
 
 
 def residual_term(oracle, params, t, v_obs, sigma, n_pl, t0, jitter, u):
