@@ -46,20 +46,18 @@ FALLBACK_SM_MHZ = 2070.0
 #   double-single mean anomaly 18 (its low part formed already scaled by
 #   2 pi), Mikkola's starting value 18 (its per-planet constants and the
 #   MUFU square root, logarithm, exponential and reciprocals not counted),
-#   one accurate sin/cos 27, the Halley step
-#   (12 in the tile kernels, 11 in the warp-per-system kernel, whose form
-#   cancels the factor 2), sin/cos update of the step 10, velocity 8, planet
-#   Kahan sum 4, and per observation the residual + weighted square + chi2
-#   Kahan sum 10 (shared by n_pl planets).  The per-(system, planet) setup
-#   is not counted.
-KEPLER_MIXED_FLOPS = 18 + 27 + 12 + 10
+#   one accurate sin/cos 27, the Halley step 11, sin/cos update of the step
+#   10, velocity 8, planet Kahan sum 4, and per observation the residual +
+#   weighted square + chi2 Kahan sum 10 (shared by n_pl planets).  The
+#   per-(system, planet) setup is not counted.
+KEPLER_MIXED_FLOPS = 18 + 27 + 11 + 10
 MEAN_ANOMALY_FLOPS = 18
 
 
 def mixed_flops_per_eval(n_pl: int, warp: bool = False) -> float:
-    """FLOPs per evaluation of the tile kernels, or (warp=True) of the
-    warp-per-system kernel (tile split 3)."""
-    return MEAN_ANOMALY_FLOPS + KEPLER_MIXED_FLOPS - (1 if warp else 0) + 8 + 4 + 10.0 / n_pl
+    """FLOPs per evaluation of the mixed chi2 kernels (the tile kernels and
+    the warp-per-system kernel run the same per-evaluation arithmetic)."""
+    return MEAN_ANOMALY_FLOPS + KEPLER_MIXED_FLOPS + 8 + 4 + 10.0 / n_pl
 
 
 def mixed_kernel_name(n_pl: int, tile) -> str:

@@ -151,38 +151,6 @@ __device__ __forceinline__ double rcp_f64(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
-// sin and cos to about one ulp for |x| <= 8, on the FMA pipe.
-// Cody & Waite (1980) reduction x = q pi/2 + r, |r| <= pi/4, with pi/2 split
-// into two floats (q <= 5, so q * hi is exact inside the FMA), then the
-// Taylor series of sin to r^9 (truncation 1.8e-9 at pi/4) and of cos to
-// r^10 (1.1e-10), and the quadrant's swap and signs.
-constexpr float kTwoOverPi = 0.636619772367581343f;
-constexpr float kPiO2Hi = 1.57079637050628662109375f;      // RN(pi/2)
-constexpr float kPiO2Lo = -4.37113900018624283e-8f;        // pi/2 - kPiO2Hi
-
-__device__ __forceinline__ void sincos_accurate(float x, float &s, float &c) {
-  const float k = __fmaf_rn(x, kTwoOverPi, kRoundMagic);
-  const unsigned q = __float_as_uint(k);                    // low bits: q mod 4
-  const float qf = __fsub_rn(k, kRoundMagic);
-  float r = __fmaf_rn(-qf, kPiO2Hi, x);
-  r = __fmaf_rn(-qf, kPiO2Lo, r);
-  const float r2 = r * r;
-  float ps = __fmaf_rn(r2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = __fmaf_rn(r2, ps, 1.0f / 120.0f);
-  ps = __fmaf_rn(r2, ps, -1.0f / 6.0f);
-  const float sr = __fmaf_rn(r * r2, ps, r);
-  float pc = __fmaf_rn(r2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-  pc = __fmaf_rn(r2, pc, -1.0f / 720.0f);
-  pc = __fmaf_rn(r2, pc, 1.0f / 24.0f);
-  pc = __fmaf_rn(r2, pc, -0.5f);
-  const float cr = __fmaf_rn(r2, pc, 1.0f);
-  const bool swap = q & 1u;
-  const float s0 = swap ? cr : sr;
-  const float c0 = swap ? sr : cr;
-  s = __uint_as_float(__float_as_uint(s0) ^ ((q & 2u) << 30));
-  c = __uint_as_float(__float_as_uint(c0) ^ (((q + 1u) & 2u) << 30));
-}
-
 // sin and cos for |x| <= 3 pi / 2 (the starting values of the
 // single-precision Kepler solve lie within pi + 0.1): x = k pi + r with
 // k = round(x / pi) in {-1, 0, 1} and pi split into two floats (the first
@@ -192,8 +160,9 @@ __device__ __forceinline__ void sincos_accurate(float x, float &s, float &c) {
 // absolute error, 4.6e-9 and 2.4e-10; minimax_sincos.py prints the
 // coefficients).  Largest error over |x| <= pi + 0.1 in a float emulation:
 // 1.3e-7 (sin) and 1.1e-7 (cos), about one ulp of 1, most of it the rounding
-// of r near |r| = pi/2; 17 FMA-pipe and 3 integer operations where
-// sincos_accurate takes 17 and 9.
+// of r near |r| = pi/2; 17 FMA-pipe and 3 integer operations, where a
+// reduction by pi/2 would also select the quadrant and exchange sin and cos
+// (6 integer operations more).
 constexpr float kInvPiF = 0.318309886183790672f;          // RN(1/pi)
 constexpr float kPiHiF = 3.14159274101257324219f;         // RN(pi)
 constexpr float kPiLoF = -8.74227800037248566e-8f;        // pi - kPiHiF
@@ -335,48 +304,9 @@ __device__ __forceinline__ double danby_delta_f64(double E, double M, double e, 
 // where the paper's M + 0.85 e sign(sin M) is up to 0.84 rad off near
 // pericentre.  The cube root is exp2(log2|t|/3) on MUFU (|t| >= a^(3/2),
 // above 1e-12 for float e < 1); the accuracy of the approximations only
-// moves the start.
-__device__ __forceinline__ float kepler_start(float M, float e) {
-  const float r = rcp_fast(__fmaf_rn(4.0f, e, 0.5f));
-  const float a = (1.0f - e) * r;
-  const float b = M * (0.5f * r);
-  const float w = __fmaf_rn(b, b, a * a * a);
-  const float t = b + copysignf(sqrt_fast(w), b);      // w >= a^3 > 0
-  const float z = copysignf(ex2_fast(lg2_fast(fabsf(t)) * (1.0f / 3.0f)), t);
-  float s = __fmaf_rn(-a, rcp_fast(z), z);
-  const float s2 = s * s;
-  s = __fmaf_rn(-0.078f * rcp_fast(1.0f + e), s2 * s2 * s, s);
-  return __fmaf_rn(e, s * __fmaf_rn(-4.0f, s * s, 3.0f), M);
-}
-
-// Halley's step -2 f f' / (2 f'^2 - f f'') for f(E) = E - e sin E - M,
-// given s = sin E, c = cos E.  From Mikkola's start its cubic convergence
-// lands within 5.1e-9 rad of the root for every e < 1 (exact arithmetic),
-// below the float rounding of E.
-__device__ __forceinline__ float halley_delta_f32(float E, float M, float e, float s, float c) {
-  const float es = e * s;
-  const float f = (E - M) - es;
-  const float f1 = __fmaf_rn(-e, c, 1.0f);
-  const float num = f * f1;
-  return -(num + num) * rcp_fast(__fmaf_rn(f1 + f1, f1, -(f * es)));
-}
-
-// Kepler's equation in single precision: Mikkola's start, sin/cos to an ulp
-// there (Cody-Waite + Taylor, FMA pipe) and one Halley step.  sin/cos of
-// the returned E come from that evaluation by the angle-addition expansion
-// to second order in the step (|delta| < 3.6e-3, truncation < 8e-9).  No
-// branch on e: the same straight-line code for every eccentricity.
-__device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &cE) {
-  const float E = kepler_start(M, e);
-  float s, c;
-  sincos_accurate(E, s, c);
-  const float d = halley_delta_f32(E, M, e, s, c);
-  const float hd2 = 0.5f * d * d;
-  sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
-  cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
-  return E + d;
-}
-
+// moves the start.  The constants that depend on e only are formed once
+// per (system, planet) where the kernel can (kepler_start_setup).
+//
 // The per-planet part of Mikkola's start, formed once per (system, planet)
 // instead of at every evaluation: r = 1/(4 e + 1/2), bs = r/2 (b = M bs),
 // a = (1 - e) r, a3 = a^3 and the quintic correction's factor
@@ -399,8 +329,7 @@ __device__ __forceinline__ StartF kepler_start_setup(float e) {
 // (sign(b) = sign(M)), so it is formed on |b|: |t| = |b| + sqrt(b^2 + a^3),
 // z = |t|^(1/3) >= sqrt(a), s = z - a/z >= 0, the quintic correction
 // s (1 + corr s^4), and the sign of M applied once before
-// E0 = M + e s (3 - 4 s^2).  The same values as kepler_start up to the
-// rounding of the factored forms.
+// E0 = M + e s (3 - 4 s^2).
 __device__ __forceinline__ float kepler_start_h(float M, float e, const StartF &m) {
   const float b = M * m.bs;
   const float w = __fmaf_rn(b, b, m.a3);
@@ -413,8 +342,10 @@ __device__ __forceinline__ float kepler_start_h(float M, float e, const StartF &
   return __fmaf_rn(e, ss * __fmaf_rn(-4.0f, s * s, 3.0f), M);
 }
 
-// Halley's step -f f' / (f'^2 - f f''/2), f'' = e sin E: the form of
-// halley_delta_f32 with the factor 2 cancelled (one operation fewer).
+// Halley's step -f f' / (f'^2 - f f''/2) for f(E) = E - e sin E - M,
+// f' = 1 - e cos E, f'' = e sin E, given s = sin E and c = cos E.  From
+// Mikkola's start its cubic convergence lands within 5.1e-9 rad of the root
+// for every e < 1 (exact arithmetic), below the float rounding of E.
 __device__ __forceinline__ float halley_delta_h(float E, float M, float e, float s, float c) {
   const float es = e * s;
   const float f = (E - M) - es;
@@ -423,9 +354,12 @@ __device__ __forceinline__ float halley_delta_h(float E, float M, float e, float
   return -(f * f1) * rcp_fast(den);
 }
 
-// kepler_f32 with the hoisted start constants and sincos_pi (the same
-// steps: start, sin/cos to about an ulp, one Halley step, angle-addition
-// update of sin/cos).
+// Kepler's equation in single precision from the hoisted start constants:
+// Mikkola's start, sin/cos to about an ulp there (sincos_pi, FMA pipe), one
+// Halley step, and sin/cos of the returned E from that evaluation by the
+// angle-addition expansion to second order in the step (|delta| < 3.6e-3,
+// truncation < 8e-9).  No branch on e: the same straight-line code for
+// every eccentricity.
 __device__ __forceinline__ float kepler_f32_h(float M, float e, const StartF &m, float &sE,
                                               float &cE) {
   const float E = kepler_start_h(M, e, m);
@@ -436,6 +370,24 @@ __device__ __forceinline__ float kepler_f32_h(float M, float e, const StartF &m,
   sE = __fmaf_rn(d, c, __fmaf_rn(-hd2, s, s));
   cE = __fmaf_rn(-d, s, __fmaf_rn(-hd2, c, c));
   return E + d;
+}
+
+// The start constants for one evaluation, where every (M, e) has its own e
+// (the Kepler-only solver; the FP64 path's single-precision first solve):
+// approximate reciprocals instead of divisions, the same values up to
+// their rounding.
+__device__ __forceinline__ StartF kepler_start_consts(float e) {
+  const float r = rcp_fast(__fmaf_rn(4.0f, e, 0.5f));
+  StartF m;
+  m.bs = 0.5f * r;
+  m.a = (1.0f - e) * r;
+  m.a3 = m.a * m.a * m.a;
+  m.corr = -0.078f * rcp_fast(1.0f + e);
+  return m;
+}
+
+__device__ __forceinline__ float kepler_f32(float M, float e, float &sE, float &cE) {
+  return kepler_f32_h(M, e, kepler_start_consts(e), sE, cE);
 }
 
 // Warp-uniform choice of the double-precision solver's HI variant: true if

@@ -37,6 +37,7 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 struct GradPlanetF {
   PlanetF base;    // phase and velocity constants of the forward path
   float K, cw, sw, beta, n2, ibeta;   // n2 = (1/P)^2
+  StartF m;        // the e-only constants of Mikkola's start
 };
 
 struct GradPlanetD {
@@ -59,6 +60,7 @@ __device__ inline GradPlanetF grad_setup_mixed(const double *p, double t_ref, do
   g.ibeta = 1.0f / g.beta;
   const float n = g.base.n_hi;
   g.n2 = n * n;
+  g.m = kepler_start_setup(e);
   return g;
 }
 
@@ -223,7 +225,7 @@ grad_mixed_kernel(UniformArgs a, int G, int obs_tile, float *__restrict__ chi2_o
       for (int j = 0; j < J; ++j) {
         const PlanetF p = q[j].base;
         const float M = mean_anomaly_mixed(o.x, o.y, p);
-        kepler_f32(M, p.e, sEj[j], cEj[j]);
+        kepler_f32_h(M, p.e, q[j].m, sEj[j], cEj[j]);
         kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
       }
       const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
@@ -492,7 +494,7 @@ __device__ __forceinline__ void gn_obs(const float4 &o, const float4 &wt, bool l
   for (int j = 0; j < J; ++j) {
     const PlanetF &p = qr[j].base;
     const float M = mean_anomaly_mixed(o.x, o.y, p);
-    kepler_f32(M, p.e, sEj[j], cEj[j]);
+    kepler_f32_h(M, p.e, qr[j].m, sEj[j], cEj[j]);
     kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
   }
   const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
@@ -620,7 +622,7 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
         for (int j = 0; j < J; ++j) {
           const PlanetF p = q[j].base;
           const float M = mean_anomaly_mixed(o.x, o.y, p);
-          kepler_f32(M, p.e, sEj[j], cEj[j]);
+          kepler_f32_h(M, p.e, q[j].m, sEj[j], cEj[j]);
           kahan_add(V, velocity_mixed(p, sEj[j], cEj[j]));
         }
         const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));

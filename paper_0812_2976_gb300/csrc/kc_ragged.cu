@@ -149,6 +149,7 @@ __global__ void predict_ragged_kernel(const double *__restrict__ params,
 struct RPlanetF {
   PlanetF base;
   float K, cw, sw, beta, n2, ibeta;   // ibeta = 1/beta
+  StartF m;                           // the e-only constants of Mikkola's start
 };
 
 struct RPlanetD {
@@ -159,6 +160,7 @@ struct RPlanetD {
 __device__ inline RPlanetF rsetup_mixed(const double *p, double t_ref, double t0, bool grad) {
   RPlanetF g;
   g.base = planet_setup_mixed(p, t_ref, t0);
+  g.m = kepler_start_setup(g.base.e);
   g.K = g.cw = g.sw = g.beta = g.n2 = g.ibeta = 0.0f;
   if (grad) {
     float w_hi, w_lo;
@@ -241,7 +243,7 @@ __device__ __forceinline__ void body_mixed(const RPlanetF *pl, float gam, const 
     for (int j = 0; j < J; ++j) {
       const PlanetF q = pl[j].base;
       const float M = mean_anomaly_mixed(o.x, o.y, q);
-      kepler_f32(M, q.e, sEj[j], cEj[j]);
+      kepler_f32_h(M, q.e, pl[j].m, sEj[j], cEj[j]);
       kahan_add(V, velocity_mixed(q, sEj[j], cEj[j]));
     }
     const float r = __fadd_rn(__fsub_rn(V.big, o.z), __fsub_rn(gam, __fadd_rn(V.small, o.w)));
