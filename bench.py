@@ -589,44 +589,65 @@ def run_kc(args):
     # end-to-end through the public API from pinned host memory: the step's
     # inputs (parameters, times, velocities, uncertainties) packed in one
     # pinned buffer and sent with one copy into one device buffer, whose
-    # views the library reads; chi2 comes back with one copy
+    # views the library reads; chi2 comes back with one copy.  Steps
+    # alternate between two streams and two sets of device and pinned
+    # output buffers, as a serving loop would drive the library: one step's
+    # copies overlap the other's kernel.  Timed from the first copy of the
+    # first step to the last read of the last (CUDA events, both streams
+    # joined), every step's copies inside; no L2 flush between the steps
+    # (each step's inputs arrive fresh from the host)
     n_par, n_obs = P.numel(), T.numel()
     hbuf = torch.cat([torch.tensor(w.params).ravel(), T.cpu(), V.cpu(), S.cpu()]).pin_memory()
-    dbuf = torch.empty_like(hbuf, device=dev)
-    dP = dbuf[:n_par].view(P.shape)
-    dT, dV, dS = (dbuf[n_par + i * n_obs:n_par + (i + 1) * n_obs] for i in range(3))
-    hout = torch.empty(w.n_sys, dtype=torch.float32).pin_memory()
+    pipe = [stream, torch.cuda.Stream(dev)]
+    bufs = []
+    for _ in pipe:
+        dbuf = torch.empty_like(hbuf, device=dev)
+        views = (dbuf[:n_par].view(P.shape),) + tuple(
+            dbuf[n_par + i * n_obs:n_par + (i + 1) * n_obs] for i in range(3))
+        bufs.append((dbuf, views, torch.empty(w.n_sys, dtype=torch.float32, device=dev),
+                     torch.empty(w.n_sys, dtype=torch.float32).pin_memory()))
 
-    def e2e_step():
-        dbuf.copy_(hbuf, non_blocking=True)
-        kc.kc_chi2_eval_mixed(dP, dT, dV, dS, out=out, stream=stream)
-        hout.copy_(out, non_blocking=True)
+    def e2e_step(i):
+        st = pipe[i % 2]
+        dbuf, (dP, dT, dV, dS), dout, hout = bufs[i % 2]
+        with torch.cuda.stream(st):
+            dbuf.copy_(hbuf, non_blocking=True)
+            kc.kc_chi2_eval_mixed(dP, dT, dV, dS, out=dout, stream=st)
+            hout.copy_(dout, non_blocking=True)
 
-    for _ in range(3):
-        e2e_step()
+    def e2e_run(n):
+        """n pipelined steps between two events on the first stream."""
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        joined = torch.cuda.Event()
+        t0e.record(pipe[0])
+        pipe[1].wait_event(t0e)
+        for i in range(n):
+            e2e_step(i)
+        joined.record(pipe[1])
+        pipe[0].wait_event(joined)
+        t1e.record(pipe[0])
+        return t0e, t1e
+
+    e2e_run(4)
     torch.cuda.synchronize(dev)
-    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in range(args.steps)]
     hold_gpu(stream, args.steps * 400.0)
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        e_ev[i][0].record(stream)
-        e2e_step()
-        e_ev[i][1].record(stream)
+    t0e, t1e = e2e_run(args.steps)
     torch.cuda.synchronize(dev)
-    e2e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
+    e2e_s = t0e.elapsed_time(t1e) / 1e3
     h2d = hbuf.numel() * 8
-    d2h = hout.numel() * 4
+    d2h = w.n_sys * 4
     e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "how": "steps alternating between two streams (copies of one overlap the other's "
+                  "kernel), CUDA events from the first copy to the last read"}
 
     # the same steps on the host's clock: back-to-back calls through the
     # binding and the C ABI (ctypes, argument checks, launch) with their
     # copies, one synchronise at the end; no GPU hold, no L2 flush
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    for i in range(args.steps):
+        e2e_step(i)
     torch.cuda.synchronize(dev)
     wall_s = time.perf_counter() - wall0
     if world > 1:
@@ -635,8 +656,8 @@ def run_kc(args):
     e2e_wall = {"value": evals * args.steps * world / wall_s, "unit": "planet-obs evals/s",
                 "ms_per_step": 1e3 * wall_s / args.steps,
                 "how": "time.perf_counter around the timed steps of the e2e leg issued back "
-                       "to back (H2D copy, kc_chi2_eval_mixed, D2H copy), final synchronise "
-                       "included"}
+                       "to back (H2D copy, kc_chi2_eval_mixed, D2H copy, alternating between "
+                       "two streams), final synchronise included"}
 
     extras = {}
     if not args.no_extras:
@@ -854,26 +875,52 @@ def ragged_measure(kc, synth, dev, stream, flush, args, world=1, rank=0, compact
                        "flops_per_step": flops_step}
 
     # end to end: host parameters in, host chi2 + gradient out (the plan
-    # writes both into views of one device buffer, returned with one copy)
+    # writes both into views of one device buffer, returned with one copy);
+    # steps alternate between two streams (the plan keeps a work queue and a
+    # graph per stream) so that one step's copies overlap the other's
+    # kernel; CUDA events from the first copy to the last read
     hP = torch.tensor(w.params).pin_memory()
-    dP = torch.empty_like(P)
     n_out = chi.numel() + (grad.numel() if want_grad else 0)
-    dout = torch.empty(n_out, dtype=chi.dtype, device=dev)
-    echi = dout[:chi.numel()]
-    egrad = dout[chi.numel():] if want_grad else None
-    hout = torch.empty(n_out, dtype=chi.dtype).pin_memory()
+    pipe = [stream, torch.cuda.Stream(dev)]
+    bufs = []
+    for _ in pipe:
+        dP = torch.empty_like(P)
+        dout = torch.empty(n_out, dtype=chi.dtype, device=dev)
+        bufs.append((dP, dout, dout[:chi.numel()], dout[chi.numel():] if want_grad else None,
+                     torch.empty(n_out, dtype=chi.dtype).pin_memory()))
 
-    def e2e_step():
-        dP.copy_(hP, non_blocking=True)
-        plan.run(dP, echi, egrad)
-        hout.copy_(dout, non_blocking=True)
+    def e2e_step(i):
+        st = pipe[i % 2]
+        dP, dout, echi, egrad, hout = bufs[i % 2]
+        with torch.cuda.stream(st):
+            dP.copy_(hP, non_blocking=True)
+            plan.run(dP, echi, egrad, stream=st)
+            hout.copy_(dout, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
-    e2e_s = time_steps(e2e_step, args.steps, stream, flush)
+    def e2e_run(n):
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        joined = torch.cuda.Event()
+        t0e.record(pipe[0])
+        pipe[1].wait_event(t0e)
+        for i in range(n):
+            e2e_step(i)
+        joined.record(pipe[1])
+        pipe[0].wait_event(joined)
+        t1e.record(pipe[0])
+        return t0e, t1e
+
+    e2e_run(4)                                  # captures each stream's graph
+    torch.cuda.synchronize(dev)
+    hold_gpu(stream, args.steps * 400.0)
+    t0e, t1e = e2e_run(args.steps)
+    torch.cuda.synchronize(dev)
+    e2e_s = t0e.elapsed_time(t1e) / 1e3
     out["e2e"] = {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
-                  "h2d_bytes_per_step": hP.numel() * 8, "d2h_bytes_per_step": hout.numel() * 4}
-    del plan, dP, dout, hP, hout, chi, grad
+                  "h2d_bytes_per_step": hP.numel() * 8,
+                  "d2h_bytes_per_step": n_out * chi.element_size(),
+                  "how": "steps alternating between two streams, CUDA events from the first "
+                         "copy to the last read"}
+    del plan, bufs, hP, chi, grad
 
     if not args.no_extras or compact:
         out.update(ragged_extras(args, kc, synth, w, P, T, V, S, evals, stream, flush, dev))
