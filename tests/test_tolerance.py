@@ -66,7 +66,7 @@ def test_ragged_rows_of_different_lengths():
 
 
 def test_derived_terms_only_where_the_terms_cancel():
-    """Non-cancelling components keep the survey's bound; cancelling ones add
+    """Non-cancelling components keep the base bound; cancelling ones add
     (KAPPA_FORM + accumulation) u sum|c| and the residual term."""
     from tolerance import KAPPA_FORM, Arith, grad_bound
     ref = np.array([[1.0, 1e-4, 1e-4, 2.0]])

@@ -2,7 +2,7 @@
 
 Each component of the chi2 (or nll) gradient is a sum over observations,
 g_i = sum_k c_ik with c_ik = 2 w_k r_k d_ik (d_ik = dV_k/dtheta_i, r_k the
-residual).  The survey's bound,
+residual).  The base bound,
 
     rel * max(|g_i|, 1e-3 ||g||)        (rel = 1e-3 single, 1e-9 double),
 
@@ -45,7 +45,7 @@ kernels' own operations rather than from measured errors:
     KAPPA_M = pi + 3.5.
 
 The same eps_k bounds the chi2 of the mixed path: |d chi2| <= 1e-5
-max(chi2, 1) (the survey's relative bound, which covers the weights and
+max(chi2, 1) (the relative bound of the mixed path, which covers the weights and
 the compensated sums) + 2 sum_k w_k |r_k| eps_k, the second term mattering
 only where chi2 is small and the amplitudes large (a model at its truth,
 few observations).
