@@ -295,13 +295,15 @@ def gn_with_split(kc, split, P, T, V, S, w, stream):
         kc.kc_set_tile("gn", "mixed", w.n_sys, w.n_pl, w.n_obs, prev)
 
 
-def demcmc_throughput(kc, w, P, T, V, S, dev, generations=50):
+def demcmc_throughput(kc, w, P, T, V, S, dev, generations=64):
     """DE-MC (two-half differential evolution) over the batch's 4096 model
     systems as a population: generations per second with graph replay."""
     import torch
     mc = kc.DEMCMC(P, T, V, S, mode="mixed", eps_scale=1e-6, hop_every=0, seed=5,
                    autotune=True)
-    mc.run(4)        # one eager generation, one to align the draw buffers, one captured pair
+    span = 2 * mc.batch                     # generations per graph replay
+    mc.run(2 * span)    # eager until the draw buffers align, then one captured span
+    generations = max(span, generations // span * span)
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     hold_gpu(torch.cuda.current_stream(dev), generations * 300.0)

@@ -517,16 +517,19 @@ class DEMCMC:
     x^2) per parameter (``eps_scale`` a number or one value per parameter; 0
     together with equal values in every chain holds a parameter fixed).
     Random draws come from a torch generator on the device; the step itself
-    is kc_demcmc_step.  The draws do not depend on the chains, so those of
-    generation g + 1 are made on a side stream while generation g steps
-    (two buffers), in the same order as one generation after another.  ``autotune``: time the chi2 tiles once for the size
-    class of half the population (what each step evaluates) and keep the
-    fastest; off by default, since the pick depends on timing and so can
-    change the summation order from one run to the next."""
+    is kc_demcmc_step.  The draws do not depend on the chains, so they are
+    made ``draw_batch`` generations at a time, for the next batch on a side
+    stream while the current batch steps (two buffers), in the same order
+    whether the generations run eagerly or from a CUDA graph; the
+    acceptances of a batch are tallied once, with the next batch's draws.
+    ``autotune``: time the chi2 tiles once for the size class of half the
+    population (what each step evaluates) and keep the fastest; off by
+    default, since the pick depends on timing and so can change the
+    summation order from one run to the next."""
 
     def __init__(self, states, t, v_obs, sigma, t0: float = 0.0, jitter: float = 0.0,
                  mode="mixed", eps_scale: float = 1e-6, hop_every: int = 10, seed: int = 0,
-                 autotune: bool = False):
+                 autotune: bool = False, draw_batch: int = 8):
         self.states = _dev_f64("states", states, 2).clone()
         n = self.states.shape[0]
         if n < 8 or n % 2:
@@ -535,6 +538,9 @@ class DEMCMC:
         self.t0, self.jitter, self.mode = float(t0), float(jitter), mode
         self.npar = self.states.shape[1]
         self.half = n // 2
+        if draw_batch < 1:
+            raise ValueError("draw_batch must be at least 1")
+        self.batch = int(draw_batch)
         self.gamma = 2.38 / (2.0 * self.npar) ** 0.5
         self.eps_scale = torch.as_tensor(eps_scale, dtype=torch.float64,
                                          device=self.states.device).expand(self.npar).clone()
@@ -550,48 +556,58 @@ class DEMCMC:
         self._prop = torch.empty((self.half, self.npar), dtype=torch.float64, device=dev)
         self._cp = torch.empty(self.half, dtype=self.chi2.dtype, device=dev)
         self.generation = 0
-        # acceptances per chain, summed only when read: one element-wise add
-        # a generation, on the side stream (a generation's accepted flags
-        # are added while the next one steps; two flag buffers)
-        self._acc = [torch.zeros(n, dtype=torch.int32, device=dev) for _ in (0, 1)]
+        # accepted flags per generation slot of a batch (two buffers),
+        # tallied per chain once a batch, on the side stream, while the
+        # next batch steps
+        G = self.batch
+        self._acc = [torch.zeros((G, n), dtype=torch.int32, device=dev) for _ in (0, 1)]
         self._n_acc = torch.zeros(n, dtype=torch.int64, device=dev)
         self.proposed = 0
         self._graph = None
         self._side = torch.cuda.Stream(device=dev)
-        self._z32 = torch.empty((n, self.npar), dtype=torch.float32, device=dev)
-        self._z = [torch.empty((n, self.npar), dtype=torch.float64, device=dev) for _ in (0, 1)]
-        self._u = [torch.empty((n, 3), dtype=torch.float64, device=dev) for _ in (0, 1)]
-        self._buf = 0                    # the buffer holding the next generation's draws
+        self._z32 = torch.empty((G, n, self.npar), dtype=torch.float32, device=dev)
+        self._z = [torch.empty((G, n, self.npar), dtype=torch.float64, device=dev)
+                   for _ in (0, 1)]
+        self._u = [torch.empty((G, n, 3), dtype=torch.float64, device=dev) for _ in (0, 1)]
+        self._buf = 0                    # the buffer holding the current batch's draws
+        self._slot = 0                   # the next generation's slot in it
         self._draws(0)
 
     def _draws(self, b: int) -> None:
-        """Every random number of one generation (both halves) into buffer
-        b: standard normal perturbations and three uniforms per chain
-        (acceptance, two partners); the step kernels scale and map them.
-        The normals are drawn in single precision (a perturbation needs no
-        more; double precision normals cost 27 us a generation on this GPU,
-        these 15) and widened."""
+        """Every random number of one batch of generations (both halves)
+        into buffer b: standard normal perturbations and three uniforms per
+        chain (acceptance, two partners) for each generation; the step
+        kernels scale and map them.  The normals are drawn in single
+        precision (a perturbation needs no more; double precision normals
+        cost 27 us a generation on this GPU, these 15) and widened."""
         torch.randn(self._z32.shape, generator=self.gen, out=self._z32)
         self._z[b].copy_(self._z32)
         torch.rand(self._u[b].shape, generator=self.gen, out=self._u[b])
 
     def _generation(self, gamma: float) -> None:
-        cur, nxt = self._buf, 1 - self._buf
+        cur, k = self._buf, self._slot
         main = torch.cuda.current_stream(self.states.device)
-        # buffers nxt were last used by the previous generation's steps
-        self._side.wait_stream(main)
-        with torch.cuda.stream(self._side):
-            self._n_acc += self._acc[nxt]          # the previous generation's flags
-            self._draws(nxt)
-        z, u, acc = self._z[cur], self._u[cur], self._acc[cur]
+        if k == 0:
+            # a new batch: the other buffer (last used by the previous
+            # batch's steps) takes the next batch's draws, after its flags
+            # are tallied
+            nxt = 1 - cur
+            self._side.wait_stream(main)
+            with torch.cuda.stream(self._side):
+                self._n_acc += self._acc[nxt].sum(dim=0)
+                self._draws(nxt)
+        z, u, acc = self._z[cur][k], self._u[cur][k], self._acc[cur][k]
         h = self.half
         for first, other in ((0, h), (h, 0)):
             kc_demcmc_step(self.states, self.chi2, self.t, self.v, self.sigma, first, h, other, h,
                            gamma, self.eps_scale, z[first:first + h], u[first:first + h],
                            self._prop, self._cp, acc[first:first + h], self.t0,
                            self.jitter, self.mode)
-        main.wait_stream(self._side)
-        self._buf = nxt
+        self._slot = k + 1
+        if self._slot == self.batch:
+            main.wait_stream(self._side)           # the next batch's draws are made
+            self._slot = 0
+            self._buf = 1 - cur
 
     def _gamma(self, ahead: int = 1) -> float:
         hop = self.hop_every and (self.generation + ahead) % self.hop_every == 0
@@ -604,25 +620,27 @@ class DEMCMC:
         self.generation += 1
 
     def run(self, generations: int, use_graph: bool = True) -> None:
-        """``generations`` generations; with use_graph, two generations (one
-        on each draw buffer) are captured into a CUDA graph, random draws
-        included, and replayed, which removes the per-launch host overhead
-        for small populations.  The first generation, the gamma = 1
-        generations and any that would leave a pair unaligned with the draw
-        buffers run eagerly."""
+        """``generations`` generations; with use_graph, two batches of
+        generations (one on each draw buffer) are captured into a CUDA
+        graph, random draws included, and replayed, which removes the
+        per-launch host overhead for small populations.  The first
+        generation, and the generations of any two batches that hold a
+        gamma = 1 generation or would be cut short, run eagerly."""
+        span = 2 * self.batch
         while generations > 0:
-            pair = (use_graph and generations >= 2 and self.generation > 0 and self._buf == 0
-                    and self._gamma(1) == self.gamma and self._gamma(2) == self.gamma)
-            if not pair:
+            whole = (use_graph and generations >= span and self.generation > 0
+                     and self._buf == 0 and self._slot == 0
+                     and all(self._gamma(i) == self.gamma for i in range(1, span + 1)))
+            if not whole:
                 self.step()
                 generations -= 1
                 continue
             if self._graph is None:
                 self._capture()
             self._graph.replay()
-            self.generation += 2
-            self.proposed += 4 * self.half
-            generations -= 2
+            self.generation += span
+            self.proposed += 2 * span * self.half
+            generations -= span
 
     def _capture(self) -> None:
         dev = self.states.device
@@ -633,16 +651,22 @@ class DEMCMC:
         g.register_generator_state(self.gen)              # replays advance self.gen
         with torch.cuda.stream(cap):
             with torch.cuda.graph(g, stream=cap):
-                self._generation(self.gamma)               # draw buffer 0 ...
-                self._generation(self.gamma)               # ... then 1: back to 0
+                for _ in range(2 * self.batch):            # buffer 0's batch, then 1's:
+                    self._generation(self.gamma)           # back to buffer 0, slot 0
         torch.cuda.current_stream(dev).wait_stream(cap)
         self._graph = g
 
     @property
     def acceptance(self) -> float:
-        """Fraction of accepted proposals so far (synchronises)."""
-        last = self._acc[1 - self._buf] if self.generation else self._acc[0][:0]
-        return (int(self._n_acc.sum()) + int(last.sum())) / max(self.proposed, 1)
+        """Fraction of accepted proposals so far (synchronises): the tallied
+        batches, the flags of the batch before the current one when its
+        tally is still to come (the current batch has not begun), and the
+        current batch's generations so far."""
+        torch.cuda.synchronize(self.states.device)
+        total = int(self._n_acc.sum()) + int(self._acc[self._buf][:self._slot].sum())
+        if self._slot == 0 and self.generation > 0:
+            total += int(self._acc[1 - self._buf].sum())
+        return total / max(self.proposed, 1)
 
 
 class _Chi2Fn(torch.autograd.Function):

@@ -129,11 +129,13 @@ def test_driver_samples_the_linear_gaussian_posterior(kc):
     assert np.all(st[:, 0] == P) and np.all(st[:, 3] == w) and np.all(st[:, 4] == M0)
 
 
-@pytest.mark.parametrize("generations,hop_every", [(12, 0), (13, 4)])
-def test_graph_replay_equals_eager(kc, generations, hop_every):
+@pytest.mark.parametrize("generations,hop_every,batch",
+                         [(12, 0, 2), (13, 4, 2), (13, 5, 2), (40, 0, 8), (7, 0, 1)])
+def test_graph_replay_equals_eager(kc, generations, hop_every, batch):
     """The same seed gives the same chain eagerly and with graph replay
-    (replayed pairs of generations, eager gamma = 1 generations between
-    them, an odd count)."""
+    (replayed spans of two draw batches, eager generations around them and
+    for spans holding a gamma = 1 generation, counts that cut a batch),
+    and the same acceptance tally."""
     from paper_0812_2976_gb300 import synth
     import oracle
     w = synth.uniform(1, n_sys=256)
@@ -141,7 +143,7 @@ def test_graph_replay_equals_eager(kc, generations, hop_every):
     runs = []
     for use_graph in (False, True):
         mc = kc.DEMCMC(dev(w.params), dev(w.t), dev(v), dev(w.sigma), mode="mixed",
-                       eps_scale=1e-6, hop_every=hop_every, seed=11)
+                       eps_scale=1e-6, hop_every=hop_every, seed=11, draw_batch=batch)
         mc.run(generations - 5, use_graph=use_graph)
         mc.run(5, use_graph=use_graph)
         assert mc.generation == generations
