@@ -594,10 +594,11 @@ def run_kc(args):
     # views the library reads; chi2 comes back with one copy.  Steps
     # alternate between two streams and two sets of device and pinned
     # output buffers, as a serving loop would drive the library: one step's
-    # copies overlap the other's kernel.  Timed from the first copy of the
-    # first step to the last read of the last (CUDA events, both streams
-    # joined), every step's copies inside; no L2 flush between the steps
-    # (each step's inputs arrive fresh from the host)
+    # copies overlap the other's kernel, while each kernel waits for the
+    # previous step's (kernels never overlap one another).  Timed from the
+    # first copy of the first step to the last read of the last (CUDA
+    # events, both streams joined), every step's copies inside; no L2 flush
+    # between the steps (each step's inputs arrive fresh from the host)
     n_par, n_obs = P.numel(), T.numel()
     hbuf = torch.cat([torch.tensor(w.params).ravel(), T.cpu(), V.cpu(), S.cpu()]).pin_memory()
     pipe = [stream, torch.cuda.Stream(dev)]
@@ -609,12 +610,17 @@ def run_kc(args):
         bufs.append((dbuf, views, torch.empty(w.n_sys, dtype=torch.float32, device=dev),
                      torch.empty(w.n_sys, dtype=torch.float32).pin_memory()))
 
+    kernel_done = [torch.cuda.Event(), torch.cuda.Event()]
+
     def e2e_step(i):
         st = pipe[i % 2]
         dbuf, (dP, dT, dV, dS), dout, hout = bufs[i % 2]
         with torch.cuda.stream(st):
             dbuf.copy_(hbuf, non_blocking=True)
+            if i > 0:
+                st.wait_event(kernel_done[(i - 1) % 2])      # the previous step's kernel
             kc.kc_chi2_eval_mixed(dP, dT, dV, dS, out=dout, stream=st)
+            kernel_done[i % 2].record(st)
             hout.copy_(dout, non_blocking=True)
 
     def e2e_run(n):
@@ -641,15 +647,26 @@ def run_kc(args):
     e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "steps alternating between two streams (copies of one overlap the other's "
-                  "kernel), CUDA events from the first copy to the last read"}
+                  "kernel; each kernel after the previous one), CUDA events from the first "
+                  "copy to the last read, no L2 flush"}
 
     # the same steps on the host's clock: back-to-back calls through the
     # binding and the C ABI (ctypes, argument checks, launch) with their
-    # copies, one synchronise at the end; no GPU hold, no L2 flush
+    # copies on one stream, one synchronise at the end; no GPU hold, no L2
+    # flush (the host's cost per call is what this measures)
+    dbuf0, (dP0, dT0, dV0, dS0), dout0, hout0 = bufs[0]
+
+    def wall_step():
+        dbuf0.copy_(hbuf, non_blocking=True)
+        kc.kc_chi2_eval_mixed(dP0, dT0, dV0, dS0, out=dout0, stream=stream)
+        hout0.copy_(dout0, non_blocking=True)
+
+    for _ in range(3):
+        wall_step()
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        e2e_step(i)
+    for _ in range(args.steps):
+        wall_step()
     torch.cuda.synchronize(dev)
     wall_s = time.perf_counter() - wall0
     if world > 1:
@@ -657,9 +674,9 @@ def run_kc(args):
         wall_s = kdist.max_over_ranks(wall_s, device=dev)
     e2e_wall = {"value": evals * args.steps * world / wall_s, "unit": "planet-obs evals/s",
                 "ms_per_step": 1e3 * wall_s / args.steps,
-                "how": "time.perf_counter around the timed steps of the e2e leg issued back "
-                       "to back (H2D copy, kc_chi2_eval_mixed, D2H copy, alternating between "
-                       "two streams), final synchronise included"}
+                "how": "time.perf_counter around the steps of the e2e leg issued back to back "
+                       "on one stream (H2D copy, kc_chi2_eval_mixed, D2H copy), final "
+                       "synchronise included"}
 
     extras = {}
     if not args.no_extras:
@@ -880,7 +897,8 @@ def ragged_measure(kc, synth, dev, stream, flush, args, world=1, rank=0, compact
     # writes both into views of one device buffer, returned with one copy);
     # steps alternate between two streams (the plan keeps a work queue and a
     # graph per stream) so that one step's copies overlap the other's
-    # kernel; CUDA events from the first copy to the last read
+    # kernel, each kernel after the previous one; CUDA events from the first
+    # copy to the last read
     hP = torch.tensor(w.params).pin_memory()
     n_out = chi.numel() + (grad.numel() if want_grad else 0)
     pipe = [stream, torch.cuda.Stream(dev)]
@@ -891,12 +909,17 @@ def ragged_measure(kc, synth, dev, stream, flush, args, world=1, rank=0, compact
         bufs.append((dP, dout, dout[:chi.numel()], dout[chi.numel():] if want_grad else None,
                      torch.empty(n_out, dtype=chi.dtype).pin_memory()))
 
+    kernel_done = [torch.cuda.Event(), torch.cuda.Event()]
+
     def e2e_step(i):
         st = pipe[i % 2]
         dP, dout, echi, egrad, hout = bufs[i % 2]
         with torch.cuda.stream(st):
             dP.copy_(hP, non_blocking=True)
+            if i > 0:
+                st.wait_event(kernel_done[(i - 1) % 2])      # the previous step's kernel
             plan.run(dP, echi, egrad, stream=st)
+            kernel_done[i % 2].record(st)
             hout.copy_(dout, non_blocking=True)
 
     def e2e_run(n):
@@ -920,8 +943,8 @@ def ragged_measure(kc, synth, dev, stream, flush, args, world=1, rank=0, compact
     out["e2e"] = {"value": evals * args.steps / e2e_s, "unit": "planet-obs evals/s",
                   "h2d_bytes_per_step": hP.numel() * 8,
                   "d2h_bytes_per_step": n_out * chi.element_size(),
-                  "how": "steps alternating between two streams, CUDA events from the first "
-                         "copy to the last read"}
+                  "how": "steps alternating between two streams, each kernel after the "
+                         "previous one, CUDA events from the first copy to the last read"}
     del plan, bufs, hP, chi, grad
 
     if not args.no_extras or compact:
