@@ -90,15 +90,16 @@ def gn_tensor_flops_per_obs(n_pl: int) -> float:
 
 
 # FP64 path, FP64 FLOPs per planet-observation evaluation (FMA = 2), from its
-# algorithm: mean anomaly 10 (the two roundings to an integer counted as one
-# each; the low part of the phase scaled in single precision), table-driven
+# algorithm: mean anomaly 6 (tau/P minus its integer part in one FMA, the
+# offset, the removal of the nearest integer, the scaled FMA; the integer
+# parts and the low part of the phase in single precision), table-driven
 # sin/cos 20 (reduction 4, b^2 and b^3 2, sin b to b^3 2, cos b to b^4 4,
 # table combination 8; the b^5 and b^6 terms in single precision), Halley
 # step with a one-Newton-step reciprocal 13, last-step update 8, velocity
 # with a one-Newton-step reciprocal and the planet sum's addition 11 (the
 # FP32 presolve, the single-precision correction terms and reciprocal seeds
 # and the per-CTA table are not counted).
-F64_FLOPS_PER_EVAL = 10 + 20 + 13 + 8 + 11
+F64_FLOPS_PER_EVAL = 6 + 20 + 13 + 8 + 11
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of

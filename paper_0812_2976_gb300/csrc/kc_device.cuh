@@ -533,6 +533,7 @@ __device__ __forceinline__ double kepler_f64(double M, double e, double &sE, dou
 // limits round-off for small e, as Sec. 4.4 advises.
 struct PlanetD {
   double inv_P, inv_P_lo, c0, e, A, B, beta;
+  float inv_P_f, inv_P_lo_f;    // the same in single precision, for the phase's helpers
 };
 
 // Single-precision constants of one planet for the mixed path: 1/P and the
@@ -596,6 +597,8 @@ __device__ __forceinline__ PlanetD planet_setup_f64(const double *p, double dref
   recip_checked(P, n, nl);
   q.inv_P = n;
   q.inv_P_lo = nl;
+  q.inv_P_f = d2f(n);
+  q.inv_P_lo_f = d2f(nl);
   q.c0 = phase_cycles(dref, n, nl, M0 * kInvTwoPi);
   q.e = e;
   double sw, cw;
@@ -809,19 +812,22 @@ __device__ __forceinline__ float mean_anomaly_single(float tau, const PlanetF &q
   return x * kTwoPiF;
 }
 
-// p = tau/P keeps its exact FMA remainder pe; the low part
-// lo = pe + tau inv_P_lo, |lo| <= ulp(p)/2 + 2^-52 p, enters the last FMA
-// already scaled by 2 pi in single precision: below 2e-12 cycles for
-// p < 6000 (a 6000-day span at P >= 1 d), so the float error stays under
-// 1e-17 rad (5e-16 rad at p = 1e6).  p - rint(p) is exact, adding c0
-// rounds once (error below 1.2e-16 cycles) and u - rint(u) is exact, so M
-// lies in [-pi, pi] up to 2 pi |lo|.
+// The phase tau/P + c0 with four FP64 instructions (the FP64 pipe runs at
+// 1/64 of the FP32 rate): the integer part n of tau/P is taken from single
+// precision (exact as a double; it may be off by one or more, which only
+// widens the range of u), u = tau inv_P - n in one FMA (exact product and
+// difference, one rounding: error below 2^-54 |u| cycles), u + c0 rounds
+// once more, and the nearest integer of that (from its single-precision
+// value, exact as a double) is removed exactly.  The low part of 1/P,
+// tau inv_P_lo (below 1e-13 cycles for tau < 6000 d), enters the final FMA
+// scaled by 2 pi in single precision.  M lies in [-pi, pi] up to the
+// single-precision rounding of u + c0 near +-1/2 (a few 1e-7 rad).
 __device__ __forceinline__ double mean_anomaly_f64(double tau, const PlanetD &q) {
-  const double p = __dmul_rn(tau, q.inv_P);
-  const double pe = fma(tau, q.inv_P, -p);
-  const float lo2pi = __fmaf_rn(d2f(tau), d2f(q.inv_P_lo), d2f(pe)) * kTwoPiF;
-  double u = (p - rint(p)) + q.c0;
-  u -= rint(u);
+  const float tf = d2f(tau);
+  const double n = f2d(rintf(tf * q.inv_P_f));
+  double u = fma(tau, q.inv_P, -n) + q.c0;
+  u -= f2d(rintf(d2f(u)));
+  const float lo2pi = (tf * q.inv_P_lo_f) * kTwoPiF;
   return fma(u, kTwoPi, f2d(lo2pi));
 }
 
