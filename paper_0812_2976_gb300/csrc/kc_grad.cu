@@ -786,8 +786,9 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// Writes one row of U^T (the lane's observation in K-half `half`) as TF32
-// (hi, lo) pairs: element (row 16 warp + p, column c) of a half sits in
+// Writes the lane's observation, one column of U^T, into the K-half that
+// `rows` points into, as TF32 (hi, lo) pairs: element (row 16 warp + p,
+// column c) of a half sits in
 // 8-row group 2 warp + p / 8 (1024 bytes each), row p % 8 (128 bytes),
 // 16-byte chunk (c / 4) ^ (p % 8), word c % 4.
 template <int NP>

@@ -48,22 +48,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// As mbar_try_wait, but the thread may sleep up to hint_ns (or until the
-// phase completes) before the answer is false: fewer polls for a thread
-// with nothing else to do.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity,
-                                                    uint32_t hint_ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(hint_ns)
-      : "memory");
-  return ok != 0;
-}
-
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -72,13 +56,10 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 // Waits for the phase with the given parity to complete, for at most
 // limit_ns nanoseconds of the GPU's global timer; false if it gave up.
-// sleep_ns > 0: each poll may sleep that long (a waiting thread that only
-// issues MMAs).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns,
-                                          uint32_t sleep_ns = 0) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t start = globaltimer_ns();
-  while (!(sleep_ns ? mbar_try_wait_sleep(bar, parity, sleep_ns) : mbar_try_wait(bar, parity)))
+  while (!mbar_try_wait(bar, parity))
     if (globaltimer_ns() - start > limit_ns) return false;
   return true;
 }
