@@ -643,13 +643,35 @@ def run_kc(args):
     t0e, t1e = e2e_run(args.steps)
     torch.cuda.synchronize(dev)
     e2e_s = t0e.elapsed_time(t1e) / 1e3
+    if world > 1:
+        from paper_0812_2976_gb300 import dist as kdist
+        e2e_s = kdist.max_over_ranks(e2e_s, device=dev)
     h2d = hbuf.numel() * 8
     d2h = w.n_sys * 4
     e2e = {"value": evals * args.steps * world / e2e_s, "unit": "planet-obs evals/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "steps alternating between two streams (copies of one overlap the other's "
                   "kernel; each kernel after the previous one), CUDA events from the first "
-                  "copy to the last read, no L2 flush"}
+                  "copy to the last read, no L2 flush (each step's inputs reach its kernel "
+                  "through L2 from its own copy)"}
+
+    # the same steps fully serialised on one stream, each between its own
+    # CUDA events with L2 flushed before it (the device-resident value's
+    # timing with the copies added)
+    def serial_step():
+        dbuf0, (dP0, dT0, dV0, dS0), dout0, hout0 = bufs[0]
+        dbuf0.copy_(hbuf, non_blocking=True)
+        kc.kc_chi2_eval_mixed(dP0, dT0, dV0, dS0, out=dout0, stream=stream)
+        hout0.copy_(dout0, non_blocking=True)
+
+    serial_s = time_steps(serial_step, args.steps, stream, flush)
+    if world > 1:
+        from paper_0812_2976_gb300 import dist as kdist
+        serial_s = kdist.max_over_ranks(serial_s, device=dev)
+    e2e["serialised"] = {"value": evals * args.steps * world / serial_s,
+                         "ms_per_step": 1e3 * serial_s / args.steps,
+                         "how": "each step's copy in, kernel and copy out on one stream between "
+                                "its own CUDA events, L2 flushed before every step"}
 
     # the same steps on the host's clock: back-to-back calls through the
     # binding and the C ABI (ctypes, argument checks, launch) with their
