@@ -209,6 +209,13 @@ TileKey key_of(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
 
 }  // namespace
 
+// The tile used without a table entry.
+Tile builtin_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
+  if (kind == Kind::Chi2Mixed) return warp_tile(n_sys, n_pl, n_obs);
+  if (kind == Kind::GnMixed) return Tile{32, 128, 0, gn_default_variant(n_pl)};
+  return default_tile(kind, n_sys, n_pl, n_obs);
+}
+
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
@@ -219,9 +226,7 @@ Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
       return t;
     }
   }
-  if (kind == Kind::Chi2Mixed) return warp_tile(n_sys, n_pl, n_obs);
-  if (kind == Kind::GnMixed) return Tile{32, 128, 0, gn_default_variant(n_pl)};
-  return default_tile(kind, n_sys, n_pl, n_obs);
+  return builtin_tile(kind, n_sys, n_pl, n_obs);
 }
 
 }  // namespace kc
@@ -658,8 +663,13 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
     return cudaErrorInvalidValue;
   };
   float best_t = 1e30f;
-  Tile best_tile = kernel == KC_KERNEL_GN ? Tile{32, 128, 0, 0}
-                                          : kc::default_tile(kind, n_sys, n_pl, n_obs);
+  Tile best_tile = kc::builtin_tile(kind, n_sys, n_pl, n_obs);
+  best_tile.obs_tile = kc::obs_tile_for(kind, n_obs);
+  // the built-in tile is kept unless a candidate beats it by 1 % (shapes
+  // within timing noise of each other would otherwise trade places from
+  // one run to the next)
+  float builtin_t = 1e30f;
+  const Tile builtin = best_tile;
   const char *env = getenv("KC_AUTOTUNE_VERBOSE");     // candidate timings to stderr
   const bool verbose = env && env[0] == '1';
   cudaError_t err = cudaSuccess;
@@ -715,10 +725,16 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
     if (verbose)
       fprintf(stderr, "kc_autotune: kind %d n_sys %lld G %3d block %3d split %d: %9.2f us\n",
               (int)kind, (long long)n_sys, G, B, split, 1e3 * tmin);
+    if (tile.G == builtin.G && tile.block == builtin.block && tile.split == builtin.split)
+      builtin_t = tmin;
     if (tmin < best_t) {
       best_t = tmin;
       best_tile = tile;
     }
+  }
+  if (builtin_t < 1e30f && best_t > 0.99f * builtin_t) {
+    best_t = builtin_t;
+    best_tile = builtin;
   }
   cudaFreeAsync(chi, s);
   if (grad) cudaFreeAsync(grad, s);

@@ -179,6 +179,7 @@ size_t smem_grad(int n_pl, const Tile &tile, bool f64);
 // Launch shape for a problem (kc_api.cu): the tuned table, else a heuristic.
 enum class Kind { Chi2F64 = 0, Chi2Mixed = 1, GradF64 = 2, GradMixed = 3, GnMixed = 4 };
 Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
+Tile builtin_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);  // without a table entry
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 int obs_tile_for(Kind kind, int n_obs);
 
