@@ -742,11 +742,17 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
 // entry), so the CTA's four warps write their systems' U^T rows into one
 // 64-row tile (rows 16 w .. 16 w + 15 for warp w; TF32 (hi, lo) pairs as in
 // gn_mixed_kernel, in two tiles, K-major, 128-byte swizzle), and thread 0
-// issues D += U^T_tile U_tile (M = 64, N = 64, three MMAs per K = 8 step:
-// lo hi, hi lo, hi hi); the four diagonal 16 x 16 blocks are kept and 3/4
-// of the products are cross-system terms that are thrown away.  A batch is
-// 64 observations, two per lane, evaluated side by side (two independent
-// chains per planet for the scheduler); its tile is two 64 x 32 halves.
+// issues the batch's MMAs (M = 64, N = 64, K = 8 per step).  H = U^T U is
+// symmetric, so of the three products of the split, hi hi^T + lo hi^T +
+// hi lo^T, the last is the transpose of the second: two accumulators in
+// TMEM, D1 += hi hi^T and D2 += lo hi^T (two MMAs per K step, not three),
+// give H = D1 + D2 + D2^T in the epilogue.  The four diagonal 16 x 16
+// blocks are kept; 3/4 of the products are cross-system terms that are
+// thrown away.  A batch is 64 observations, two per lane, evaluated side by
+// side (two independent chains per planet for the scheduler); its tile is
+// two 64 x 32 halves.  The order of the observations along K is free (the
+// sum runs over all of them), so lane l puts its pair at K = 2l and 2l + 1
+// and writes both words of an element with one 8-byte store.
 // One tile suffices: a warp rewrites it only after evaluating the next 64
 // observations, by which time the MMAs that read it have long completed
 // (its lane 0 still waits on the mbarrier their commit arrives on).  A CTA
@@ -754,15 +760,16 @@ gn_mixed_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restrict__
 // GB300 this ran 822 us on 65536 x 3 x 512 against 891 us with a "full"
 // mbarrier that let the other warps run a batch ahead of warp 0).  With
 // M = 64 the accumulator's row r sits in TMEM lane 32 (r / 16) + r % 16, so
-// warp w reads its system's block from its own lanes 32 w .. 32 w + 15,
-// columns 16 w .. 16 w + 15.  Every wait is bounded; a wait that gives up
-// makes the CTA's results NaN (counted by the invalid-system counter) and
-// the TMEM is still freed.
+// warp w reads its system's blocks from its own lanes 32 w .. 32 w + 15,
+// columns 16 w .. 16 w + 15 (D1) and 64 + 16 w .. 64 + 16 w + 15 (D2), and
+// transposes D2's block through shared memory.  Every wait is bounded; a
+// wait that gives up makes the CTA's results NaN (counted by the
+// invalid-system counter) and the TMEM is still freed.
 
 constexpr int kTcHalfBytes = 64 * 32 * 4;       // 64 rows x 32 observations, TF32
 constexpr int kTcBatch = 64;                    // observations per batch
 constexpr int kTcObsTile = 512;                 // observations staged at a time
-constexpr int kTcCols = 64;                     // TMEM columns per CTA
+constexpr int kTcCols = 128;                    // TMEM columns per CTA: D1, D2
 constexpr uint64_t kTcWaitLimit = 20000000;     // ns an mbarrier wait may take (20 ms)
 
 struct GnTcLayout {
@@ -786,20 +793,28 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-// Writes the lane's observation, one column of U^T, into the K-half that
-// `rows` points into, as TF32 (hi, lo) pairs: element (row 16 warp + p,
-// column c) of a half sits in
-// 8-row group 2 warp + p / 8 (1024 bytes each), row p % 8 (128 bytes),
-// 16-byte chunk (c / 4) ^ (p % 8), word c % 4.
+// Writes the lane's two observations, columns 2 l and 2 l + 1 of U^T for
+// lane l, into the tile: element (row 16 warp + p, column c) of a half
+// (columns 0-31 and 32-63 of the batch) sits in 8-row group 2 warp + p / 8
+// (1024 bytes each), row p % 8 (128 bytes), 16-byte chunk (c / 4) ^ (p % 8),
+// word c % 4, so the pair is one aligned 8-byte word.  `rows` points at the
+// lane's half, 8-row group and word; `lane_q` is its chunk before the
+// swizzle.  The hi parts are TF32 (low 13 bits cleared), so that hi + lo is
+// exact; the lo parts are stored whole: the tensor core takes their upper
+// 19 bits, as clearing the rest here would (were it to round them instead,
+// an element would move by less than 2^-20 of itself).
 template <int NP>
 __device__ __forceinline__ void gn_tc_store(unsigned char *rows, uint32_t lane_q,
-                                            const float (&urow)[NP]) {
+                                            const float (&ua)[NP], const float (&ub)[NP]) {
+  constexpr unsigned kTf32Mask = 0xffffe000u;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const float2 pr = tf32_pair(urow[p]);
+    const float ha = __uint_as_float(__float_as_uint(ua[p]) & kTf32Mask);
+    const float hb = __uint_as_float(__float_as_uint(ub[p]) & kTf32Mask);
     const uint32_t off = (p >> 3) * 1024 + (p & 7) * 128 + ((lane_q ^ (p & 7)) << 4);
-    *reinterpret_cast<float *>(rows + off) = pr.x;
-    *reinterpret_cast<float *>(rows + 2 * kTcHalfBytes + off) = pr.y;
+    *reinterpret_cast<float2 *>(rows + off) = make_float2(ha, hb);
+    *reinterpret_cast<float2 *>(rows + 2 * kTcHalfBytes + off) =
+        make_float2(__fsub_rn(ua[p], ha), __fsub_rn(ub[p], hb));
   }
 }
 
@@ -857,8 +872,13 @@ gn_mixed_tc_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restric
 #pragma unroll
   for (int j = 0; j < J; ++j) qr[j] = pl_s[warp * J + j];
   const float gam = gam_s[warp];
-  const uint32_t lane_q = (uint32_t)lane >> 2;
-  unsigned char *my_rows = tiles + 2048 * warp + 4 * (lane & 3);
+  // lane l: columns 2 l, 2 l + 1 of the batch, in half l / 16
+  const uint32_t lane_q = (uint32_t)(lane & 15) >> 1;
+  unsigned char *my_rows = tiles + (lane >> 4) * kTcHalfBytes + 2048 * warp + 8 * (lane & 1);
+  // The descriptors of the batch's K steps differ from the tile's in the
+  // start address alone (bits 0-13: the address / 16; the tiles end below
+  // 2^18 bytes, so an offset adds without a carry out of the field).
+  const uint64_t dtile = tc::desc_kmajor_sw128(tiles_a);
   Kahan acc = {0.0f, 0.0f};
   Kahan gP[J];
   float g[NP];
@@ -892,21 +912,19 @@ gn_mixed_tc_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restric
       gn_obs<J>(obs_s[ib], wt_s[ib], kbb < nk, gam, qr, acc, gP, g, ub);
       if (nb > 0 && ok)                  // the MMAs that read the tile before
         ok = warp_wait(bar_a, (nb - 1) & 1u, kTcWaitLimit, lane);
-      gn_tc_store<NP>(my_rows, lane_q, ua);
-      gn_tc_store<NP>(my_rows + kTcHalfBytes, lane_q, ub);
+      gn_tc_store<NP>(my_rows, lane_q, ua, ub);
       tc::fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after_sync();
 #pragma unroll
         for (int ks = 0; ks < 8; ++ks) {
-          // K step ks: observations 8 ks .. 8 ks + 7 of the batch, in half ks / 4
-          const uint32_t hi = tiles_a + (ks >> 2) * kTcHalfBytes + 32u * (ks & 3);
-          const uint32_t lo = hi + 2 * kTcHalfBytes;
-          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(lo), tc::desc_kmajor_sw128(hi), IDESC,
-                       (nb | ks) != 0);
-          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(hi), tc::desc_kmajor_sw128(lo), IDESC, 1u);
-          tc::mma_tf32(taddr, tc::desc_kmajor_sw128(hi), tc::desc_kmajor_sw128(hi), IDESC, 1u);
+          // K step ks: columns 8 ks .. 8 ks + 7 of the batch, in half ks / 4
+          const uint32_t off = ((ks >> 2) * kTcHalfBytes + 32 * (ks & 3)) >> 4;
+          const uint64_t hi = dtile + off, lo = dtile + off + (2 * kTcHalfBytes >> 4);
+          const uint32_t accumulate = (nb | ks) != 0;
+          tc::mma_tf32(taddr, hi, hi, IDESC, accumulate);                 // D1 += hi hi^T
+          tc::mma_tf32(taddr + kTcCols / 2, lo, hi, IDESC, accumulate);   // D2 += lo hi^T
         }
         tc::commit(bar_a);
       }
@@ -922,7 +940,24 @@ gn_mixed_tc_kernel(UniformArgs a, float *__restrict__ chi2_out, float *__restric
                                    lane);
     ok = ok && last_ok;
     tc::fence_after_sync();
-    tc::tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + 16u * warp, h);
+    const uint32_t blk = taddr + ((uint32_t)(32 * warp) << 16) + 16u * warp;
+    float h2[16];
+    tc::tmem_ld16(blk, h);
+    tc::tmem_ld16(blk + kTcCols / 2, h2);
+    // H = D1 + D2 + D2^T: lane r < 16 holds row r of both blocks; D2's is
+    // transposed through 16 x 17 floats of the warp's own in the staged
+    // observations' shared memory (read by no warp after the last batch's
+    // barrier).
+    float *tr = reinterpret_cast<float *>(obs_s) + warp * 16 * 17;
+    if (lane < 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) tr[lane * 17 + i] = h2[i];
+    }
+    __syncwarp();
+    if (lane < 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) h[i] += h2[i] + tr[i * 17 + lane];
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < 16; ++i) h[i] = 0.0f;
