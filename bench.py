@@ -80,9 +80,13 @@ def gn_flops_per_eval(n_pl: int) -> float:
     return grad_flops_per_eval(n_pl) + 5 + 1.0 / n_pl
 
 
-def gn_tensor_flops_per_obs(n_pl: int) -> float:
-    """Tensor FLOPs per observation of the U^T U update as issued: 16 x 8 x 8
-    tiles on or above the diagonal, three TF32 products each, 2 FLOP/MAC."""
+def gn_tensor_flops_per_obs(n_pl: int, split: int) -> float:
+    """Tensor FLOPs per (system, observation) of the U^T U update as issued
+    (2 FLOP/MAC).  split 0 (mma.sync): 16 x 8 x 8 tiles on or above the
+    diagonal, three TF32 products each.  split 4 (tcgen05): M = N = 64 tiles
+    shared by four systems, two TF32 products (hi hi^T, lo hi^T)."""
+    if split == 4:
+        return 2 * 64 * 64 * 2 / 4
     n = 5 * n_pl + 1
     mt, nt = (n + 15) // 16, (n + 7) // 8
     tiles = sum(1 for m in range(mt) for q in range(nt) if 8 * q + 7 >= 16 * m)
@@ -270,8 +274,8 @@ def gradient_throughput(kc, synth, dev, stream, args):
         "nll_grad_frac": out["nll_grad"] * grad_flops_per_eval(w.n_pl) / 1e12 / peak,
         "gauss_newton_frac": out["gauss_newton"] * gn_flops_per_eval(w.n_pl) / 1e12 / peak,
         "flops_per_eval": {"grad": grad_flops_per_eval(w.n_pl), "gauss_newton": gn_flops_per_eval(w.n_pl)},
-        "gauss_newton_tensor_tflops": out["gauss_newton"] / w.n_pl
-                                      * gn_tensor_flops_per_obs(w.n_pl) / 1e12}
+        "gauss_newton_tensor_tflops": out["gauss_newton"] / w.n_pl * gn_tensor_flops_per_obs(
+            w.n_pl, kc.kc_get_tile("gn", "mixed", w.n_sys, w.n_pl, w.n_obs)[2]) / 1e12}
     # the two ways of adding U^T U, side by side
     out["gauss_newton_variants"] = {
         name: out.pop(f"gauss_newton_split{split}")

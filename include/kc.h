@@ -348,8 +348,8 @@ typedef struct kc_tile {
  * (threads_per_system = 32, block = 128); split chooses how it adds U^T U:
  * 0 = warp-level mma.sync (TF32), 32 observations per batch; 4 = tcgen05
  * MMAs for the CTA's four systems stacked in one M = 64, N = 64 tile (one
- * issuing thread, accumulator in 64 TMEM columns per CTA), 64 observations
- * per batch, n_pl <= 3 only.  Without a tuned entry split 4 is used for
+ * issuing thread, two accumulators in 128 TMEM columns per CTA), 64
+ * observations per batch, n_pl <= 3 only.  Without a tuned entry split 4 is used for
  * n_pl <= 3 and split 0 above. */
 typedef enum kc_kernel {
     KC_KERNEL_CHI2 = 0,
