@@ -32,8 +32,8 @@
 //    (griddepcontrol.launch_dependents), so that a following batch's CTAs
 //    are placed on the SMs as this grid's CTAs exit instead of after the
 //    whole grid has completed (back-to-back 4096 x 4 x 256 batches: 14.0 us
-//    each instead of 16.4 us).  The launch asks for it only outside stream
-//    capture.
+//    each instead of 16.4 us).  Under stream capture the launch becomes a
+//    graph node with a programmatic edge from the kernel node before it.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -435,9 +435,7 @@ cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float
   int lg = log2_lanes(G), tl = obs_tile, nt = (a.n_obs + obs_tile - 1) / obs_tile;
   void *params[] = {&args, &lg, &tl, &nt, &out, &resid};
   // programmatic stream serialisation (the kernel's griddepcontrol.wait
-  // keeps it ordered after the grids before it), not under stream capture
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cudaGetLastError();
+  // keeps it ordered after the grids before it)
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -447,7 +445,7 @@ cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  cfg.numAttrs = 1;
   return cudaLaunchKernelExC(&cfg, fn, params);
 }
 
