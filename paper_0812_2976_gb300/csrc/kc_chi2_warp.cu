@@ -32,8 +32,11 @@
 //    (griddepcontrol.launch_dependents), so that a following batch's CTAs
 //    are placed on the SMs as this grid's CTAs exit instead of after the
 //    whole grid has completed (back-to-back 4096 x 4 x 256 batches: 14.0 us
-//    each instead of 16.4 us).  Under stream capture the launch becomes a
-//    graph node with a programmatic edge from the kernel node before it.
+//    each instead of 16.4 us).  The launch asks for it only outside stream
+//    capture: as programmatic edges in the DE-MC driver's graph (4096
+//    chains, halves of 2048) it cost a quarter of the generations per
+//    second (2.36e4 against 3.12e4), where back-to-back launches of 1024 to
+//    4096 systems gained 2.7-2.9 us each.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -292,7 +295,7 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
     note_invalid(a.invalid, value);
     if (RESID) resid_out[s] = rmax;
     // the proposals this CTA formed are visible here after the barrier
-    if (DEMC) demc_accept(a, s, 5 * J + 1, value);
+    if (DEMC) demc_accept<5 * J + 1>(a, s, value);
   }
 }
 
@@ -435,7 +438,9 @@ cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float
   int lg = log2_lanes(G), tl = obs_tile, nt = (a.n_obs + obs_tile - 1) / obs_tile;
   void *params[] = {&args, &lg, &tl, &nt, &out, &resid};
   // programmatic stream serialisation (the kernel's griddepcontrol.wait
-  // keeps it ordered after the grids before it)
+  // keeps it ordered after the grids before it), not under stream capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return cudaGetLastError();
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -445,7 +450,7 @@ cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
   return cudaLaunchKernelExC(&cfg, fn, params);
 }
 

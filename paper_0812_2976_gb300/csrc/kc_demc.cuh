@@ -13,16 +13,31 @@ namespace kc {
 
 // The Metropolis decision of DE-MC in the epilogue of the chi2 kernel that
 // has just evaluated proposal s (demcmc_accept_kernel's rule and
-// arithmetic, applied to the value the kernel stores).
-template <typename T>
-__device__ __forceinline__ void demc_accept(const UniformArgs &a, int64_t s, int npar, T value) {
+// arithmetic, applied to the value the kernel stores).  NPAR parameters per
+// chain.  An accepted proposal is copied in chunks whose loads are all
+// issued before their stores: the states and the proposals may alias as far
+// as the compiler knows, so a plain loop would hold every load back until
+// the one before it had returned (NPAR dependent memory round trips at the
+// end of the CTA's work).
+template <int NPAR, typename T>
+__device__ __forceinline__ void demc_accept(const UniformArgs &a, int64_t s, T value) {
+  constexpr int kCopy = 8;
   const DemcAccept &d = a.demc;
   const int64_t i = d.first + s;
   T *chi2 = static_cast<T *>(d.chi2);
   const double delta = (double)value - (double)chi2[i];
   const bool acc = log(d.u[3 * s]) < -0.5 * delta;      // false when delta is NaN
   if (acc) {
-    for (int p = 0; p < npar; ++p) d.states[i * npar + p] = a.params[s * npar + p];
+#pragma unroll
+    for (int p0 = 0; p0 < NPAR; p0 += kCopy) {
+      double x[kCopy];
+#pragma unroll
+      for (int k = 0; k < kCopy; ++k)
+        if (p0 + k < NPAR) x[k] = a.params[s * NPAR + p0 + k];
+#pragma unroll
+      for (int k = 0; k < kCopy; ++k)
+        if (p0 + k < NPAR) d.states[i * NPAR + p0 + k] = x[k];
+    }
     chi2[i] = value;
   }
   if (d.accepted) d.accepted[s] = acc ? 1 : 0;
@@ -39,11 +54,14 @@ __device__ __forceinline__ void demc_form(const UniformArgs &a, int64_t s, int p
   demc_partners(d.u[3 * s + 1], d.u[3 * s + 2], d.partner_first, d.partner_count, r1, r2);
   double *prop = const_cast<double *>(a.params) + s * npar;
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
+  for (int k = 0; k < N; ++k)
     out[k] = demc_proposal(d.states, npar, d.first + s, r1, r2, p0 + k, d.gamma,
                            d.eps_scale[p0 + k], d.z[s * npar + p0 + k]);
-    prop[p0 + k] = out[k];
-  }
+  // stored after every load (a store between them would hold the next
+  // parameter's loads back until the previous ones had returned: the
+  // proposals may alias the states as far as the compiler knows)
+#pragma unroll
+  for (int k = 0; k < N; ++k) prop[p0 + k] = out[k];
 }
 
 }  // namespace kc

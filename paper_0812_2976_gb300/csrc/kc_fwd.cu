@@ -337,7 +337,7 @@ chi2_mixed_kernel(UniformArgs a, MixedPrep prep, int G, int obs_tile, float *__r
     out[s] = value;
     note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = rmax;
-    if (DEMC) demc_accept(a, s, npar, value);
+    if (DEMC) demc_accept<5 * J + 1 + (NLL ? 1 : 0)>(a, s, value);
   }
 }
 
@@ -579,7 +579,7 @@ chi2_f64_kernel(UniformArgs a, int G, int obs_tile, double *__restrict__ out,
     out[s] = value;
     note_invalid(a.invalid, value);
     if (resid_out) resid_out[s] = (float)rmax;
-    if (DEMC) demc_accept(a, s, 5 * J + 1, value);
+    if (DEMC) demc_accept<5 * J + 1 + (NLL ? 1 : 0)>(a, s, value);
   }
 }
 
