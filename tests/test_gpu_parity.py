@@ -119,6 +119,36 @@ def test_config1_in_the_benchmarked_launch(kc, oracle_mod):
         kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, None)
 
 
+def test_back_to_back_launches_see_the_writes_before_them(kc, oracle_mod):
+    """Launches queued back to back on one stream behind a GPU spin (the
+    headline kernel waits for the grids before it, then lets the next launch
+    start placing its CTAs): before every launch a torch kernel rewrites the
+    parameters in place, and each launch's chi2, read after one synchronise
+    at the end, matches the oracle on the parameters written just before it."""
+    from paper_0812_2976_gb300 import synth
+    w = synth.uniform(1, n_sys=512)
+    v = observed(oracle_mod, w)
+    P, T, V, S = dev(w.params, w.t, v, w.sigma)
+    batches = []
+    for scale in (1.0, 1.01, 0.97, 1.05, 0.9):
+        p = w.params.copy()
+        p[:, 1:5 * w.n_pl:5] *= scale                     # every planet's K
+        batches.append(p)
+    staged = [torch.tensor(p, device="cuda") for p in batches]
+    outs = [torch.empty(w.n_sys, dtype=torch.float32, device="cuda") for _ in batches]
+    torch.cuda.synchronize()
+    sleep = getattr(torch.cuda, "_sleep", None)
+    if sleep is not None:
+        sleep(4_000_000)                # the GPU starts once every launch is queued
+    for src, out in zip(staged, outs):
+        torch.mul(src, 1.0, out=P)      # a kernel, not a copy-engine transfer
+        kc.kc_chi2_eval_mixed(P, T, V, S, out=out)
+    torch.cuda.synchronize()
+    for p, out in zip(batches, outs):
+        ref = oracle_mod.chi2(p, w.t, v, w.sigma, w.n_pl)
+        assert rel_err(out.cpu().numpy(), ref).max() <= MIXED_TOL
+
+
 # ------------------------------------------------------------ config 2
 
 def test_config2_grid_sweep_full_size_sampled(kc, oracle_mod):
