@@ -598,6 +598,8 @@ def run_kc(args):
         step(i)
     t1e.record(stream)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
     # the same K steps, each between its own events after an L2 flush
     hold_gpu(stream, args.steps * 300.0)
     for i in range(args.steps):
