@@ -332,11 +332,14 @@ void kc_plan_destroy(kc_plan *plan);
  * being captured into a CUDA graph the split variants are replaced by the
  * fused kernel (no allocation inside a graph).
  * split = 3 (mixed chi2 only): the warp-per-system kernel,
- * threads_per_system = 8, 16 or 32 lanes per system, block a multiple of 32
- * up to 1024; one CTA per block * threads_per_system / 32 systems.
- * Allocates nothing, so it also runs under stream capture.  With no tuned
- * entry the mixed chi2 (and the mixed DE-MC step) uses this variant with
- * the block that spreads the CTAs most evenly over the SMs. */
+ * threads_per_system = 8, 16, 32, 64 or 128 lanes per system (64 and 128:
+ * the system's observations split over two or four warps, whose sums are
+ * combined through shared memory), block a multiple of 32 and of
+ * threads_per_system, up to 1024; one CTA per block / threads_per_system
+ * systems.  Allocates nothing, so it also runs under stream capture.  With
+ * no tuned entry the mixed chi2 (and the mixed DE-MC step) uses this
+ * variant with the lanes per system and block that spread the work most
+ * evenly over the SMs. */
 typedef struct kc_tile {
     int32_t threads_per_system;
     int32_t block;

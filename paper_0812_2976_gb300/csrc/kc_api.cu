@@ -216,6 +216,11 @@ Tile builtin_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
   return default_tile(kind, n_sys, n_pl, n_obs);
 }
 
+bool has_tile_entry(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  return g_tiles.count(key_of(kind, n_sys, n_pl, n_obs)) != 0;
+}
+
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
@@ -502,7 +507,11 @@ kc_status kc_demcmc_step(double *states, void *chi2, int64_t n_chains, int32_t n
     const Tile tile = kc::choose_tile(Kind::Chi2F64, count, n_pl, n_obs);
     e = kc::launch_chi2_f64(a, tile, static_cast<double *>(chi2_prop), nullptr, s);
   } else {
-    const Tile tile = kc::choose_tile(Kind::Chi2Mixed, count, n_pl, n_obs);
+    // a tuned or pinned tile if there is one, else the built-in warp tile
+    // with one warp (or less) per system
+    Tile tile = kc::choose_tile(Kind::Chi2Mixed, count, n_pl, n_obs);
+    if (!kc::has_tile_entry(Kind::Chi2Mixed, count, n_pl, n_obs))
+      tile = kc::warp_tile(count, n_pl, n_obs, false);
     e = kc::launch_chi2_mixed(a, tile, static_cast<float *>(chi2_prop), nullptr, s);
   }
   return cuda_status(e, "kc_demcmc_step");
@@ -694,16 +703,17 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
         for (int G : {8, 16, 32}) cands.push_back(kc_tile{G, B, split});
     }
   }
-  // the warp-per-system kernel: 8, 16 or 32 lanes per system, 4..32 warps
-  // per CTA
-  for (int G : {8, 16, 32})
-    for (int W = 4; W <= 32 && kernel == KC_KERNEL_CHI2; ++W) cands.push_back(kc_tile{G, 32 * W, 3});
+  // the warp-per-system kernel: 8 to 128 lanes per system (a system over
+  // two or four warps at 64 and 128), 4..32 warps per CTA
+  for (int G : {8, 16, 32, 64, 128})
+    for (int W = 4; W <= 32 && kernel == KC_KERNEL_CHI2; ++W)
+      if ((32 * W) % G == 0) cands.push_back(kc_tile{G, 32 * W, 3});
   for (const kc_tile &cand : cands) {
     const int G = cand.threads_per_system, B = cand.block, split = cand.split;
     if (!tile_ok(kernel, mode, cand)) continue;
     if (n_obs > 0 && G > n_obs && split != 3 && kernel != KC_KERNEL_GN) continue;
     if (split == 2 && G / 32 > (n_obs + 31) / 32) continue;   // chunks of >= 32 obs
-    if (split == 3 && G > kc::warp_lanes_for(n_obs)) continue;  // >= 4 obs per lane
+    if (split == 3 && !kc::warp_lanes_fit(G, n_obs)) continue;  // >= 4 obs per lane
     Tile tile{G, B, kc::obs_tile_for(kind, n_obs), split};
     err = launch(tile);                       // warm-up (and smem attribute)
     if (err == cudaErrorInvalidConfiguration && split >= 3) {

@@ -1,6 +1,7 @@
 // kc_chi2_warp.cu -- the mixed-precision chi-square of a uniform batch with
-// G = 8, 16 or 32 lanes per system (one warp per system at G = 32), sized
-// by the host so that the CTAs spread evenly over the SMs.
+// G = 8, 16, 32, 64 or 128 lanes per system (one warp per system at G = 32,
+// two or four at 64 and 128), sized by the host so that the CTAs spread
+// evenly over the SMs.
 //
 // Same arithmetic as the fused kernel of kc_fwd.cu (double-single phase,
 // Sec. 5; Kepler's equation in single precision, Sec. 4.3; Eq. 3 velocity;
@@ -25,7 +26,10 @@
 //    shared memory once per chunk, and the chunk's kChunk Kepler solves are
 //    independent chains for the scheduler to interleave.
 //  - The lanes of a system combine their compensated sums with TwoSum
-//    shuffles; no shared-memory reduction, no atomics, no scratch memory.
+//    shuffles, and the warps of a system (G > 32) through a few words of
+//    shared memory; no atomics, no scratch memory.  Splitting a system over
+//    several warps keeps the SMs' warp slots filled when the batch is small
+//    (2048 systems: 28 warps per SM instead of 14).
 //  - Programmatic dependent launch: the kernel waits for the grids before
 //    it in the stream to complete (griddepcontrol.wait, ahead of its first
 //    global access) and at once lets the next launch on the stream begin
@@ -66,13 +70,14 @@ struct PlanetW {
 };
 
 struct WarpLayout {
-  size_t pl, gam, obs, w, total;
-  __host__ __device__ WarpLayout(int spr, int J, int tile) {
+  size_t pl, gam, obs, w, red, total;
+  __host__ __device__ WarpLayout(int spr, int J, int tile, int nwarps) {
     pl = 0;
     gam = pl + sizeof(PlanetW) * spr * J;
     obs = align16(gam + sizeof(float) * spr);
     w = obs + sizeof(float4) * tile;
-    total = align16(w + sizeof(float) * tile);
+    red = align16(w + sizeof(float) * tile);      // G > 32: 3 words per warp
+    total = align16(red + sizeof(float) * 3 * nwarps);
   }
 };
 
@@ -157,8 +162,8 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
   const int block = blockDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = 1 << lg;
-  const int spr = (block >> 5) << (5 - lg);      // systems of this CTA
-  const WarpLayout L(spr, J, tile);
+  const int spr = block >> lg;                   // systems of this CTA
+  const WarpLayout L(spr, J, tile, block >> 5);
   PlanetW *pl_s = reinterpret_cast<PlanetW *>(smem + L.pl);
   float *gam_s = reinterpret_cast<float *>(smem + L.gam);
   float4 *obs_s = reinterpret_cast<float4 *>(smem + L.obs);
@@ -217,9 +222,9 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
   __syncthreads();
 
   // ---- the CTA's systems, one per G lanes ----
-  int slot = (warp << (5 - lg)) + (lane >> lg);
+  int slot = tid >> lg;
   if (!dbg_ok(a.invalid, slot < spr, kDbgSmem, slot)) slot = 0;
-  const int c = lane & (G - 1);
+  const int c = tid & (G - 1);                   // the thread's place in its system
   const int64_t s = sys0 + slot;
   const PlanetW *q = pl_s + slot * J;
   const float gam = gam_s[slot];
@@ -283,11 +288,30 @@ chi2_mixed_warp_kernel(UniformArgs a, int lg, int tile, int ntiles, float *__res
     }
   }
 
-  // combine the G lanes of the system (G a power of two within the warp)
-  for (int m = G >> 1; m >= 1; m >>= 1) {
+  // combine the system's lanes within each of its warps (G a power of two)
+  for (int m = (G < 32 ? G : 32) >> 1; m >= 1; m >>= 1) {
     Kahan o = {shfl_xor(acc.big, m), shfl_xor(acc.small, m)};
     kahan_merge(acc, o);
     if (RESID) rmax = fmaxf(rmax, shfl_xor(rmax, m));
+  }
+  if (G > 32) {
+    // then its G / 32 warps, in warp order, through shared memory (lg is
+    // the same for the whole CTA, so every thread reaches the barrier)
+    float *red_s = reinterpret_cast<float *>(smem + L.red);
+    if (lane == 0) {
+      red_s[3 * warp] = acc.big;
+      red_s[3 * warp + 1] = acc.small;
+      red_s[3 * warp + 2] = rmax;
+    }
+    __syncthreads();
+    if (c == 0) {
+      for (int w = warp + 1; w < warp + (G >> 5); ++w) {
+        if (!dbg_ok(a.invalid, w < (block >> 5), kDbgSmem, w)) break;
+        const Kahan o = {red_s[3 * w], red_s[3 * w + 1]};
+        kahan_merge(acc, o);
+        rmax = fmaxf(rmax, red_s[3 * w + 2]);
+      }
+    }
   }
   if (c == 0 && s < a.n_sys) {
     const float value = kahan_value(acc) + poison;   // NaN survives n_obs == 0
@@ -360,15 +384,20 @@ int blocks_per_sm(int J, int variant, int block, size_t smem) {
 }
 
 size_t warp_smem(int J, int G, int block, int n_obs) {
-  return WarpLayout((block / 32) * (32 / G), J, warp_obs_tile(n_obs, G)).total;
+  return WarpLayout(block / G, J, warp_obs_tile(n_obs, G), block / 32).total;
 }
 
-int log2_lanes(int G) { return G == 8 ? 3 : (G == 16 ? 4 : 5); }
+int log2_lanes(int G) {
+  int lg = 3;
+  while ((8 << (lg - 3)) < G) ++lg;
+  return lg;
+}
 
 }  // namespace
 
 bool warp_tile_ok(int G, int block) {
-  return (G == 8 || G == 16 || G == 32) && block >= 32 && block <= 1024 && !(block & 31);
+  const bool lanes = G == 8 || G == 16 || G == 32 || G == 64 || G == 128;
+  return lanes && block >= 32 && block <= 1024 && !(block & 31) && block % G == 0;
 }
 
 int warp_lanes_for(int n_obs) {
@@ -377,45 +406,64 @@ int warp_lanes_for(int n_obs) {
   return 8;
 }
 
-Tile warp_tile(int64_t n_sys, int n_pl, int n_obs) {
-  // A grid of one CTA per W * 32 / G systems.  When it fits on the device
+bool warp_lanes_fit(int G, int n_obs) { return G == 8 || n_obs >= G * kChunk; }
+
+Tile warp_tile(int64_t n_sys, int n_pl, int n_obs, bool multi_warp) {
+  // A grid of one CTA per block / G systems.  When it fits on the device
   // at once, an SM holds at most ceil(CTAs / n_sm) CTAs; otherwise the
   // hardware refills the SMs wave after wave and the load per SM is the
-  // total over the SMs.  Pick the W whose busiest SM carries the fewest
-  // warps of work; among equals, the one with more warps resident per SM
-  // (more latency hidden), then the larger CTA (fewer CTAs share an SM: on
-  // the 4096-system batch one CTA of 27 warps per SM ran 18.4 us where
-  // three of nine ran 20.5 us, with the same 27 systems per SM).
-  const int G = warp_lanes_for(n_obs);
-  const int spw = 32 / G;
+  // total over the SMs.  Pick the shape whose busiest SM carries the least
+  // work (warps x 32 / G: systems' worth of lanes); among equals, the one
+  // with more warps resident per SM (more latency hidden), then the larger
+  // CTA (fewer CTAs share an SM: on the 4096-system batch one CTA of 27
+  // warps per SM ran 18.4 us where three of nine ran 20.5 us, with the
+  // same 27 systems per SM).  With multi_warp, 32 lanes per system and at
+  // least 4 observations per lane at G = 64 or 128, a system split over 2
+  // or 4 warps replaces that shape if its load is lower by more than 1 %,
+  // or within 1 % in fewer waves, or in as many waves with at least as many
+  // warps resident (then the larger CTA).  Back to back on n_obs = 256
+  // (us per launch): 256 systems 6.51 -> 5.24, 512: 6.65 -> 5.41, 1024:
+  // 7.44 -> 6.75, 2048: 9.52 -> 9.23; the 4096-system batch keeps its single
+  // wave of 27-warp CTAs (13.9 against 17.4 for 64 lanes in 28-warp CTAs).
+  const int G0 = warp_lanes_for(n_obs);
   const int64_t n_sm = sm_count();
-  Tile best{G, 8 * 32, 0, 3};
+  Tile best{G0, 8 * 32, 0, 3};
   double best_load = 1e300;
-  int64_t best_warps = 0;
-  for (int W = 4; W <= 32; ++W) {
-    const int block = 32 * W;
-    const int occ = blocks_per_sm(n_pl, 0, block, warp_smem(n_pl, G, block, n_obs));
-    if (occ < 1) continue;
-    const int64_t ctas = (n_sys + (int64_t)W * spw - 1) / ((int64_t)W * spw);
-    const int64_t cap = n_sm * occ;
-    double load;
-    int64_t resident;
-    if (ctas <= cap) {
-      resident = (ctas + n_sm - 1) / n_sm;
-      load = (double)resident * W;
-    } else {
-      resident = occ;
-      load = (double)((ctas + n_sm - 1) / n_sm) * W;
-    }
-    const int64_t warps = resident * W;
-    const bool tie = load <= best_load * (1.0 + 1e-9);
-    if (load < best_load * (1.0 - 1e-9) || (tie && warps >= best_warps)) {
-      best_load = load;
-      best_warps = warps;
-      best = Tile{G, block, 0, 3};
+  int64_t best_warps = 0, best_waves = 0;
+  for (int G : {G0, 64, 128}) {
+    const bool multi = G > 32;
+    if (multi && (!multi_warp || G0 != 32 || !warp_lanes_fit(G, n_obs))) continue;
+    for (int W = 4; W <= 32; ++W) {
+      const int block = 32 * W;
+      if (block % G) continue;
+      const int occ = blocks_per_sm(n_pl, 0, block, warp_smem(n_pl, G, block, n_obs));
+      if (occ < 1) continue;
+      const int64_t spc = block / G;                 // systems per CTA
+      const int64_t ctas = (n_sys + spc - 1) / spc;
+      const int64_t cap = n_sm * occ;
+      const int64_t per_sm = (ctas + n_sm - 1) / n_sm;
+      const int64_t resident = ctas <= cap ? per_sm : occ;
+      const double load = (double)per_sm * W * 32.0 / G;
+      const int64_t warps = resident * W;
+      const int64_t waves = (ctas + cap - 1) / cap;
+      bool take;
+      if (!multi) {
+        const bool tie = load <= best_load * (1.0 + 1e-9);
+        take = load < best_load * (1.0 - 1e-9) || (tie && warps >= best_warps);
+      } else {
+        const bool near = load <= best_load * 1.01;
+        take = load < best_load * 0.99 ||
+               (near && (waves < best_waves || (waves == best_waves && warps >= best_warps)));
+      }
+      if (take) {
+        best_load = load;
+        best_warps = warps;
+        best_waves = waves;
+        best = Tile{G, block, 0, 3};
+      }
     }
   }
-  best.obs_tile = warp_obs_tile(n_obs, G);
+  best.obs_tile = warp_obs_tile(n_obs, best.G);
   return best;
 }
 
@@ -428,9 +476,9 @@ cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float
   if (variant == 2) resid = nullptr;
   const void *fn = warp_kernel_for(a.n_pl, variant);
   if (!fn) return cudaErrorInvalidValue;
-  const int spr = (block / 32) * (32 / G);
+  const int spr = block / G;
   const int obs_tile = warp_obs_tile(a.n_obs, G);
-  const size_t smem = WarpLayout(spr, a.n_pl, obs_tile).total;
+  const size_t smem = WarpLayout(spr, a.n_pl, obs_tile, block / 32).total;
   if (blocks_per_sm(a.n_pl, variant, block, smem) < 1) return cudaErrorInvalidConfiguration;
   const int64_t ctas = (a.n_sys + spr - 1) / spr;
   if (ctas > 0x7fffffff) return cudaErrorInvalidConfiguration;

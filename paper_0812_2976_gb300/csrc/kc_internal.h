@@ -151,7 +151,12 @@ cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out
 // evenly over the SMs.  Carries a DE-MC step when a.demc.states is set.
 bool warp_tile_ok(int G, int block);
 int warp_lanes_for(int n_obs);
-Tile warp_tile(int64_t n_sys, int n_pl, int n_obs);
+// G lanes per system give every lane at least 4 observations (G = 8: always)
+bool warp_lanes_fit(int G, int n_obs);
+// The built-in warp tile; multi_warp admits systems split over 2 or 4 warps
+// (not for the DE-MC step, whose epilogue those shapes move behind a CTA
+// barrier: 2.93e4 against 3.12e4 generations/s on halves of 2048 chains).
+Tile warp_tile(int64_t n_sys, int n_pl, int n_obs, bool multi_warp = true);
 cudaError_t launch_chi2_mixed_warp(const UniformArgs &a, const Tile &tile, float *out,
                                    float *resid, cudaStream_t st);
 // Gradient (kc_grad.cu); nll = true: the free-jitter log-likelihood variant
@@ -181,6 +186,7 @@ enum class Kind { Chi2F64 = 0, Chi2Mixed = 1, GradF64 = 2, GradMixed = 3, GnMixe
 Tile default_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
 Tile builtin_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);  // without a table entry
 Tile choose_tile(Kind kind, int64_t n_sys, int n_pl, int n_obs);
+bool has_tile_entry(Kind kind, int64_t n_sys, int n_pl, int n_obs);  // tuned or pinned
 int obs_tile_for(Kind kind, int n_obs);
 
 // DE-MC step pieces (kc_demcmc.cu).

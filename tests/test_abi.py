@@ -175,10 +175,12 @@ def test_tile_table_host_logic(lib):
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(16, 64, 2))) == 1
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(2048, 64, 2))) == 1
     assert lib.kc_set_tile(0, 1, 4096, 4, 256, None) == 0
-    # split = 3 (persistent): 8, 16 or 32 lanes, whole warps up to 1024 threads
-    for good in ((32, 288, 3), (8, 1024, 3), (16, 32, 3)):
+    # split = 3 (warp kernel): 8 to 128 lanes (64, 128: a system over two or
+    # four warps), whole warps up to 1024 threads, whole systems per CTA
+    for good in ((32, 288, 3), (8, 1024, 3), (16, 32, 3), (64, 128, 3), (128, 1024, 3)):
         assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*good))) == 0
-    for bad in ((4, 128, 3), (32, 100, 3), (32, 2048, 3)):
+    for bad in ((4, 128, 3), (32, 100, 3), (32, 2048, 3), (64, 96, 3), (128, 64, 3),
+                (256, 256, 3), (48, 96, 3)):
         assert lib.kc_set_tile(0, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(*bad))) == 1
     assert lib.kc_set_tile(1, 1, 4096, 4, 256, ctypes.byref(_lib.KcTile(32, 288, 3))) == 1
     assert lib.kc_set_tile(0, 0, 4096, 4, 256, ctypes.byref(_lib.KcTile(32, 288, 3))) == 1

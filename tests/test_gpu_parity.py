@@ -476,7 +476,7 @@ def test_high_eccentricity_chi2_and_gradient(kc, oracle_mod):
 
 
 @pytest.mark.parametrize("tile", [(4, 128, 0), (8, 64, 1), (32, 128, 0), (64, 128, 2),
-                                  (8, 64, 3), (16, 96, 3), (32, 288, 3)])
+                                  (8, 64, 3), (16, 96, 3), (32, 288, 3), (64, 128, 3)])
 def test_high_eccentricity_mixed_warps(kc, oracle_mod, tile):
     """Every third system has a planet at e = 0.985, the others e <= 0.9:
     with 4 or 8 threads per system a warp holds several systems of both
@@ -521,7 +521,8 @@ def test_rv_predict_vs_oracle(kc, oracle_mod):
                                   (32, 128, 2), (128, 64, 2), (256, 256, 2), (1024, 32, 2),
                                   (24, 96, 0), (12, 192, 0), (48, 96, 0), (24, 192, 1),
                                   (3, 96, 0), (16, 224, 0), (32, 160, 0), (8, 224, 1),
-                                  (32, 288, 3), (32, 1024, 3), (16, 160, 3), (8, 32, 3)])
+                                  (32, 288, 3), (32, 1024, 3), (16, 160, 3), (8, 32, 3),
+                                  (64, 256, 3), (64, 896, 3), (128, 512, 3), (128, 128, 3)])
 def test_split_variant_matches_oracle(kc, oracle_mod, tile):
     """The two-pass (preparation + main) variant of the mixed kernel and the
     fused kernel with a thread count per system that is not a power of two
@@ -543,7 +544,7 @@ def test_split_variant_matches_oracle(kc, oracle_mod, tile):
         kc.kc_set_tile("chi2", "mixed", w.n_sys, w.n_pl, w.n_obs, None)
 
 
-@pytest.mark.parametrize("tile", [(32, 128, 3), (16, 512, 3)])
+@pytest.mark.parametrize("tile", [(32, 128, 3), (16, 512, 3), (64, 192, 3), (128, 512, 3)])
 def test_persistent_kernel_rounds_and_observation_tiles(kc, oracle_mod, tile):
     """The persistent kernel with more rounds than resident CTAs (each CTA
     takes several rounds, setting up each one's planets) and more
