@@ -146,9 +146,10 @@ cudaError_t launch_chi2_single(const UniformArgs &a, const Tile &tile, float *ou
 cudaError_t launch_chi2_mixed(const UniformArgs &a, const Tile &tile, float *out,
                               float *resid, cudaStream_t st);
 // Warp-per-system mixed chi2 (kc_chi2_warp.cu): G = 8, 16 or 32 lanes per
-// system, `block` threads (a multiple of 32, at most 1024) per CTA, one CTA
-// per block * G / 32 systems; warp_tile picks the block that spreads the CTAs
-// evenly over the SMs.  Carries a DE-MC step when a.demc.states is set.
+// system, or 64 or 128 (a system over two or four warps), `block` threads (a
+// multiple of 32 and of G, at most 1024) per CTA, one CTA per block / G
+// systems; warp_tile picks the shape that spreads the work evenly over the
+// SMs.  Carries a DE-MC step when a.demc.states is set.
 bool warp_tile_ok(int G, int block);
 int warp_lanes_for(int n_obs);
 // G lanes per system give every lane at least 4 observations (G = 8: always)
