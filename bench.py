@@ -112,12 +112,14 @@ F64_FLOPS_PER_EVAL = 6 + 20 + 13 + 8 + 11
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the mixed chi2 kernel in its current form, from an ncu capture of this
-# benchmark's own default workload (tile 32,864,3, the warp-per-system
-# kernel): the batch reads its 688 KB of parameters and 6 KB of observations
-# once (the rest is sector granularity of the 168-byte parameter rows).
-# Keyed by (config, n_sys override, tile); other launches report null.
-DRAM_BYTES_PER_LAUNCH = {(1, None, (32, 864, 3)): 761344}
+# the mixed chi2 kernel in its current form, from ncu captures of this
+# benchmark's own default workload at the two tiles its autotuner picks
+# (the warp-per-system kernel with 27- or 28-warp CTAs, within 0.1 % of each
+# other back to back): the batch reads its 688 KB of parameters and 6 KB of
+# observations once (the rest is sector granularity of the 168-byte
+# parameter rows).  Keyed by (config, n_sys override, tile); other launches
+# report null.
+DRAM_BYTES_PER_LAUNCH = {(1, None, (32, 864, 3)): 763904, (1, None, (32, 896, 3)): 763904}
 
 
 def sm_count() -> int:

@@ -371,7 +371,8 @@ kc_status kc_get_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys,
 
 /* Autotuner: times every admissible tile on the given problem (device
  * arrays as for kc_chi2_eval_ex / kc_chi2_grad / kc_chi2_gauss_newton;
- * t0 = 0, no jitter), stores the fastest in the table (the built-in tile
+ * t0 = 0, no jitter; per launch, the mean of four launches back to back,
+ * the best of three), stores the fastest in the table (the built-in tile
  * unless another is at least 1 % faster, so that shapes within timing
  * noise of each other do not trade places from run to run) and returns it
  * in *best (and its time in *best_ms, may be NULL).  Blocking: synchronises `stream`; must not be

@@ -721,14 +721,19 @@ kc_status kc_autotune(const double *params, const double *t, const double *v_obs
       continue;
     }
     if (err != cudaSuccess) break;
+    // per launch: the mean of four launches back to back (as a caller
+    // evaluating batch after batch runs them: launches that overlap their
+    // neighbours' start and end are credited for it), the best of three
+    constexpr int kBackToBack = 4;
     float tmin = 1e30f;
-    for (int rep = 0; rep < 5 && err == cudaSuccess; ++rep) {
+    for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
       cudaEventRecord(e0, s);
-      err = launch(tile);
+      for (int i = 0; i < kBackToBack && err == cudaSuccess; ++i) err = launch(tile);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
+      ms /= kBackToBack;
       tmin = ms < tmin ? ms : tmin;
     }
     if (err != cudaSuccess) break;
