@@ -149,6 +149,22 @@ def test_back_to_back_launches_see_the_writes_before_them(kc, oracle_mod):
         assert rel_err(out.cpu().numpy(), ref).max() <= MIXED_TOL
 
 
+def test_builtin_warp_tiles_on_a_152_sm_gpu(kc):
+    """The built-in tile of the mixed chi2 (no table entry) for n_obs = 256:
+    a system over two warps where one warp per system leaves the SMs few
+    warps, one 27-warp CTA per SM for the 4096-system batch, the tile kernel
+    nowhere (the shapes measured fastest back to back on a GB300)."""
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("the expected shapes are those of a 152-SM part")
+    want = {256: (64, 128, 3), 512: (64, 256, 3), 1024: (64, 448, 3), 2048: (64, 896, 3),
+            4096: (32, 864, 3)}
+    for n_sys, tile in want.items():
+        kc.kc_set_tile("chi2", "mixed", n_sys, 4, 256, None)
+        assert kc.kc_get_tile("chi2", "mixed", n_sys, 4, 256) == tile
+    # fewer than 4 observations per lane at 64 lanes: one warp per system
+    assert kc.kc_get_tile("chi2", "mixed", 1024, 4, 200)[0] == 32
+
+
 # ------------------------------------------------------------ config 2
 
 def test_config2_grid_sweep_full_size_sampled(kc, oracle_mod):
