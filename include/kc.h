@@ -361,8 +361,8 @@ typedef enum kc_kernel {
 } kc_kernel;
 
 /* Tiles are looked up by (kernel, mode, n_pl, power-of-two bucket of n_sys,
- * power-of-two bucket of n_obs) in a process-wide table; a missing entry
- * uses a built-in heuristic.  kc_set_tile (tile == NULL removes the entry)
+ * power-of-two bucket of n_obs, SM count of the current device) in a
+ * process-wide table; a missing entry uses a built-in heuristic.  kc_set_tile (tile == NULL removes the entry)
  * and kc_get_tile (the tile that would be used) act on that table. */
 kc_status kc_set_tile(kc_kernel kernel, kc_mode mode, int64_t n_sys,
                       int32_t n_pl, int32_t n_obs, const kc_tile *tile);

@@ -193,10 +193,14 @@ int bucket(int64_t x) {
   return b;
 }
 
+// A table entry holds for one kernel, planet count, power-of-two size class
+// of n_sys and n_obs, and SM count (a shape tuned on one part is not taken
+// for another with a different number of SMs).
 struct TileKey {
-  int kind, n_pl, sys_b, obs_b;
+  int kind, n_pl, sys_b, obs_b, sms;
   bool operator<(const TileKey &o) const {
-    return std::tie(kind, n_pl, sys_b, obs_b) < std::tie(o.kind, o.n_pl, o.sys_b, o.obs_b);
+    return std::tie(kind, n_pl, sys_b, obs_b, sms) <
+           std::tie(o.kind, o.n_pl, o.sys_b, o.obs_b, o.sms);
   }
 };
 
@@ -204,7 +208,7 @@ std::mutex g_tile_mu;
 std::map<TileKey, Tile> g_tiles;
 
 TileKey key_of(Kind kind, int64_t n_sys, int n_pl, int n_obs) {
-  return TileKey{(int)kind, n_pl, bucket(n_sys), bucket(n_obs)};
+  return TileKey{(int)kind, n_pl, bucket(n_sys), bucket(n_obs), sm_count()};
 }
 
 }  // namespace
