@@ -416,10 +416,14 @@ def peaks():
         return {}, "fallback"
 
 
-def oracle_cpu_baseline(w, seconds=3.0):
+def oracle_cpu_baseline(w, seconds=3.0, gpu_chi2=None):
     """Time the FP64 CPU oracle on the host cores over this workload's batch:
     whole batches repeated until ~`seconds` of wall time.  Its observations
-    are formed by the oracle itself from the same seeded draws."""
+    are formed by the oracle itself from the same seeded draws.  With
+    gpu_chi2(mode, v_obs) (the library's chi2 of the same batch on those
+    observations), also the paper's accuracy figures (Table 2: maximum
+    fractional and absolute error, L1 norm of the error) of both paths
+    against the oracle over every system of the batch."""
     import oracle
     oracle.build()
     v_obs = oracle.predict(w.truth, w.t, w.n_pl, w.t0)[0] + w.noise
@@ -428,7 +432,7 @@ def oracle_cpu_baseline(w, seconds=3.0):
     oracle.chi2(w.params[:64], w.t, v_obs, w.sigma, w.n_pl, w.t0)   # warm
     reps, t_start = 0, time.perf_counter()
     while True:
-        oracle.chi2(w.params, w.t, v_obs, w.sigma, w.n_pl, w.t0)
+        ref = oracle.chi2(w.params, w.t, v_obs, w.sigma, w.n_pl, w.t0)
         reps += 1
         el = time.perf_counter() - t_start
         if el >= seconds:
@@ -448,6 +452,14 @@ def oracle_cpu_baseline(w, seconds=3.0):
         oracle.set_threads(cores)
     out["single_thread"] = {"value": n1 * w.n_pl * w.n_obs / el1, "cores": 1,
                             "sample": f"the first {n1} systems, {el1:.2f} s wall"}
+    if gpu_chi2 is not None:
+        acc = {"systems": int(w.n_sys), "against": "the FP64 CPU oracle on the same inputs"}
+        for mode in ("mixed", "fp64"):
+            err = np.abs(np.asarray(gpu_chi2(mode, v_obs), dtype=np.float64) - ref)
+            acc[mode] = {"max_frac_err": float(np.max(err / np.abs(ref))),
+                         "max_abs_err": float(np.max(err)),
+                         "l1_rel_err": float(np.sum(err) / np.sum(np.abs(ref)))}
+        out["accuracy"] = acc
     return out
 
 
@@ -818,7 +830,13 @@ def run_kc(args):
     }
     line.update(extras)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_cpu_baseline(w)
+        def gpu_chi2(mode, v_obs):
+            vo = torch.tensor(v_obs, device=dev)
+            if mode == "mixed":
+                return kc.kc_chi2_eval_mixed(P, T, vo, S).cpu().numpy()
+            return kc.kc_chi2_eval(P, T, vo, S).cpu().numpy()
+        line["cpu_baseline"] = oracle_cpu_baseline(w, gpu_chi2=gpu_chi2)
+        line["accuracy"] = line["cpu_baseline"].pop("accuracy")
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
