@@ -9,10 +9,11 @@
 // the SMs rather than for a tile:
 //
 //  - A CTA of W warps evaluates W * 32 / G systems (one round).  The host
-//    picks W so that the CTAs of the first wave land evenly on the SMs (for
-//    4096 systems, 27 warps per CTA: one CTA and 27 systems on every SM,
-//    where tiles of 16 systems leave some SMs with 32 and others with 16).  Larger batches run many waves; the hardware then overlaps one
-//    CTA's prologue with the work of the others on its SM.
+//    picks G and W so that the CTAs of the first wave land evenly on the
+//    SMs (for 4096 systems, 27 warps per CTA: one CTA and 27 systems on
+//    every SM, where tiles of 16 systems leave some SMs with 32 and others
+//    with 16).  Larger batches run many waves; the hardware then overlaps
+//    one CTA's prologue with the work of the others on its SM.
 //  - Prologue: every global load (the reference time, this thread's
 //    observation and its planet's parameters) is issued before any of them
 //    is used, so the CTA waits for memory once.
